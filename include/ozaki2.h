@@ -1,0 +1,247 @@
+/*
+ * ozaki2.h -- C ABI of the GB300 Ozaki-scheme-II multiple-precision GEMM.
+ *
+ * The library computes C = A * B for p-bit floating-point matrices
+ * (p = 2 .. 2048) with the Ozaki scheme II of "Ozaki Scheme II Is Fast on CPUs
+ * Too" (Kouya, 2026): shared-exponent integerization (Sec. 4.2, Eq. 1-3),
+ * centered residues over the pairwise-coprime modulus set of Sec. 4.3 (54
+ * one-limb moduli <= 255, then two-limb primes <= 16191 split in balanced base
+ * 128 with the 3-GEMM Karatsuba combine of Eq. 4-5), one exact integer GEMM
+ * per plane on the sm_103a tensor cores, mod-reduction of each product, the
+ * direct CRT of Sec. 4.4 and one final round-to-nearest-even to p bits.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an int status (OZ2_OK = 0 or one of the OZ2_E* codes
+ *   below); nothing aborts and no C++ exception crosses this boundary.
+ * - Device work is enqueued on the given stream (a cudaStream_t; NULL is the
+ *   legacy default stream) and runs asynchronously.  Argument errors are
+ *   reported before anything is enqueued.  Errors detected on the device
+ *   (a range check of the CRT failing, a wait that timed out) set a status
+ *   word that ozaki2_check() reads after synchronising the stream.
+ * - All matrix pointers are device pointers owned by the caller; the library
+ *   never frees them.  Plans, caches and graphs are owned by the library and
+ *   released by their destroy calls.
+ * - A plan may be executed many times but not concurrently from two host
+ *   threads or on two streams at once.
+ *
+ * Matrix storage (ozaki2_mat), row-major, struct of arrays:
+ *   element (i, j) has nl = ceil(p/64) limbs, limb q at
+ *       limbs[q * plane_stride + i * ld + j]           (uint64, least significant first)
+ *   and exponent exp[i * ld + j], sign sign[i * ld + j] (0 = +, 1 = -).
+ *   Value = (-1)^sign * (sum_q limb_q 2^(64 q)) * 2^(exp - 64 nl), the MPFR
+ *   convention |x| in [2^(exp-1), 2^exp).  A nonzero significand has bit 63 of
+ *   its top limb set (MSB-normalised); an element whose top limb is zero is
+ *   zero (its other limbs, exp and sign are ignored).  Inf/NaN are not
+ *   representable (the paper treats them as 0, Sec. 10).  |exp| <= 2^28.
+ *   Outputs are written MSB-normalised with the 64 nl - p low bits zero;
+ *   a zero output has all limbs 0, exp 0 and sign 0.
+ */
+#ifndef OZAKI2_H
+#define OZAKI2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OZ2_API __attribute__((visibility("default")))
+#else
+#define OZ2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+  OZ2_OK = 0,
+  OZ2_EINVAL = 1,    /* null pointer, size <= 0, p < 2, bad option, workspace too small */
+  OZ2_ERANGE = 2,    /* K > 133000 (int32 exactness cap, Sec. 4.3(a)), p > 2048, or the
+                        modulus table cannot reach the CRT bound (Eq. crtcond) */
+  OZ2_ENOMEM = 3,    /* a library-owned allocation failed */
+  OZ2_ECUDA = 4,     /* a CUDA runtime/driver call failed */
+  OZ2_EINTERNAL = 5, /* a device-side consistency check failed (status word set) */
+  OZ2_ETIMEOUT = 6,  /* a bounded device-side wait gave up (status word set) */
+  OZ2_ENODEV = 7     /* no usable sm_103 device */
+};
+
+/* GEMM engines for the per-plane products. */
+enum {
+  OZ2_ENGINE_TC = 0,   /* tcgen05 kind::f16 tensor-core kernel (TMA + TMEM), default */
+  OZ2_ENGINE_SIMT = 1  /* CUDA-core int32 kernel: slow cross-check engine */
+};
+
+/* Plane schedules. */
+enum {
+  OZ2_SCHED_GROUPED = 0, /* all planes of all problems in one persistent launch */
+  OZ2_SCHED_PLAIN = 1    /* one GEMM launch per modulus per problem */
+};
+
+typedef struct {
+  uint64_t* limbs;
+  int32_t* exp;
+  int8_t* sign;
+  int64_t ld;           /* row stride in elements (>= number of columns) */
+  int64_t plane_stride; /* elements between limb planes (>= rows * ld) */
+} ozaki2_mat;
+
+typedef struct {
+  int guard_bits; /* g of Eq. 3, default 16 */
+  int t_bits;     /* 0: t = p + g + ceil(log2 K) (Eq. 3); > 0 forces t */
+  int engine;     /* OZ2_ENGINE_* */
+  int k_chunk;    /* K per exact fp32 accumulation chunk: multiple of 64, <= 1024;
+                     0 = 1024 (127^2 * 1024 + 16191 < 2^24 keeps every partial sum exact) */
+  int grid;       /* persistent CTAs of the grouped GEMM; 0 = one per SM */
+  int schedule;   /* OZ2_SCHED_* */
+  int timing;     /* nonzero: record per-stage CUDA events (ozaki2_last_timings) */
+} ozaki2_opts;
+
+/* Facts about a plan (all computed on the host at plan creation). */
+typedef struct {
+  int count;        /* problems in the plan (1 for a single GEMM) */
+  int t;            /* internal width of problem 0 (Eq. 3) */
+  int L;            /* moduli of problem 0 */
+  int L1;           /* one-limb moduli among them */
+  int G;            /* int8 planes (GEMMs) of problem 0: L1 + 3 (L - L1) */
+  int crt_digits;   /* 32-bit digits of the CRT accumulator: ceil(bits(P)/32) + 2 */
+  int units;        /* (modulus, output tile) work units over all problems */
+  int jobs;         /* tensor-core accumulation jobs over all problems */
+  size_t workspace_bytes;
+} ozaki2_info;
+
+typedef struct {
+  int64_t M, N, K;
+  int p;
+  ozaki2_mat A; /* M x K */
+  ozaki2_mat B; /* K x N */
+  ozaki2_mat C; /* M x N (written) */
+} ozaki2_problem;
+
+typedef struct ozaki2_plan_s* ozaki2_plan;
+typedef struct ozaki2_cache_s* ozaki2_cache;
+typedef struct ozaki2_graph_s* ozaki2_graph;
+
+/* Fill *o with the defaults (g = 16, auto t, tensor-core engine, k_chunk 1024,
+   one CTA per SM, grouped schedule, no timing).  Host only. */
+OZ2_API int ozaki2_opts_default(ozaki2_opts* o);
+
+/* Human-readable text of a status code (static storage). */
+OZ2_API const char* ozaki2_strerror(int status);
+
+/* Create a plan for one M x N x K product at p bits (Sec. 4.1 flow).  Host
+   only: chooses t (Eq. 3) and the shortest modulus prefix with
+   log2 P > 2t + log2 K + 2 (Sec. 4.3), builds the CRT tables (Sec. 4.4) and
+   the tile schedule.  Device tables are uploaded lazily by the first execute
+   on the device that is current then.  opts may be NULL (defaults). */
+OZ2_API int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts,
+                       ozaki2_plan* out);
+
+/* Plan for `count` independent products (only M, N, K, p of each problem are
+   read).  All of them run in one grouped persistent launch per stage. */
+OZ2_API int ozaki2_plan_create_batched(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
+                               ozaki2_plan* out);
+
+OZ2_API int ozaki2_plan_destroy(ozaki2_plan plan);
+
+/* Host-side facts; see ozaki2_info. */
+OZ2_API int ozaki2_plan_info(ozaki2_plan plan, ozaki2_info* out);
+
+/* Copy the moduli of problem `prob` (in plane order) into out[0..cap). Host only. */
+OZ2_API int ozaki2_plan_moduli(ozaki2_plan plan, int prob, int32_t* out, int cap);
+
+/* Host copies of problem `prob`'s CRT tables (Sec. 4.4): P as crt_digits
+   little-endian 32-bit digits, M_l = P / m_l as L x crt_digits digits
+   (row l), and M_l^{-1} mod m_l.  Any output may be NULL.  Host only. */
+OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digits, uint32_t* M_digits,
+                           uint32_t* Minv);
+
+/* Byte offsets of the workspace regions of problem `prob` (for inspection of
+   intermediates after an execute):
+     off[0] row exponents e   int32 [M]
+     off[1] column exponents f int32 [N]
+     off[2] A planes  bf16 [G][M][Kp]   (Kp = K rounded up to 8; K-major)
+     off[3] B planes  bf16 [G][N][Kp]   (transposed: column j of B is row j)
+     off[4] reduced products u  uint16 [L][M][N]
+   and *kp = Kp.  Plane order: one-limb moduli in plane order, then for each
+   two-limb modulus the planes r0, r1, r0 + r1 (balanced base-128 split). */
+OZ2_API int ozaki2_plan_layout(ozaki2_plan plan, int prob, size_t off[5], int64_t* kp);
+
+/* Debugging aid: when dev_buf is not NULL, later executes also write the
+   CRT integer c_hat of every output of problem `prob` to dev_buf (device,
+   uint32 [M*N][crt_digits + 1]: word 0 = 1 for a negative c_hat, then
+   |c_hat| as crt_digits little-endian digits), row-major over (i, j). */
+OZ2_API int ozaki2_plan_set_debug_chat(ozaki2_plan plan, int prob, uint32_t* dev_buf);
+
+/* Run the plan: C = A * B rounded to p bits, via workspace `ws` (device,
+   >= info.workspace_bytes, 256-byte aligned, caller-owned, contents need not
+   be initialised and are clobbered).  Single-problem plans only. */
+OZ2_API int ozaki2_execute(ozaki2_plan plan, const ozaki2_mat* A, const ozaki2_mat* B, ozaki2_mat* C,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* Run a batched plan on `count` problems with the planned shapes. */
+OZ2_API int ozaki2_execute_batched(ozaki2_plan plan, int count, const ozaki2_problem* probs, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Capture one execute of a (batched or single) plan with fixed pointers into
+   a CUDA graph; ozaki2_graph_launch replays it on any stream. */
+OZ2_API int ozaki2_graph_create(ozaki2_plan plan, int count, const ozaki2_problem* probs, void* ws,
+                        size_t ws_bytes, void* stream, ozaki2_graph* out);
+OZ2_API int ozaki2_graph_launch(ozaki2_graph g, void* stream);
+OZ2_API int ozaki2_graph_destroy(ozaki2_graph g);
+
+/* Convenience single call: C = A * B at p bits with a plan and workspace
+   cached by the library (library-owned device memory, kept until
+   ozaki2_release_cache()). */
+OZ2_API int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
+                ozaki2_mat* C, const ozaki2_opts* opts, void* stream);
+
+/* Convenience batched call (library-owned plan and workspace). */
+OZ2_API int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts,
+                        void* stream);
+
+/* Free the plans and workspaces cached by ozaki2_gemm / ozaki2_gemm_batched. */
+OZ2_API int ozaki2_release_cache(void);
+
+/* Synchronise `stream` and read the plan's device status word:
+   OZ2_OK, OZ2_EINTERNAL or OZ2_ETIMEOUT.  Clears the word. */
+OZ2_API int ozaki2_check(ozaki2_plan plan, void* stream);
+
+/* Per-stage device times of the plan's last execute with opts.timing set, in
+   milliseconds: [0] exponent scan, [1] residues (integerize + centered
+   residues + plane writes), [2] plane GEMMs with fused mod-reduce, [3] CRT and
+   rounding, [4] total.  Synchronises on the recorded events. */
+OZ2_API int ozaki2_last_timings(ozaki2_plan plan, float ms[5]);
+
+/* ---------------------------------------------------------------------------
+ * binary64 mode (p = 53): C = A B for row-major double matrices, computed
+ * through the same exact path, with a cache of the forward's int8 residue
+ * planes for the backward.  Readings for the backward (the paper has none):
+ * dA = dC B^T reuses the cached planes of B (scaled per column j by 2^f_j),
+ * with dC scaled by 2^f_j per column and integerized per row; dB = A^T dC
+ * reuses the cached planes of A, with dC scaled by 2^e_i per row and
+ * integerized per column.  The forward's modulus set is chosen to cover all
+ * three products.  Results are rounded to nearest-even binary64.
+ * ------------------------------------------------------------------------- */
+
+/* Forward.  cache_out may be NULL (no backward); else *cache_out receives a
+   library-owned cache (device memory) to pass to ozaki2_dgemm_bwd. */
+OZ2_API int ozaki2_dgemm_fwd(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, double* C, int64_t ldc,
+                     const ozaki2_opts* opts, ozaki2_cache* cache_out, void* stream);
+
+/* Backward: dA = dC B^T (M x K) and dB = A^T dC (K x N); either output may be
+   NULL.  dC is M x N. */
+OZ2_API int ozaki2_dgemm_bwd(ozaki2_cache cache, const double* dC, int64_t lddc, double* dA,
+                     int64_t ldda, double* dB, int64_t lddb, void* stream);
+
+OZ2_API int ozaki2_cache_destroy(ozaki2_cache cache);
+
+/* Library version string (static storage). */
+OZ2_API const char* ozaki2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZAKI2_H */

@@ -359,14 +359,19 @@ def crt_signed(u: list[int], tab: CrtTables) -> int:
 # ---------------------------------------------------------------------------
 
 class Params:
-    """t, the modulus set and its CRT tables for an M x N x K product at p bits."""
+    """t, the modulus set and its CRT tables for an M x N x K product at p bits.
 
-    def __init__(self, K: int, p: int, g: int = GUARD_BITS):
+    ``inner`` (binary64 mode) widens t and the CRT bound to cover inner
+    lengths up to max(K, inner), so that one modulus set serves the forward
+    and both backward products."""
+
+    def __init__(self, K: int, p: int, g: int = GUARD_BITS, inner: int = 0):
         if K > K_CAP:
             raise ValueError("K above the int32 exactness cap")
         self.K, self.p = K, p
-        self.t = internal_width(p, K, g)
-        self.moduli = select_moduli(self.t, self.t, K)
+        q = max(K, inner)
+        self.t = internal_width(p, q, g)
+        self.moduli = select_moduli(self.t, self.t, q)
         self.L = len(self.moduli)
         self.G = gemm_count(self.moduli)
         self.tab = CrtTables(self.moduli)
@@ -573,3 +578,78 @@ def fp64_as_mat(X: np.ndarray) -> dict:
 
 def to_double(limbs, e: int, s: int) -> float:
     return float(to_fraction(limbs, e, s))
+
+
+# ---------------------------------------------------------------------------
+# binary64 mode: forward and backward entries (reading for the backward, which
+# the paper does not cover: the forward's integerized B_hat / A_hat are reused;
+# dC is scaled by 2^f_j per column (dA) or 2^e_i per row (dB), exactly, and
+# integerized with its own shared exponents per row (dA) / column (dB))
+# ---------------------------------------------------------------------------
+
+def f64_exponents(X: np.ndarray, axis: int) -> np.ndarray:
+    """MPFR exponent max over the nonzero entries of each row (axis=1 reduces
+    over columns) or column (axis=0); None for an all-zero line."""
+    m, e = np.frexp(X)            # X = m 2^e, |m| in [0.5, 1): MPFR exponent e
+    e = np.where(X != 0, e, np.iinfo(np.int64).min)
+    best = e.max(axis=axis)
+    return [None if b == np.iinfo(np.int64).min else int(b) for b in best]
+
+
+def _f64_int(x: float, shift: int, e_line: int, t: int) -> int:
+    if x == 0.0:
+        return 0
+    ssig, e, nl = from_double(float(x))
+    return integerize(ssig, e + shift, nl, e_line, t)
+
+
+def dgemm_params(M: int, N: int, K: int) -> Params:
+    return Params(K, 53, inner=max(M, N, K))
+
+
+def _round_double(chat: int, scale: int) -> float:
+    sg, S, e = round_to_p(chat, scale, 53)
+    return float((-1) ** sg * Fraction(S) * Fraction(2) ** (e - 53)) if S else 0.0
+
+
+def dgemm_fwd_entry(X, Y, i, j, par: Params, e=None, f=None) -> float:
+    e = f64_exponents(X, 1) if e is None else e
+    f = f64_exponents(Y, 0) if f is None else f
+    if e[i] is None or f[j] is None:
+        return 0.0
+    arow = [_f64_int(x, 0, e[i], par.t) for x in X[i, :]]
+    bcol = [_f64_int(y, 0, f[j], par.t) for y in Y[:, j]]
+    return _round_double(entry(arow, e[i], bcol, f[j], par)["chat"], e[i] + f[j] - 2 * par.t)
+
+
+def dgemm_dA_entry(Y, dC, i, k, par: Params, f=None) -> float:
+    """dA_ik = sum_j dC_ij B_kj through the cached B_hat (see module notes)."""
+    f = f64_exponents(Y, 0) if f is None else f
+    d1 = [(float(dC[i, j]), f[j]) for j in range(Y.shape[1])]
+    exps = [from_double(x)[1] + fj for x, fj in d1 if x != 0.0 and fj is not None]
+    if not exps:
+        return 0.0
+    g_i = max(exps)
+    drow = [_f64_int(x, fj, g_i, par.t) if fj is not None else 0 for x, fj in d1]
+    brow = [_f64_int(float(Y[k, j]), 0, f[j], par.t) if f[j] is not None else 0
+            for j in range(Y.shape[1])]
+    return _round_double(entry(drow, g_i, brow, 0, par)["chat"], g_i - 2 * par.t)
+
+
+def dgemm_dB_entry(X, dC, k, j, par: Params, e=None) -> float:
+    """dB_kj = sum_i A_ik dC_ij through the cached A_hat (see module notes)."""
+    e = f64_exponents(X, 1) if e is None else e
+    d2 = [(float(dC[i, j]), e[i]) for i in range(X.shape[0])]
+    exps = [from_double(x)[1] + ei for x, ei in d2 if x != 0.0 and ei is not None]
+    if not exps:
+        return 0.0
+    h_j = max(exps)
+    dcol = [_f64_int(x, ei, h_j, par.t) if ei is not None else 0 for x, ei in d2]
+    acol = [_f64_int(float(X[i, k]), 0, e[i], par.t) if e[i] is not None else 0
+            for i in range(X.shape[0])]
+    return _round_double(entry(acol, 0, dcol, h_j, par)["chat"], h_j - 2 * par.t)
+
+
+def exact_dot_double(xs, ys) -> float:
+    """Correctly rounded binary64 value of sum x*y (exact rational sum)."""
+    return float(sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(xs, ys)))

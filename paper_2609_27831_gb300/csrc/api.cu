@@ -1,0 +1,1036 @@
+// Host side of the C ABI: plan construction (internal width t, modulus
+// prefix, CRT tables, work schedule), device upload, TMA descriptors and the
+// stream-ordered execution of the five stages (Sec. 4.1).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "oz2_internal.h"
+
+namespace oz2 {
+
+// ---------------------------------------------------------------------------
+// Small host bignum (little-endian 32-bit digits) for the CRT tables.
+// ---------------------------------------------------------------------------
+using Big = std::vector<uint32_t>;
+
+static void big_trim(Big& a) {
+  while (!a.empty() && a.back() == 0u) a.pop_back();
+}
+static void big_mul_small(Big& a, uint32_t m) {
+  uint64_t carry = 0;
+  for (auto& d : a) {
+    const uint64_t t = (uint64_t)d * m + carry;
+    d = (uint32_t)t;
+    carry = t >> 32;
+  }
+  if (carry) a.push_back((uint32_t)carry);
+}
+static uint32_t big_divmod_small(const Big& a, uint32_t m, Big* q) {
+  uint64_t r = 0;
+  if (q) q->assign(a.size(), 0u);
+  for (size_t i = a.size(); i-- > 0;) {
+    const uint64_t cur = (r << 32) | a[i];
+    if (q) (*q)[i] = (uint32_t)(cur / m);
+    r = cur % m;
+  }
+  if (q) big_trim(*q);
+  return (uint32_t)r;
+}
+static int big_bitlen(const Big& a) {
+  if (a.empty()) return 0;
+  int top = 31;
+  while (!((a.back() >> top) & 1u)) --top;
+  return 32 * (int)(a.size() - 1) + top + 1;
+}
+static int big_cmp(const Big& a, const Big& b) {
+  if (a.size() != b.size()) return a.size() < b.size() ? -1 : 1;
+  for (size_t i = a.size(); i-- > 0;)
+    if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+  return 0;
+}
+// (k << sh) as a bignum
+static Big big_shifted(uint64_t k, int sh) {
+  Big a((size_t)(sh / 32) + 3, 0u);
+  const int w = sh / 32, b = sh % 32;
+  const unsigned __int128 v = (unsigned __int128)k << b;
+  a[w] = (uint32_t)v;
+  a[w + 1] = (uint32_t)(v >> 32);
+  a[w + 2] = (uint32_t)(v >> 64);
+  big_trim(a);
+  return a;
+}
+// 2^(32 D) - x, as exactly D digits (x < 2^(32 D), x != 0)
+static Big big_neg_mod(const Big& x, int D) {
+  Big r((size_t)D, 0u);
+  uint64_t carry = 1;
+  for (int i = 0; i < D; ++i) {
+    const uint64_t t = (uint64_t)(uint32_t)~(i < (int)x.size() ? x[i] : 0u) + carry;
+    r[i] = (uint32_t)t;
+    carry = t >> 32;
+  }
+  return r;
+}
+
+static uint32_t inv_mod(uint32_t a, uint32_t m) {
+  // extended Euclid; a and m coprime
+  int64_t t = 0, nt = 1, r = m, nr = a % m;
+  while (nr) {
+    const int64_t q = r / nr;
+    std::tie(t, nt) = std::make_tuple(nt, t - q * nt);
+    std::tie(r, nr) = std::make_tuple(nr, r - q * nr);
+  }
+  if (t < 0) t += m;
+  return (uint32_t)t;
+}
+
+// ---------------------------------------------------------------------------
+// The modulus list (Sec. 4.3): for every prime q <= 255 the largest power
+// q^k <= 255, in descending order; then the primes in (255, 16191], in
+// descending order.
+// ---------------------------------------------------------------------------
+static const std::vector<uint32_t>& modulus_list() {
+  static std::vector<uint32_t> list;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int lim = 16191;
+    std::vector<char> comp(lim + 1, 0);
+    for (int i = 2; i * i <= lim; ++i)
+      if (!comp[i])
+        for (int j = i * i; j <= lim; j += i) comp[j] = 1;
+    std::vector<uint32_t> one;
+    for (int q = 2; q <= 255; ++q) {
+      if (comp[q]) continue;
+      int m = q;
+      while (m * q <= 255) m *= q;
+      one.push_back((uint32_t)m);
+    }
+    std::sort(one.rbegin(), one.rend());
+    list = one;
+    for (int m = lim; m > 255; --m)
+      if (!comp[m]) list.push_back((uint32_t)m);
+  });
+  return list;
+}
+static int one_limb_count() {
+  static int n = [] {
+    int c = 0;
+    for (uint32_t m : modulus_list()) c += m <= 255;
+    return c;
+  }();
+  return n;
+}
+
+static int ceil_log2(int64_t k) {
+  int c = 0;
+  while (((int64_t)1 << c) < k) ++c;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct CrtHost {
+  int L, D32, DS, cls;
+  Big P;
+  std::vector<uint32_t> words;   // pool layout (see CrtView), DS-padded
+};
+
+struct ProbHost {
+  int64_t M, N, K;
+  int p, nl, t, L, L1, G, W16, D32, Kp, res_cls, crt_cls, DS;
+  int tiles_m, tiles_n, nchunks, kchunk;
+  int crt_key;                 // index into crt tables
+  size_t off_e, off_f, off_pa, off_pb, off_u;   // workspace offsets
+  int kind;                    // 0: limb output; 1: binary64 output
+  bool skip_a, skip_b;         // planes of that side are written by the caller
+};
+
+struct ListRef {
+  const int32_t* ptr = nullptr;
+  int n = 0;
+  int smem = 0;      // dynamic shared memory of the launch
+  int lmax = 0;      // largest modulus count among its problems
+};
+
+struct PlainSeg {
+  int cta_off, grid;
+};
+
+struct LaunchBlock {
+  void* d_mem = nullptr;       // ProbDev[count], then CUtensorMap[2 count] (64-byte aligned)
+  void* h_stage = nullptr;     // pinned staging buffer
+  size_t bytes = 0, tmap_off = 0;
+  cudaEvent_t copied = nullptr;
+  bool pending = false;
+  std::vector<uint8_t> last;
+};
+
+struct DevState {
+  int device = -1, sms = 0;
+  void* mem = nullptr;
+  DevTables tab{};
+  const Unit* unsorted = nullptr;
+  ListRef scan_rows, scan_cols, simt;
+  ListRef res[6], crt[7];
+  const int32_t* cta_grouped = nullptr;
+  int grid = 0;
+  const int32_t* cta_plain = nullptr;
+  std::vector<PlainSeg> plain;
+  std::vector<int> crt_off;    // per problem, uint32 offset in the pool
+};
+
+static void free_launch_block(LaunchBlock& lb) {
+  if (lb.copied) cudaEventSynchronize(lb.copied), cudaEventDestroy(lb.copied);
+  if (lb.d_mem) cudaFree(lb.d_mem);
+  if (lb.h_stage) cudaFreeHost(lb.h_stage);
+  lb = LaunchBlock();
+}
+
+}  // namespace oz2
+
+struct ozaki2_plan_s {
+  ozaki2_opts opts{};
+  std::vector<oz2::ProbHost> probs;
+  std::vector<oz2::CrtHost> crts;
+  int lmax = 0, w16max = 0;
+  size_t ws_bytes = 0, ef_bytes = 0;
+  int64_t total_units = 0, total_jobs = 0;
+  oz2::DevState dev;
+  oz2::LaunchBlock lb;
+  std::vector<uint32_t*> dbg_chat;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool timed = false;
+};
+
+struct ozaki2_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  oz2::LaunchBlock lb;
+};
+
+namespace oz2 {
+
+cudaError_t init_prep_attributes();
+cudaError_t init_gemm_attributes();
+cudaError_t init_crt_attributes();
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int p,
+                         const PlanExtra* ex = nullptr) {
+  const ozaki2_opts& o = pl->opts;
+  const PlanExtra none{};
+  if (!ex) ex = &none;
+  if (M <= 0 || N <= 0 || K <= 0 || p < 2) return OZ2_EINVAL;
+  if (K > kMaxK || p > kMaxP) return OZ2_ERANGE;
+  if (M > 65535LL * kBM || N > 65535LL * kBN) return OZ2_ERANGE;
+  ProbHost h{};
+  h.M = M; h.N = N; h.K = K; h.p = p;
+  h.nl = (p + 63) / 64;
+  const int64_t inner = std::max<int64_t>(K, ex->inner);
+  h.t = ex->force_t > 0 ? ex->force_t
+                        : (o.t_bits > 0 ? o.t_bits : p + o.guard_bits + ceil_log2(inner));   // Eq. 3
+  if (h.t > kMaxP + 64) return OZ2_ERANGE;
+  // shortest modulus prefix with P > inner 2^(2t + 2)   (Eq. crtcond, +2 margin)
+  const Big bound = big_shifted((uint64_t)inner, 2 * h.t + 2);
+  const auto& ml = modulus_list();
+  Big P{1u};
+  int L = 0;
+  while (ex->force_L > 0 ? L < ex->force_L : big_cmp(P, bound) <= 0) {
+    if (L >= (int)ml.size()) return OZ2_ERANGE;
+    big_mul_small(P, ml[L]);
+    ++L;
+  }
+  if (big_cmp(P, bound) <= 0) return OZ2_ERANGE;
+  h.kind = ex->kind;
+  h.skip_a = ex->skip_a;
+  h.skip_b = ex->skip_b;
+  h.L = L;
+  h.L1 = std::min(L, one_limb_count());
+  h.G = h.L1 + 3 * (L - h.L1);
+  h.W16 = (h.t + 1 + 15) / 16;
+  h.res_cls = residue_class_for(h.W16);
+  if (h.res_cls < 0) return OZ2_ERANGE;
+  h.D32 = (big_bitlen(P) + 31) / 32 + 2;   // headroom: S < L P (Sec. 5.4)
+  h.crt_cls = crt_class_for(h.D32);
+  if (h.crt_cls < 0) return OZ2_ERANGE;
+  h.DS = crt_class_digits(h.crt_cls);
+  h.Kp = (int)align_up((size_t)K, 8);
+  h.tiles_m = (int)((M + kBM - 1) / kBM);
+  h.tiles_n = (int)((N + kBN - 1) / kBN);
+  const int kc = o.k_chunk > 0 ? o.k_chunk : kMaxKChunk;
+  if (kc % kBK != 0 || kc > kMaxKChunk) return OZ2_EINVAL;
+  h.kchunk = kc;
+  h.nchunks = (int)((K + kc - 1) / kc);
+  // CRT tables, shared by problems with the same modulus count
+  int key = -1;
+  for (size_t i = 0; i < pl->crts.size(); ++i)
+    if (pl->crts[i].L == L) key = (int)i;
+  if (key < 0) {
+    CrtHost c;
+    c.L = L; c.D32 = h.D32; c.DS = h.DS; c.cls = h.crt_cls; c.P = P;
+    const int DS = c.DS, D = c.D32;
+    c.words.assign((size_t)3 * DS + L + (size_t)L * DS, 0u);
+    for (int i = 0; i < (int)P.size(); ++i) c.words[i] = P[i];
+    const Big negP = big_neg_mod(P, D);
+    for (int i = 0; i < D; ++i) c.words[DS + i] = negP[i];
+    Big H1;
+    big_divmod_small(P, 2, &H1);               // floor(P / 2) ...
+    uint64_t carry = 1;                        // ... + 1
+    for (auto& dg : H1) {
+      const uint64_t t = (uint64_t)dg + carry;
+      dg = (uint32_t)t;
+      carry = t >> 32;
+      if (!carry) break;
+    }
+    if (carry) H1.push_back(1u);
+    const Big negH1 = big_neg_mod(H1, D);
+    for (int i = 0; i < D; ++i) c.words[2 * DS + i] = negH1[i];
+    for (int l = 0; l < L; ++l) {
+      Big Ml;
+      const uint32_t m = ml[l];
+      big_divmod_small(P, m, &Ml);                       // M_l = P / m_l
+      const uint32_t r = big_divmod_small(Ml, m, nullptr);
+      c.words[3 * DS + l] = inv_mod(r, m);               // M_l^{-1} mod m_l
+      for (int i = 0; i < (int)Ml.size(); ++i) c.words[3 * DS + L + (size_t)l * DS + i] = Ml[i];
+    }
+    pl->crts.push_back(std::move(c));
+    key = (int)pl->crts.size() - 1;
+  }
+  h.crt_key = key;
+  pl->probs.push_back(h);
+  pl->lmax = std::max(pl->lmax, L);
+  pl->w16max = std::max(pl->w16max, residue_class_w16(h.res_cls));
+  pl->total_units += (int64_t)L * h.tiles_m * h.tiles_n;
+  pl->total_jobs += (int64_t)h.G * h.tiles_m * h.tiles_n * h.nchunks;
+  return OZ2_OK;
+}
+
+static void layout_workspace(ozaki2_plan_s* pl) {
+  size_t off = 0;
+  for (auto& h : pl->probs) { h.off_e = off; off += align_up(4 * (size_t)h.M, 256); }
+  for (auto& h : pl->probs) { h.off_f = off; off += align_up(4 * (size_t)h.N, 256); }
+  pl->ef_bytes = off;
+  for (auto& h : pl->probs) {
+    h.off_pa = off; off += align_up(2 * (size_t)h.G * h.M * h.Kp, 256);
+    h.off_pb = off; off += align_up(2 * (size_t)h.G * h.N * h.Kp, 256);
+    h.off_u = off; off += align_up(2 * (size_t)h.L * h.M * h.N, 256);
+  }
+  pl->ws_bytes = off;
+}
+
+static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
+  auto* pl = new (std::nothrow) ozaki2_plan_s();
+  if (!pl) return OZ2_ENOMEM;
+  if (opts) pl->opts = *opts;
+  else ozaki2_opts_default(&pl->opts);
+  const ozaki2_opts& o = pl->opts;
+  if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
+      (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
+      (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN)) {
+    delete pl;
+    return OZ2_EINVAL;
+  }
+  *res = pl;
+  return OZ2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device side of a plan
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct Builder {
+  std::vector<uint8_t> img;
+  size_t add(const void* p, size_t n, size_t align = 256) {
+    const size_t off = align_up(img.size(), align);
+    img.resize(off + std::max<size_t>(n, 1));
+    if (p && n) std::memcpy(img.data() + off, p, n);
+    return off;
+  }
+};
+
+static int upload(ozaki2_plan_s* pl) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OZ2_ENODEV;
+  DevState& d = pl->dev;
+  if (d.mem) return d.device == dev ? OZ2_OK : OZ2_EINVAL;
+  int major = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return OZ2_ENODEV;
+  if (major != 10) return OZ2_ENODEV;
+  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
+      init_crt_attributes() != cudaSuccess)
+    return OZ2_ECUDA;
+  if (!get_encode()) return OZ2_ECUDA;
+  cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  const int count = (int)pl->probs.size();
+  const auto& ml = modulus_list();
+
+  // modulus constants and the 2^(16 d) mod m tables (Sec. 5.3)
+  std::vector<ModConst> mods(pl->lmax);
+  for (int l = 0; l < pl->lmax; ++l) {
+    const uint32_t m = ml[l];
+    ModConst& c = mods[l];
+    c.m = m;
+    c.mu = (uint32_t)((1ull << 32) / m);
+    c.c24 = (uint32_t)((1ull << 24) % m);
+    c.rcp = (float)(1.0 / (double)m);
+    if (m > 255) {
+      // sum r^a r^b = -127 P0 + 128 Ps + 16256 P2 (Eq. 4); the epilogue keeps
+      // the running value scaled by the inverse of the next plane's coefficient
+      const uint32_t c0 = (m - 127u) % m, cs = 128u % m, c2 = 16256u % m;
+      c.kmul01 = (uint32_t)((uint64_t)c0 * inv_mod(cs, m) % m);
+      c.kmul12 = (uint32_t)((uint64_t)cs * inv_mod(c2, m) % m);
+      c.kfin = c2;
+    } else {
+      c.kmul01 = c.kmul12 = c.kfin = 1u;
+    }
+  }
+  std::vector<uint32_t> t16((size_t)pl->lmax * pl->w16max);
+  for (int l = 0; l < pl->lmax; ++l) {
+    uint64_t v = 1 % ml[l];
+    for (int dd = 0; dd < pl->w16max; ++dd) {
+      t16[(size_t)l * pl->w16max + dd] = (uint32_t)v;
+      v = (v << 16) % ml[l];
+    }
+  }
+  std::vector<uint32_t> pool;
+  std::vector<int> key_off(pl->crts.size());
+  for (size_t i = 0; i < pl->crts.size(); ++i) {
+    key_off[i] = (int)pool.size();
+    pool.insert(pool.end(), pl->crts[i].words.begin(), pl->crts[i].words.end());
+    pool.resize(align_up(pool.size(), 64), 0u);
+  }
+  d.crt_off.resize(count);
+  for (int i = 0; i < count; ++i) d.crt_off[i] = key_off[pl->probs[i].crt_key];
+
+  // units in (problem, modulus, tile row, tile col) order; persistent CTA c
+  // takes units c, c + grid, ... so that the CTAs running at one time share
+  // the planes of a few moduli in L2
+  std::vector<Unit> units;
+  std::vector<std::pair<int, int>> seg;   // (first unit, count) per (problem, modulus)
+  for (int pi = 0; pi < count; ++pi) {
+    const ProbHost& h = pl->probs[pi];
+    for (int l = 0; l < h.L; ++l) {
+      seg.emplace_back((int)units.size(), h.tiles_m * h.tiles_n);
+      for (int tm = 0; tm < h.tiles_m; ++tm)
+        for (int tn = 0; tn < h.tiles_n; ++tn)
+          units.push_back(Unit{(uint16_t)pi, (uint16_t)l, (uint16_t)tm, (uint16_t)tn});
+    }
+  }
+  const int nunits = (int)units.size();
+  const int grid = std::max(1, std::min(pl->opts.grid > 0 ? pl->opts.grid : d.sms, nunits));
+  std::vector<Unit> ordered;
+  ordered.reserve(2 * units.size());
+  std::vector<int32_t> cta_g(grid + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    cta_g[c] = (int)ordered.size();
+    for (int u = c; u < nunits; u += grid) ordered.push_back(units[u]);
+  }
+  cta_g[grid] = (int)ordered.size();
+  // plain schedule: one launch per (problem, modulus), appended after the
+  // grouped order; each launch has its own [grid + 1] range array
+  std::vector<int32_t> cta_p;
+  d.plain.clear();
+  for (auto& sg : seg) {
+    const int first = sg.first, cnt = sg.second;
+    const int g = std::max(1, std::min(cnt, d.sms));
+    d.plain.push_back(PlainSeg{(int)cta_p.size(), g});
+    for (int c = 0; c < g; ++c) {
+      cta_p.push_back((int)ordered.size());
+      for (int u = c; u < cnt; u += g) ordered.push_back(units[first + u]);
+    }
+    cta_p.push_back((int)ordered.size());
+  }
+
+  // block lists
+  std::vector<int4> scan_rows, scan_cols, simt;
+  std::vector<std::vector<int4>> res(6), crt(7);
+  int res_l[6] = {0}, crt_l[7] = {0};
+  for (int pi = 0; pi < count; ++pi) {
+    const ProbHost& h = pl->probs[pi];
+    if (!h.skip_a)
+      for (int64_t r = 0; r < h.M; r += 8) scan_rows.push_back(make_int4(pi, 0, (int)r, 1));
+    const int kparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 256));
+    if (!h.skip_b)
+      for (int64_t c = 0; c < h.N; c += 32)
+        for (int kp = 0; kp < kparts; ++kp) scan_cols.push_back(make_int4(pi, 1 | (kp << 8), (int)c, kparts));
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 ? h.skip_a : h.skip_b) continue;
+      const int64_t R = side ? h.N : h.M;
+      for (int64_t r = 0; r < R; r += 8)
+        for (int64_t k = 0; k < h.K; k += 32) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
+    }
+    res_l[h.res_cls] = std::max(res_l[h.res_cls], h.L);
+    const int epb = crt_class_elems_per_block(h.crt_cls);
+    const int64_t nb = (h.M * h.N + epb - 1) / epb;
+    if (nb > INT_MAX) return OZ2_ERANGE;
+    for (int64_t bb = 0; bb < nb; ++bb) crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
+    crt_l[h.crt_cls] = std::max(crt_l[h.crt_cls], h.L);
+  }
+  for (int u = 0; u < nunits; ++u) {
+    const ProbHost& h = pl->probs[units[u].prob];
+    const int64_t r0 = (int64_t)units[u].tm * kBM, c0 = (int64_t)units[u].tn * kBN;
+    for (int sy = 0; sy < kBM / 32; ++sy)
+      for (int sx = 0; sx < kBN / 32; ++sx)
+        if (r0 + 32 * sy < h.M && c0 + 32 * sx < h.N) simt.push_back(make_int4(u, sy, sx, 0));
+  }
+
+  Builder b;
+  const size_t o_mods = b.add(mods.data(), mods.size() * sizeof(ModConst));
+  const size_t o_t16 = b.add(t16.data(), t16.size() * 4);
+  const size_t o_pool = b.add(pool.data(), pool.size() * 4);
+  const size_t o_units = b.add(units.data(), units.size() * sizeof(Unit));
+  const size_t o_ordered = b.add(ordered.data(), ordered.size() * sizeof(Unit));
+  const size_t o_ctag = b.add(cta_g.data(), cta_g.size() * 4);
+  const size_t o_ctap = b.add(cta_p.data(), cta_p.size() * 4);
+  const size_t o_srows = b.add(scan_rows.data(), scan_rows.size() * 16);
+  const size_t o_scols = b.add(scan_cols.data(), scan_cols.size() * 16);
+  const size_t o_simt = b.add(simt.data(), simt.size() * 16);
+  size_t o_res[6], o_crt[7];
+  for (int i = 0; i < 6; ++i) o_res[i] = b.add(res[i].data(), res[i].size() * 16);
+  for (int i = 0; i < 7; ++i) o_crt[i] = b.add(crt[i].data(), crt[i].size() * 16);
+  const size_t o_status = b.add(nullptr, 256);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, b.img.size()) != cudaSuccess) return OZ2_ENOMEM;
+  if (cudaMemcpy(mem, b.img.data(), b.img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(mem);
+    return OZ2_ECUDA;
+  }
+  d.mem = mem;
+  d.device = dev;
+  auto* base = static_cast<uint8_t*>(mem);
+  d.tab = DevTables{};
+  d.tab.mods = reinterpret_cast<const ModConst*>(base + o_mods);
+  d.tab.t16 = reinterpret_cast<const uint32_t*>(base + o_t16);
+  d.tab.w16max = pl->w16max;
+  d.tab.lmax = pl->lmax;
+  d.tab.crt_pool = reinterpret_cast<const uint32_t*>(base + o_pool);
+  d.tab.units = reinterpret_cast<const Unit*>(base + o_ordered);
+  d.tab.cta_begin = reinterpret_cast<const int32_t*>(base + o_ctag);
+  d.tab.status = reinterpret_cast<int32_t*>(base + o_status);
+  d.tab.count = count;
+  d.unsorted = reinterpret_cast<const Unit*>(base + o_units);
+  d.grid = grid;
+  d.cta_grouped = reinterpret_cast<const int32_t*>(base + o_ctag);
+  d.cta_plain = reinterpret_cast<const int32_t*>(base + o_ctap);
+  d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + o_srows), (int)scan_rows.size(), 0, 0};
+  d.scan_cols = ListRef{reinterpret_cast<const int32_t*>(base + o_scols), (int)scan_cols.size(), 0, 0};
+  d.simt = ListRef{reinterpret_cast<const int32_t*>(base + o_simt), (int)simt.size(), 0, 0};
+  for (int i = 0; i < 6; ++i)
+    d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + o_res[i]), (int)res[i].size(),
+                       res_l[i] * residue_class_w16(i) * 4, res_l[i]};
+  for (int i = 0; i < 7; ++i)
+    d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + o_crt[i]), (int)crt[i].size(), 0, crt_l[i]};
+  if (pl->opts.timing) {
+    for (auto& e : pl->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return OZ2_ECUDA;
+  }
+  return OZ2_OK;
+}
+
+static int alloc_launch_block(LaunchBlock& lb, int count) {
+  const size_t probs_bytes = align_up(sizeof(ProbDev) * count, 128);
+  lb.tmap_off = probs_bytes;
+  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 2 * count;
+  if (cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) { lb.d_mem = nullptr; return OZ2_ENOMEM; }
+  if (cudaMallocHost(&lb.h_stage, lb.bytes) != cudaSuccess) { lb.h_stage = nullptr; return OZ2_ENOMEM; }
+  if (cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming) != cudaSuccess) return OZ2_ECUDA;
+  return OZ2_OK;
+}
+
+static bool mat_ok(const ozaki2_mat& m, int64_t rows, int64_t cols) {
+  return m.limbs && m.exp && m.sign && m.ld >= cols && m.plane_stride >= rows * m.ld;
+}
+
+static int encode_planes(CUtensorMap* map, void* base, int64_t K, int64_t rows, int64_t Kp, int G,
+                         int box_rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)G};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2)};
+  const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  const CUresult r = get_encode()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? OZ2_OK : OZ2_ECUDA;
+}
+
+// Fill the launch image (ProbDev + tensor maps) for the given problems.
+static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* ws,
+                       std::vector<uint8_t>& img, size_t tmap_off, size_t bytes) {
+  const int count = (int)pl->probs.size();
+  img.assign(bytes, 0);
+  auto* pd = reinterpret_cast<ProbDev*>(img.data());
+  auto* tm = reinterpret_cast<CUtensorMap*>(img.data() + tmap_off);
+  for (int i = 0; i < count; ++i) {
+    const ProbHost& h = pl->probs[i];
+    const ozaki2_problem& q = probs[i];
+    if (q.M != h.M || q.N != h.N || q.K != h.K || q.p != h.p) return OZ2_EINVAL;
+    if ((!h.skip_a && !mat_ok(q.A, h.M, h.K)) || (!h.skip_b && !mat_ok(q.B, h.K, h.N))) return OZ2_EINVAL;
+    if (h.kind == 0 && !mat_ok(q.C, h.M, h.N)) return OZ2_EINVAL;
+    if (h.kind == 1 && (!q.C.limbs || q.C.ld < h.N)) return OZ2_EINVAL;
+    ProbDev& P = pd[i];
+    P.a_limbs = q.A.limbs; P.a_exp = q.A.exp; P.a_sign = q.A.sign; P.a_ld = q.A.ld; P.a_ps = q.A.plane_stride;
+    P.b_limbs = q.B.limbs; P.b_exp = q.B.exp; P.b_sign = q.B.sign; P.b_ld = q.B.ld; P.b_ps = q.B.plane_stride;
+    P.c_limbs = q.C.limbs; P.c_exp = q.C.exp; P.c_sign = q.C.sign; P.c_ld = q.C.ld; P.c_ps = q.C.plane_stride;
+    P.e = reinterpret_cast<int32_t*>(ws + h.off_e);
+    P.f = reinterpret_cast<int32_t*>(ws + h.off_f);
+    P.pa = reinterpret_cast<uint16_t*>(ws + h.off_pa);
+    P.pb = reinterpret_cast<uint16_t*>(ws + h.off_pb);
+    P.u = reinterpret_cast<uint16_t*>(ws + h.off_u);
+    P.M = (int32_t)h.M; P.N = (int32_t)h.N; P.K = (int32_t)h.K; P.p = h.p; P.nl = h.nl; P.t = h.t;
+    P.L = h.L; P.L1 = h.L1; P.G = h.G; P.Kp = h.Kp; P.W16 = h.W16; P.D32 = h.D32;
+    P.crt_off = pl->dev.crt_off[i];
+    P.tiles_m = h.tiles_m; P.tiles_n = h.tiles_n; P.nchunks = h.nchunks; P.kchunk = h.kchunk;
+    P.kind = h.kind;
+    if (h.kind == 1) {
+      // binary64 output: C.limbs carries the double pointer, C.ld its row stride
+      P.c_f64 = reinterpret_cast<double*>(q.C.limbs);
+      P.c_f64_ld = q.C.ld;
+      P.c_limbs = nullptr; P.c_exp = nullptr; P.c_sign = nullptr;
+    }
+    P.DS = h.DS;
+    P.dbg_chat = pl->dbg_chat.empty() ? nullptr : pl->dbg_chat[i];
+    int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
+    if (rc) return rc;
+    rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);
+    if (rc) return rc;
+  }
+  return OZ2_OK;
+}
+
+static int stage_image(LaunchBlock& lb, const std::vector<uint8_t>& img, cudaStream_t s) {
+  if (img == lb.last) return OZ2_OK;
+  if (lb.pending && cudaEventSynchronize(lb.copied) != cudaSuccess) return OZ2_ECUDA;
+  std::memcpy(lb.h_stage, img.data(), img.size());
+  if (cudaMemcpyAsync(lb.d_mem, lb.h_stage, img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return OZ2_ECUDA;
+  if (cudaEventRecord(lb.copied, s) != cudaSuccess) return OZ2_ECUDA;
+  lb.pending = true;
+  lb.last = img;
+  return OZ2_OK;
+}
+
+#define OZ2_CU(x)                                  \
+  do {                                             \
+    if ((x) != cudaSuccess) return OZ2_ECUDA;      \
+  } while (0)
+
+// Enqueue the five stages on `s` using launch block `lb` (already staged).
+static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t s, bool timing) {
+  DevState& d = pl->dev;
+  DevTables tab = d.tab;
+  tab.probs = reinterpret_cast<const ProbDev*>(lb.d_mem);
+  tab.tmaps = reinterpret_cast<const CUtensorMap*>(static_cast<uint8_t*>(lb.d_mem) + lb.tmap_off);
+  const int count = (int)pl->probs.size();
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[0], s));
+  OZ2_CU(cudaMemsetAsync(ws, 0x80, pl->ef_bytes, s));   // exponent sentinel below every valid exponent
+  for (const ProbHost& h : pl->probs) {
+    // a side whose planes the caller supplies is used unscaled: exponent 0
+    if (h.skip_a) OZ2_CU(cudaMemsetAsync(ws + h.off_e, 0, 4 * (size_t)h.M, s));
+    if (h.skip_b) OZ2_CU(cudaMemsetAsync(ws + h.off_f, 0, 4 * (size_t)h.N, s));
+  }
+  OZ2_CU(launch_scan(tab, count, d.scan_rows.ptr, d.scan_cols.ptr, d.scan_rows.n, d.scan_cols.n, s));
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[1], s));
+  for (int c = 0; c < 6; ++c)
+    if (d.res[c].n) OZ2_CU(launch_residues(tab, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
+  if (pl->opts.engine == OZ2_ENGINE_SIMT) {
+    DevTables t2 = tab;
+    t2.units = d.unsorted;
+    OZ2_CU(launch_gemm_simt(t2, d.simt.ptr, d.simt.n, s));
+  } else if (pl->opts.schedule == OZ2_SCHED_GROUPED) {
+    OZ2_CU(launch_gemm_tc(tab, d.grid, s));
+  } else {
+    for (const PlainSeg& sg : d.plain) {
+      DevTables t2 = tab;
+      t2.cta_begin = d.cta_plain + sg.cta_off;
+      OZ2_CU(launch_gemm_tc(t2, sg.grid, s));
+    }
+  }
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
+  for (int c = 0; c < 7; ++c)
+    if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[4], s));
+  return OZ2_OK;
+}
+
+static int execute_impl(ozaki2_plan_s* pl, int count, const ozaki2_problem* probs, void* ws,
+                        size_t ws_bytes, cudaStream_t s) {
+  if (!pl || !probs || !ws) return OZ2_EINVAL;
+  if (count != (int)pl->probs.size()) return OZ2_EINVAL;
+  if (ws_bytes < pl->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZ2_EINVAL;
+  int rc = upload(pl);
+  if (rc) return rc;
+  if (!pl->lb.d_mem && (rc = alloc_launch_block(pl->lb, count))) return rc;
+  std::vector<uint8_t> img;
+  rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, pl->lb.tmap_off, pl->lb.bytes);
+  if (rc) return rc;
+  rc = stage_image(pl->lb, img, s);
+  if (rc) return rc;
+  pl->timed = pl->opts.timing != 0;
+  return enqueue(pl, pl->lb, static_cast<uint8_t*>(ws), s, pl->timed);
+}
+
+int plan_create_ex(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts,
+                   const PlanExtra& ex, ozaki2_plan* out) {
+  if (!out) return OZ2_EINVAL;
+  *out = nullptr;
+  ozaki2_plan_s* pl = nullptr;
+  int rc = new_plan(opts, &pl);
+  if (rc) return rc;
+  try {
+    rc = build_problem(pl, M, N, K, p, &ex);
+  } catch (const std::bad_alloc&) {
+    rc = OZ2_ENOMEM;
+  }
+  if (rc) { delete pl; return rc; }
+  layout_workspace(pl);
+  *out = pl;
+  return OZ2_OK;
+}
+
+int plan_query(ozaki2_plan pl, PlanFacts* f) {
+  if (!pl || !f) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[0];
+  f->t = h.t; f->L = h.L; f->G = h.G; f->Kp = h.Kp;
+  f->off_e = h.off_e; f->off_f = h.off_f; f->off_pa = h.off_pa; f->off_pb = h.off_pb;
+  f->ws_bytes = pl->ws_bytes;
+  return OZ2_OK;
+}
+
+int plan_run(ozaki2_plan pl, const ozaki2_problem* q, void* ws, size_t ws_bytes, cudaStream_t s) {
+  return execute_impl(pl, 1, q, ws, ws_bytes, s);
+}
+
+}  // namespace oz2
+
+using namespace oz2;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int ozaki2_opts_default(ozaki2_opts* o) {
+  if (!o) return OZ2_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->guard_bits = 16;
+  o->t_bits = 0;
+  o->engine = OZ2_ENGINE_TC;
+  o->k_chunk = 0;
+  o->grid = 0;
+  o->schedule = OZ2_SCHED_GROUPED;
+  o->timing = 0;
+  return OZ2_OK;
+}
+
+const char* ozaki2_strerror(int st) {
+  switch (st) {
+    case OZ2_OK: return "success";
+    case OZ2_EINVAL: return "invalid argument";
+    case OZ2_ERANGE: return "size or precision outside the supported range";
+    case OZ2_ENOMEM: return "out of memory";
+    case OZ2_ECUDA: return "CUDA call failed";
+    case OZ2_EINTERNAL: return "device-side consistency check failed";
+    case OZ2_ETIMEOUT: return "device-side wait timed out";
+    case OZ2_ENODEV: return "no usable sm_103 device";
+  }
+  return "unknown status";
+}
+
+const char* ozaki2_version(void) { return "ozaki2-gb300 0.1"; }
+
+int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts,
+                       ozaki2_plan* out) {
+  if (!out) return OZ2_EINVAL;
+  *out = nullptr;
+  ozaki2_plan_s* pl = nullptr;
+  int rc = new_plan(opts, &pl);
+  if (rc) return rc;
+  try {
+    rc = build_problem(pl, M, N, K, p);
+  } catch (const std::bad_alloc&) {
+    rc = OZ2_ENOMEM;
+  }
+  if (rc) { delete pl; return rc; }
+  layout_workspace(pl);
+  *out = pl;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_create_batched(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
+                               ozaki2_plan* out) {
+  if (!out || !shapes || count <= 0 || count > 65535) return OZ2_EINVAL;
+  *out = nullptr;
+  ozaki2_plan_s* pl = nullptr;
+  int rc = new_plan(opts, &pl);
+  if (rc) return rc;
+  try {
+    for (int i = 0; i < count && !rc; ++i) rc = build_problem(pl, shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].p);
+  } catch (const std::bad_alloc&) {
+    rc = OZ2_ENOMEM;
+  }
+  if (rc) { delete pl; return rc; }
+  layout_workspace(pl);
+  *out = pl;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_destroy(ozaki2_plan pl) {
+  if (!pl) return OZ2_EINVAL;
+  free_launch_block(pl->lb);
+  if (pl->dev.mem) cudaFree(pl->dev.mem);
+  for (auto& e : pl->ev)
+    if (e) cudaEventDestroy(e);
+  delete pl;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_info(ozaki2_plan pl, ozaki2_info* out) {
+  if (!pl || !out) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[0];
+  out->count = (int)pl->probs.size();
+  out->t = h.t;
+  out->L = h.L;
+  out->L1 = h.L1;
+  out->G = h.G;
+  out->crt_digits = h.D32;
+  out->units = (int)std::min<int64_t>(INT_MAX, pl->total_units);
+  out->jobs = (int)std::min<int64_t>(INT_MAX, pl->total_jobs);
+  out->workspace_bytes = pl->ws_bytes;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_moduli(ozaki2_plan pl, int prob, int32_t* out, int cap) {
+  if (!pl || !out || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[prob];
+  if (cap < h.L) return OZ2_EINVAL;
+  for (int l = 0; l < h.L; ++l) out[l] = (int32_t)modulus_list()[l];
+  return OZ2_OK;
+}
+
+int ozaki2_plan_crt_tables(ozaki2_plan pl, int prob, uint32_t* P_digits, uint32_t* M_digits,
+                           uint32_t* Minv) {
+  if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[prob];
+  const CrtHost& c = pl->crts[h.crt_key];
+  const int D = c.D32, DS = c.DS, L = c.L;
+  if (P_digits)
+    for (int i = 0; i < D; ++i) P_digits[i] = c.words[i];
+  if (M_digits)
+    for (int l = 0; l < L; ++l)
+      for (int i = 0; i < D; ++i) M_digits[(size_t)l * D + i] = c.words[3 * DS + L + (size_t)l * DS + i];
+  if (Minv)
+    for (int l = 0; l < L; ++l) Minv[l] = c.words[3 * DS + l];
+  return OZ2_OK;
+}
+
+int ozaki2_plan_layout(ozaki2_plan pl, int prob, size_t off[5], int64_t* kp) {
+  if (!pl || !off || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[prob];
+  off[0] = h.off_e;
+  off[1] = h.off_f;
+  off[2] = h.off_pa;
+  off[3] = h.off_pb;
+  off[4] = h.off_u;
+  if (kp) *kp = h.Kp;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_set_debug_chat(ozaki2_plan pl, int prob, uint32_t* dev_buf) {
+  if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
+  if (pl->dbg_chat.empty()) pl->dbg_chat.assign(pl->probs.size(), nullptr);
+  pl->dbg_chat[prob] = dev_buf;
+  return OZ2_OK;
+}
+
+int ozaki2_execute(ozaki2_plan pl, const ozaki2_mat* A, const ozaki2_mat* B, ozaki2_mat* C, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!pl || !A || !B || !C || pl->probs.size() != 1) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[0];
+  ozaki2_problem q{h.M, h.N, h.K, h.p, *A, *B, *C};
+  try {
+    return execute_impl(pl, 1, &q, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
+int ozaki2_execute_batched(ozaki2_plan pl, int count, const ozaki2_problem* probs, void* ws,
+                           size_t ws_bytes, void* stream) {
+  try {
+    return execute_impl(pl, count, probs, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
+int ozaki2_graph_create(ozaki2_plan pl, int count, const ozaki2_problem* probs, void* ws,
+                        size_t ws_bytes, void* stream, ozaki2_graph* out) {
+  if (!pl || !probs || !ws || !out || !stream) return OZ2_EINVAL;
+  if (count != (int)pl->probs.size() || ws_bytes < pl->ws_bytes) return OZ2_EINVAL;
+  *out = nullptr;
+  int rc = upload(pl);
+  if (rc) return rc;
+  auto* g = new (std::nothrow) ozaki2_graph_s();
+  if (!g) return OZ2_ENOMEM;
+  rc = alloc_launch_block(g->lb, count);
+  std::vector<uint8_t> img;
+  if (!rc) rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, g->lb.tmap_off, g->lb.bytes);
+  if (!rc && cudaMemcpy(g->lb.d_mem, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = OZ2_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!rc && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = OZ2_ECUDA;
+  if (!rc) {
+    const int erc = enqueue(pl, g->lb, static_cast<uint8_t*>(ws), s, false);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g->graph);
+    rc = erc ? erc : (ce != cudaSuccess ? OZ2_ECUDA : OZ2_OK);
+  }
+  if (!rc && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = OZ2_ECUDA;
+  if (rc) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    free_launch_block(g->lb);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return OZ2_OK;
+}
+
+int ozaki2_graph_launch(ozaki2_graph g, void* stream) {
+  if (!g) return OZ2_EINVAL;
+  return cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? OZ2_OK : OZ2_ECUDA;
+}
+
+int ozaki2_graph_destroy(ozaki2_graph g) {
+  if (!g) return OZ2_EINVAL;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  free_launch_block(g->lb);
+  delete g;
+  return OZ2_OK;
+}
+
+int ozaki2_check(ozaki2_plan pl, void* stream) {
+  if (!pl) return OZ2_EINVAL;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return OZ2_ECUDA;
+  if (!pl->dev.mem) return OZ2_OK;
+  int32_t st = 0;
+  if (cudaMemcpy(&st, pl->dev.tab.status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OZ2_ECUDA;
+  if (st) {
+    const int32_t zero = 0;
+    if (cudaMemcpy(pl->dev.tab.status, &zero, 4, cudaMemcpyHostToDevice) != cudaSuccess) return OZ2_ECUDA;
+  }
+  if (st & kStatusTimeout) return OZ2_ETIMEOUT;
+  if (st) return OZ2_EINTERNAL;
+  return OZ2_OK;
+}
+
+int ozaki2_last_timings(ozaki2_plan pl, float ms[5]) {
+  if (!pl || !ms || !pl->timed || !pl->ev[0]) return OZ2_EINVAL;
+  if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return OZ2_ECUDA;
+  if (cudaEventElapsedTime(&ms[4], pl->ev[0], pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
+  return OZ2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Convenience calls with library-owned plans and workspaces
+// ---------------------------------------------------------------------------
+namespace {
+struct Cached {
+  ozaki2_plan plan = nullptr;
+  void* ws = nullptr;
+};
+std::mutex g_cache_mu;
+std::map<std::vector<int64_t>, Cached> g_cache;
+
+std::vector<int64_t> cache_key(int count, const ozaki2_problem* probs, const ozaki2_opts& o) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  std::vector<int64_t> k{dev, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule, o.timing, count};
+  for (int i = 0; i < count; ++i) {
+    k.push_back(probs[i].M);
+    k.push_back(probs[i].N);
+    k.push_back(probs[i].K);
+    k.push_back(probs[i].p);
+  }
+  return k;
+}
+
+int cached_run(int count, const ozaki2_problem* probs, const ozaki2_opts* opts, void* stream) {
+  ozaki2_opts o;
+  if (opts) o = *opts;
+  else ozaki2_opts_default(&o);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  const auto key = cache_key(count, probs, o);
+  auto it = g_cache.find(key);
+  if (it == g_cache.end()) {
+    Cached c;
+    int rc = count == 1 ? ozaki2_plan_create(probs[0].M, probs[0].N, probs[0].K, probs[0].p, &o, &c.plan)
+                        : ozaki2_plan_create_batched(count, probs, &o, &c.plan);
+    if (rc) return rc;
+    if (cudaMalloc(&c.ws, c.plan->ws_bytes) != cudaSuccess) {
+      ozaki2_plan_destroy(c.plan);
+      return OZ2_ENOMEM;
+    }
+    it = g_cache.emplace(key, c).first;
+  }
+  return ozaki2_execute_batched(it->second.plan, count, probs, it->second.ws, it->second.plan->ws_bytes, stream);
+}
+}  // namespace
+
+int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
+                ozaki2_mat* C, const ozaki2_opts* opts, void* stream) {
+  if (!A || !B || !C) return OZ2_EINVAL;
+  ozaki2_problem q{M, N, K, p, *A, *B, *C};
+  try {
+    return cached_run(1, &q, opts, stream);
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
+int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts, void* stream) {
+  if (!probs || count <= 0) return OZ2_EINVAL;
+  try {
+    return cached_run(count, probs, opts, stream);
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
+int ozaki2_release_cache(void) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto& kv : g_cache) {
+    cudaFree(kv.second.ws);
+    ozaki2_plan_destroy(kv.second.plan);
+  }
+  g_cache.clear();
+  return OZ2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,507 @@
+// Stages 3-4 of the Ozaki-II flow (Sec. 4.1): one exact integer GEMM per
+// residue plane and the reduction of each product mod m_l, with the
+// Karatsuba combine of the three two-limb planes (Eq. 4-5) fused into the
+// epilogue.
+//
+// Engine: tcgen05.mma kind::f16 with bf16 operands.  Every plane entry is an
+// integer with |r| <= 127, exact in bf16; products are exact in fp32 and the
+// fp32 accumulator in TMEM stays exact while every partial sum is an integer
+// below 2^24.  K is therefore processed in chunks of at most 1024
+// (127^2 * 1024 + 16191 < 2^24).  Between chunks (and between the three
+// Karatsuba planes of a two-limb modulus) the epilogue warps read the
+// accumulator, reduce it mod m and write the small residue back into TMEM, so
+// the next chunk accumulates on top of it: no running state lives in registers
+// and no partial product ever leaves the SM.
+//
+// Persistent grouped kernel: one CTA per SM walks its list of (problem,
+// modulus, 128x256 output tile) units; two TMEM accumulator slots of 256
+// columns alternate between two unit streams so that the MMA of one job
+// overlaps the epilogue of the other.
+//
+// Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer (+ TMEM owner),
+// warps 2..9 = epilogue (two per TMEM lane quadrant, 128 columns each).
+#include <climits>
+
+#include "oz2_internal.h"
+
+namespace oz2 {
+
+namespace {
+
+constexpr int kTileABytes = kBM * kBK * 2;            // 16 KB
+constexpr int kTileBBytes = kBN * kBK * 2;            // 32 KB
+constexpr int kStageBytes = kTileABytes + kTileBBytes;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + kEpiWarps * 32;         // 320
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait.  On timeout the CTA-wide abort flag and the device status word
+// are set and false is returned; every other waiter then leaves its loop.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                          int32_t* status) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (it > 1024) __nanosleep(32);
+  }
+  *abort_flag = 1;
+  atomicOr(status, kStatusTimeout);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile written by TMA with
+// 128-byte swizzle (rows of 64 bf16, 8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = f32, A = B = bf16, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+      "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+      "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t m, uint32_t mu) {
+  uint32_t q = __umulhi(x, mu);
+  uint32_t r = x - q * m;
+  return r >= m ? r - m : r;
+}
+
+// x: exact integer held in fp32 with |x| < 2^25.  Returns x mod m in [0, m).
+// q = rint(x * rcp) is within 0.52 of x/m, so r = x - q m lies in
+// (-0.52 m, 0.52 m) and is computed exactly by the fma; one correction
+// brings it into [0, m).
+__device__ __forceinline__ uint32_t fmod_small(float x, float mf, float rcp) {
+  const float q = rintf(x * rcp);
+  float r = fmaf(-q, mf, x);
+  r = r < 0.f ? r + mf : r;
+  return static_cast<uint32_t>(r);
+}
+
+// One accumulation job: plane `plane` of unit `u` over K chunk `chunk`.
+struct Job {
+  Unit u;
+  int slot;
+  int plane;
+  int chunk;
+  bool first;       // first job of the unit: the MMA overwrites the slot
+  bool last;        // last job of the unit: the epilogue writes u_l
+  uint32_t kmul;    // write-back multiplier (not last)
+};
+
+// Deterministic job order shared by the producer, MMA and epilogue roles:
+// units s, s+2, s+4, ... of the CTA's list go to TMEM slot s, and the jobs of
+// the two slot streams alternate.
+struct JobIter {
+  const DevTables* T;
+  int ubeg, n;
+  int uidx[2], job[2], turn;
+
+  __device__ void init(const DevTables* t, int b, int e) {
+    T = t; ubeg = b; n = e - b;
+    uidx[0] = 0; uidx[1] = 1; job[0] = job[1] = 0; turn = 0;
+  }
+  __device__ bool next(Job& j) {
+    int s = turn;
+    if (uidx[s] >= n) {
+      s ^= 1;
+      if (uidx[s] >= n) return false;
+    }
+    const Unit u = T->units[ubeg + uidx[s]];
+    const ProbDev& P = T->probs[u.prob];
+    const bool two = u.ell >= P.L1;
+    const int nch = P.nchunks;
+    const int njobs = (two ? 3 : 1) * nch;
+    const int jj = job[s];
+    const int pi = jj / nch;
+    j.u = u;
+    j.slot = s;
+    j.chunk = jj - pi * nch;
+    if (two) {
+      const int g0 = P.L1 + 3 * (u.ell - P.L1);
+      j.plane = g0 + (pi == 0 ? 0 : (pi == 1 ? 2 : 1));   // P0, Ps, P2
+    } else {
+      j.plane = u.ell;
+    }
+    j.first = jj == 0;
+    j.last = jj == njobs - 1;
+    j.kmul = 1u;
+    if (!j.last && j.chunk == nch - 1) {
+      const ModConst& mc = T->mods[u.ell];
+      j.kmul = pi == 0 ? mc.kmul01 : mc.kmul12;
+    }
+    if (++job[s] == njobs) {
+      job[s] = 0;
+      uidx[s] += 2;
+    }
+    turn = s ^ 1;
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ DevTables T) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* full = bars;                 // [kStages]
+  uint64_t* empty = bars + kStages;      // [kStages]
+  uint64_t* slot_full = bars + 2 * kStages;   // [2]
+  uint64_t* slot_free = bars + 2 * kStages + 2;   // [2]
+  uint64_t* drain = bars + 2 * kStages + 4;       // [1] abort drain of the MMA pipe
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 2 * kStages + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cta = blockIdx.x;
+  const int ubeg = T.cta_begin[cta], uend = T.cta_begin[cta + 1];
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(slot_full + s, 1);
+      mbar_init(slot_free + s, kEpiWarps * 32);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    JobIter it;
+    it.init(&T, ubeg, uend);
+    Job j;
+    int st = 0;
+    uint32_t ph = 0;
+    int issued_phase[kStages];
+    for (int i = 0; i < kStages; ++i) issued_phase[i] = -1;
+    bool ok = true;
+    while (ok && it.next(j)) {
+      const ProbDev& P = T.probs[j.u.prob];
+      const CUtensorMap* ma = T.tmaps + 2 * j.u.prob;
+      const CUtensorMap* mb = ma + 1;
+      const int k0 = j.chunk * P.kchunk;
+      const int k1 = min(P.K, k0 + P.kchunk);
+      for (int k = k0; k < k1; k += kBK) {
+        if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
+        mbar_expect_tx(full + st, kStageBytes);
+        const uint32_t sa = base + st * kStageBytes;
+        tma_load_3d(sa, ma, smem_u32(full + st), k, j.u.tm * kBM, j.plane);
+        tma_load_3d(sa + kTileABytes, mb, smem_u32(full + st), k, j.u.tn * kBN, j.plane);
+        issued_phase[st] = (int)ph;
+        if (++st == kStages) { st = 0; ph ^= 1u; }
+      }
+    }
+    if (!ok) {
+      // let copies already in flight land before the CTA exits
+      for (int i = 0; i < kStages; ++i) {
+        if (issued_phase[i] >= 0) {
+          for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(full + i, (uint32_t)issued_phase[i]); ++t) {}
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    JobIter it;
+    it.init(&T, ubeg, uend);
+    Job j;
+    int st = 0;
+    uint32_t ph = 0;
+    int uses[2] = {0, 0};
+    bool ok = true;
+    bool any = false;
+    while (ok && it.next(j)) {
+      const ProbDev& P = T.probs[j.u.prob];
+      const int s = j.slot;
+      if (uses[s] > 0) {
+        if (!mbar_wait(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status)) { ok = false; break; }
+      }
+      ++uses[s];
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(s * kBN);
+      const int k0 = j.chunk * P.kchunk;
+      const int k1 = min(P.K, k0 + P.kchunk);
+      bool acc = !j.first;
+      for (int k = k0; k < k1; k += kBK) {
+        if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sa = base + st * kStageBytes;
+        const uint64_t da = desc_sw128(sa);
+        const uint64_t db = desc_sw128(sa + kTileABytes);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+          umma(d, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), acc ? 1u : 0u);
+          acc = true;
+        }
+        umma_commit(empty + st);
+        any = true;
+        if (++st == kStages) { st = 0; ph ^= 1u; }
+      }
+      if (!ok) break;
+      umma_commit(slot_full + s);
+    }
+    if (!ok && any) {
+      // drain issued MMAs before TMEM is released
+      umma_commit(drain);
+      for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(drain, 0); ++t) {}
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;
+    const int quad = warp & 3;          // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;           // column half of the 256-column slot
+    JobIter it;
+    it.init(&T, ubeg, uend);
+    Job j;
+    int uses[2] = {0, 0};
+    while (it.next(j)) {
+      const int s = j.slot;
+      if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status)) break;
+      ++uses[s];
+      tc_fence_after();
+      const ProbDev& P = T.probs[j.u.prob];
+      const ModConst mc = T.mods[j.u.ell];
+      const float mf = (float)mc.m;
+      const int row = j.u.tm * kBM + quad * 32 + lane;
+      const uint32_t tbase =
+          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kBN + half * 128);
+      uint16_t* urow = P.u + (int64_t)j.u.ell * P.M * P.N + (int64_t)row * P.N;
+      const int col_base = j.u.tn * kBN + half * 128;
+      const bool vec_ok = (P.N & 7) == 0;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        uint32_t v[32];
+        tmem_ld32(tbase + (uint32_t)(c * 32), v);
+        if (!j.last) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
+            if (j.kmul != 1u) r = barrett32(r * j.kmul, mc.m, mc.mu);
+            v[i] = __float_as_uint((float)r);
+          }
+          tmem_st32(tbase + (uint32_t)(c * 32), v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
+            if (mc.kfin != 1u) r = barrett32(r * mc.kfin, mc.m, mc.mu);
+            v[i] = r;
+          }
+          const int col0 = col_base + c * 32;
+          if (row < P.M) {
+            if (vec_ok && col0 + 32 <= P.N) {
+              uint4* dst = reinterpret_cast<uint4*>(urow + col0);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                uint4 w;
+                w.x = v[8 * q + 0] | (v[8 * q + 1] << 16);
+                w.y = v[8 * q + 2] | (v[8 * q + 3] << 16);
+                w.z = v[8 * q + 4] | (v[8 * q + 5] << 16);
+                w.w = v[8 * q + 6] | (v[8 * q + 7] << 16);
+                dst[q] = w;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (col0 + i < P.N) urow[col0 + i] = (uint16_t)v[i];
+            }
+          }
+        }
+      }
+      if (!j.last) tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(slot_free + s);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core cross-check engine: the same unit list, exact int32 dot products
+// of the bf16 planes, Karatsuba combine in int64.  Slow; used to test the
+// tensor-core engine.  Block = one unit's 32 x 32 sub-tile.
+// Entry: {unit index, sub-tile row, sub-tile col, 0}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bf2i(uint16_t h) {
+  return (int)__uint_as_float(((uint32_t)h) << 16);
+}
+
+__global__ void __launch_bounds__(256) k_gemm_simt(DevTables T, const int4* __restrict__ list) {
+  __shared__ int sa[3][32][33];
+  __shared__ int sb[3][32][33];
+  const int4 e = list[blockIdx.x];
+  const Unit u = T.units[e.x];
+  const ProbDev& P = T.probs[u.prob];
+  const bool two = u.ell >= P.L1;
+  const int np = two ? 3 : 1;
+  const int g0 = two ? P.L1 + 3 * (u.ell - P.L1) : u.ell;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const int row0 = u.tm * kBM + e.y * 32, col0 = u.tn * kBN + e.z * 32;
+  int acc[3][4];
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 4; ++q) acc[p][q] = 0;
+  const int64_t psA = (int64_t)P.M * P.Kp, psB = (int64_t)P.N * P.Kp;
+  for (int k0 = 0; k0 < P.K; k0 += 32) {
+    for (int p = 0; p < np; ++p) {
+      for (int q = 0; q < 4; ++q) {
+        const int rr = ty + 8 * q;
+        const int k = k0 + tx;
+        const int ra = row0 + rr, cb = col0 + rr;
+        sa[p][rr][tx] = (ra < P.M && k < P.K) ? bf2i(P.pa[(g0 + p) * psA + (int64_t)ra * P.Kp + k]) : 0;
+        sb[p][rr][tx] = (cb < P.N && k < P.K) ? bf2i(P.pb[(g0 + p) * psB + (int64_t)cb * P.Kp + k]) : 0;
+      }
+    }
+    __syncthreads();
+    for (int p = 0; p < np; ++p)
+      for (int q = 0; q < 4; ++q) {
+        const int rr = ty + 8 * q;
+        int s = 0;
+        for (int kk = 0; kk < 32; ++kk) s += sa[p][rr][kk] * sb[p][tx][kk];
+        acc[p][q] += s;
+      }
+    __syncthreads();
+  }
+  const int64_t m = T.mods[u.ell].m;
+  for (int q = 0; q < 4; ++q) {
+    const int row = row0 + ty + 8 * q, col = col0 + tx;
+    if (row >= P.M || col >= P.N) continue;
+    int64_t v;
+    if (!two) {
+      v = acc[0][q];
+    } else {
+      const int64_t P0 = acc[0][q], P2 = acc[1][q], Ps = acc[2][q];
+      v = P0 + 128 * (Ps - P0 - P2) + 16384 * P2;
+    }
+    v %= m;
+    if (v < 0) v += m;
+    P.u[(int64_t)u.ell * P.M * P.N + (int64_t)row * P.N + col] = (uint16_t)v;
+  }
+}
+
+}  // namespace
+
+cudaError_t init_gemm_attributes() {
+  return cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+cudaError_t launch_gemm_tc(const DevTables& t, int grid, cudaStream_t s) {
+  k_gemm_tc<<<grid, kThreads, kSmemBytes, s>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_simt(const DevTables& t, const int32_t* unit_list, int nunits,
+                             cudaStream_t s) {
+  if (nunits == 0) return cudaSuccess;
+  k_gemm_simt<<<nunits, 256, 0, s>>>(t, reinterpret_cast<const int4*>(unit_list));
+  return cudaGetLastError();
+}
+
+}  // namespace oz2

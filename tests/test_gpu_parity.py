@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer stages (shared exponents, residue planes, reduced products u_l, CRT
+integers) must match bit for bit; final p-bit results must equal the oracle's
+stage-by-stage result bit for bit and lie within 1 ulp of the correctly
+rounded exact product (0 ulp where the exponent spread is within t - p).
+"""
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ozaki2_oracle as o
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def ozk():
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as pkg
+    return pkg
+
+
+def run_gpu(ozk, A, B, p, debug=True, **kw):
+    """Execute one product; return output and every intermediate."""
+    M, K = A["exp"].shape
+    N = B["exp"].shape[1]
+    plan = ozk.Plan((M, N, K, p), **kw)
+    ws = plan.workspace()
+    dA, dB = ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B)
+    dC = ozk.MPMatrix.empty(M, N, p)
+    D = plan.info["crt_digits"]
+    chat = torch.zeros((M * N, D + 1), dtype=torch.int32, device="cuda") if debug else None
+    if debug:
+        plan.set_debug_chat(0, chat)
+    plan.execute(dA, dB, dC, ws)
+    plan.check()
+    torch.cuda.synchronize()
+    off, kp = plan.layout()
+    G, L = plan.info["G"], plan.info["L"]
+    w = ws.cpu().numpy()
+
+    def region(o_, dtype, n):
+        return w[o_: o_ + n * np.dtype(dtype).itemsize].view(dtype)
+
+    out = {
+        "plan": plan, "C": dC.to_host(),
+        "e": region(off[0], np.int32, M), "f": region(off[1], np.int32, N),
+        "pa": region(off[2], np.uint16, G * M * kp).reshape(G, M, kp)[:, :, :K],
+        "pb": region(off[3], np.uint16, G * N * kp).reshape(G, N, kp)[:, :, :K],
+        "u": region(off[4], np.uint16, L * M * N).reshape(L, M, N),
+    }
+    if debug:
+        ch = chat.cpu().numpy().view(np.uint32)
+        vals = []
+        for r in ch:
+            mag = 0
+            for d in range(D):
+                mag |= int(r[1 + d]) << (32 * d)
+            vals.append(-mag if r[0] else mag)
+        out["chat"] = np.array(vals, dtype=object).reshape(M, N)
+    return out
+
+
+def bf16_to_int(a):
+    return (a.astype(np.uint32) << 16).view(np.float32).astype(np.int64)
+
+
+def assert_full_parity(ozk, A, B, p, truth=True, **kw):
+    got = run_gpu(ozk, A, B, p, **kw)
+    ref = o.ozaki2_full(A, B, p)
+    M, N = got["u"].shape[1:]
+    e_ok = np.where(ref["e"] == 0, True, got["e"] == ref["e"])  # all-zero lines keep the sentinel
+    assert e_ok.all()
+    assert np.array_equal(bf16_to_int(got["pa"]), ref["planes_a"])
+    assert np.array_equal(bf16_to_int(got["pb"]), ref["planes_b"])
+    assert np.array_equal(got["u"].astype(np.int64), ref["u"])
+    assert all(got["chat"][i, j] == ref["chat"][i, j] for i in range(M) for j in range(N))
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got["C"][key], ref["C"][key]), key
+    if truth:
+        T = o.truth_full(A, B, p)
+        worst = Fraction(0)
+        for i in range(M):
+            for j in range(N):
+                g = o.to_fraction(*o.matrix_entry(got["C"], i, j))
+                t = o.to_fraction(*o.matrix_entry(T, i, j))
+                worst = max(worst, o.ulp_distance(g, t, p) if t else abs(g))
+        assert worst <= 1
+    return got, ref
+
+
+def test_gemm_256_p53_all_stages(ozk):
+    """The 256^3, p = 53 workload: every stage bit-exact, results 0 ulp."""
+    A, B = synth.gemm_256_p53()
+    got, ref = assert_full_parity(ozk, A, B, 53, truth=False)
+    T = o.truth_full(A, B, 53)   # spread 16 <= t - p: quantisation is exact
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got["C"][key], T[key])
+
+
+def test_ragged_tiles_two_limb_moduli(ozk):
+    """Ragged M, N, K (tile tails in every dimension) and two-limb moduli."""
+    rng = np.random.Generator(np.random.PCG64(2001))
+    A = synth.mp_matrix(rng, 150, 70, 256, -20, 20)
+    B = synth.mp_matrix(rng, 70, 270, 256, -20, 20)
+    assert_full_parity(ozk, A, B, 256)
+
+
+def test_k_chunks_and_karatsuba_write_back(ozk):
+    """k_chunk = 64 forces many exact accumulation chunks per plane, with the
+    reduce-and-write-back step between chunks and between Karatsuba planes."""
+    rng = np.random.Generator(np.random.PCG64(2002))
+    A = synth.mp_matrix(rng, 130, 300, 200, -6, 6)
+    B = synth.mp_matrix(rng, 300, 40, 200, -6, 6)
+    assert_full_parity(ozk, A, B, 200, truth=False, k_chunk=64)
+
+
+def test_engines_and_schedules_agree(ozk):
+    rng = np.random.Generator(np.random.PCG64(2003))
+    A = synth.mp_matrix(rng, 200, 96, 300, -10, 10)
+    B = synth.mp_matrix(rng, 96, 300, 300, -10, 10)
+    base = run_gpu(ozk, A, B, 300, debug=False)
+    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}):
+        other = run_gpu(ozk, A, B, 300, debug=False, **kw)
+        assert np.array_equal(other["u"], base["u"]), kw
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(other["C"][key], base["C"][key]), kw
+
+
+@pytest.mark.parametrize("K", [1024, 1040, 2048, 2100])
+def test_fp32_accumulation_exactness_torture(ozk, K):
+    """All-equal inputs make every plane product K r_a r_b with the largest
+    residues: partial sums approach 2^24 within one chunk (K = 1024) and cross
+    chunk boundaries (K > 1024).  Every u_l must be exact."""
+    p = 53
+    rng = np.random.Generator(np.random.PCG64(2004 + K))
+    one = synth.mp_matrix(rng, 1, 1, p, 0, 0)
+    A = {k: (np.broadcast_to(v, v.shape[:-2] + (64, K)).copy() if isinstance(v, np.ndarray) else v)
+         for k, v in one.items()}
+    one_b = synth.mp_matrix(rng, 1, 1, p, 0, 0)
+    B = {k: (np.broadcast_to(v, v.shape[:-2] + (K, 64)).copy() if isinstance(v, np.ndarray) else v)
+         for k, v in one_b.items()}
+    got = run_gpu(ozk, A, B, p)
+    par = o.Params(K, p)
+    ai, e = o.integer_line(A, 0, 0, par.t)
+    bj, f = o.integer_line(B, 0, 1, par.t)
+    ref = o.entry(ai, e, bj, f, par)
+    # the largest plane sums really are near 2^24
+    big = max(abs(c) for c in ref["prods"][:par.L1]) / max(1, -(-K // 1024))
+    assert big > 2 ** 22
+    assert np.all(got["u"].astype(np.int64) == np.array(ref["u"])[:, None, None])
+    assert all(got["chat"][i, j] == ref["chat"] for i in (0, 63) for j in (0, 63))
+    want = (ref["limbs"], ref["exp"], ref["sign"])
+    assert o.matrix_entry(got["C"], 5, 7) == want
+
+
+def test_zero_lines_and_tiny_shapes(ozk):
+    rng = np.random.Generator(np.random.PCG64(2005))
+    A = synth.zero_rows(synth.mp_matrix(rng, 33, 17, 113, -40, 40), [0, 5])
+    B = synth.zero_cols(synth.mp_matrix(rng, 17, 9, 113, -40, 40), [3])
+    got, _ = assert_full_parity(ozk, A, B, 113)
+    assert not got["C"]["limbs"][:, 0, :].any() and not got["C"]["limbs"][:, :, 3].any()
+    for (M, N, K, p) in [(1, 1, 1, 53), (1, 5, 1, 2), (3, 1, 2, 64), (2, 2, 3, 8)]:
+        A = synth.mp_matrix(rng, M, K, p, -3, 3)
+        B = synth.mp_matrix(rng, K, N, p, -3, 3)
+        assert_full_parity(ozk, A, B, p)
+
+
+def test_cancellation_to_zero(ozk):
+    """x * y + (-x) * y = 0 exactly: the CRT integer is 0 and the output zero."""
+    rng = np.random.Generator(np.random.PCG64(2006))
+    A = synth.mp_matrix(rng, 4, 2, 128, -5, 5)
+    A["limbs"][:, :, 1] = A["limbs"][:, :, 0]
+    A["exp"][:, 1] = A["exp"][:, 0]
+    A["sign"][:, 1] = 1 - A["sign"][:, 0]
+    B = synth.mp_matrix(rng, 2, 3, 128, -5, 5)
+    B["limbs"][:, 1, :] = B["limbs"][:, 0, :]
+    B["exp"][1, :] = B["exp"][0, :]
+    B["sign"][1, :] = B["sign"][0, :]
+    got, _ = assert_full_parity(ozk, A, B, 128)
+    assert not got["C"]["limbs"].any() and not got["C"]["exp"].any()
+
+
+def test_gemm_1024_p256_sampled(ozk):
+    """The 1024^3, p = 256 workload in the launch configuration the benchmark
+    times: sampled outputs against the oracle entry by entry (every stage) and
+    against the exact product (<= 1 ulp)."""
+    A, B = synth.gemm_1024_p256()
+    got = run_gpu(ozk, A, B, 256)
+    rnd = random.Random(7)
+    pairs = [(0, 0), (1023, 1023), (0, 1023), (1023, 0), (511, 257)]
+    pairs += [(rnd.randrange(1024), rnd.randrange(1024)) for _ in range(11)]
+    ref = o.ozaki2_entries(A, B, 256, pairs)
+    worst = Fraction(0)
+    for (i, j), r in zip(pairs, ref):
+        assert [int(x) for x in got["u"][:, i, j]] == r["u"]
+        assert got["chat"][i, j] == r["chat"]
+        assert o.matrix_entry(got["C"], i, j) == (r["limbs"], r["exp"], r["sign"])
+        t = o.to_fraction(*o.truth_entry(A, B, i, j, 256))
+        worst = max(worst, o.ulp_distance(o.to_fraction(r["limbs"], r["exp"], r["sign"]), t, 256))
+    assert worst <= 1
+    # the integer planes of a 256 x 256 corner, in full
+    par = o.Params(1024, 256)
+    for i in (0, 100, 1023):
+        row, _ = o.integer_line(A, i, 0, par.t)
+        assert np.array_equal(bf16_to_int(got["pa"][:, i, :]).T,
+                              np.array([o.plane_values(x, par.moduli) for x in row]))
+
+
+def test_batched_and_graph(ozk):
+    rng = np.random.Generator(np.random.PCG64(2007))
+    shapes = [(70, 300, 90, 113), (129, 40, 200, 256), (33, 260, 17, 512), (5, 5, 5, 53)]
+    mats = []
+    for (M, N, K, p) in shapes:
+        mats.append((synth.mp_matrix(rng, M, K, p, -8, 8), synth.mp_matrix(rng, K, N, p, -8, 8)))
+    plan = ozk.Plan(shapes)
+    ws = plan.workspace()
+    trip = []
+    for (M, N, K, p), (A, B) in zip(shapes, mats):
+        trip.append((ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), ozk.MPMatrix.empty(M, N, p)))
+    plan.execute_batched(trip, ws)
+    plan.check()
+    for (M, N, K, p), (A, B), (_, _, Cd) in zip(shapes, mats, trip):
+        ref = o.ozaki2_full(A, B, p)["C"]
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(Cd.to_host()[key], ref[key])
+    # the same problems through a captured CUDA graph
+    s = torch.cuda.Stream()
+    for _, _, Cd in trip:
+        Cd.limbs.zero_()
+    with torch.cuda.stream(s):
+        g = plan.graph(trip, ws, s)
+        g.launch(s)
+        g.launch(s)
+    s.synchronize()
+    for (M, N, K, p), (A, B), (_, _, Cd) in zip(shapes, mats, trip):
+        ref = o.ozaki2_full(A, B, p)["C"]
+        assert np.array_equal(Cd.to_host()["limbs"], ref["limbs"])
+
+
+def test_convenience_gemm_call(ozk):
+    rng = np.random.Generator(np.random.PCG64(2008))
+    A = synth.mp_matrix(rng, 40, 50, 160, -4, 4)
+    B = synth.mp_matrix(rng, 50, 30, 160, -4, 4)
+    Cd = ozk.gemm(ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), 160)
+    torch.cuda.synchronize()
+    ref = o.ozaki2_full(A, B, 160)["C"]
+    assert np.array_equal(Cd.to_host()["limbs"], ref["limbs"])

@@ -1,0 +1,112 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, and
+its host-side planner (t, modulus prefix, CRT tables) agrees with the oracle.
+No GPU is needed: only host-only entry points are called."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from oracle import ozaki2_oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ozk():
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ozaki2.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"OZ2_API\s+(?:const\s+char\s*\*|int)\s+(ozaki2_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(ozk):
+    names = _declared()
+    assert len(names) >= 20
+    h = C.CDLL(ozk._lib.LIB_PATH)
+    for n in names:
+        assert hasattr(h, n), n
+    # and the binding knows all of them
+    assert set(names) <= set(ozk._lib._SIGS)
+
+
+def test_strerror_and_defaults(ozk):
+    lib = ozk.lib()
+    for st in range(8):
+        assert lib.ozaki2_strerror(st)
+    o_ = ozk.opts()
+    assert o_.guard_bits == 16 and o_.engine == 0 and o_.schedule == 0
+    assert lib.ozaki2_version().startswith(b"ozaki2")
+
+
+@pytest.mark.parametrize("M,N,K,p", [(256, 256, 256, 53), (1024, 1024, 1024, 256), (100, 70, 4096, 1024),
+                                     (64, 64, 4096, 2048), (3, 5, 1, 2), (4096, 4096, 4096, 53)])
+def test_plan_parameters_match_oracle(ozk, M, N, K, p):
+    plan = ozk.Plan((M, N, K, p))
+    par = o.Params(K, p)
+    assert plan.info["t"] == par.t
+    assert plan.info["L"] == par.L
+    assert plan.info["G"] == par.G
+    assert plan.info["L1"] == sum(1 for m in par.moduli if m <= 255)
+    assert plan.moduli() == par.moduli
+    D = plan.info["crt_digits"]
+    assert D == -(-par.tab.P.bit_length() // 32) + 2
+    P, Md, inv = plan.crt_tables()
+    as_int = lambda ds: sum(int(d) << (32 * i) for i, d in enumerate(ds))
+    assert as_int(P) == par.tab.P
+    assert [as_int(r) for r in Md] == par.tab.M
+    assert inv == par.tab.Minv
+    assert plan.workspace_bytes > 0
+    off, kp = plan.layout()
+    assert kp % 8 == 0 and kp >= K and all(x % 256 == 0 for x in off)
+
+
+def test_moduli_table_through_the_library(ozk):
+    """The library's planner reproduces the paper's moduli table (Sec. 4.3)."""
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", "moduli_table.json")) as fh:
+        g = json.load(fh)
+    for row in g["rows"]:
+        plan = ozk.Plan((8, 8, g["K"], row["p"]))
+        assert (plan.info["t"], plan.info["L"], plan.info["G"]) == (row["t"], row["L"], row["gemms"])
+
+
+def test_batched_plan(ozk):
+    shapes = [(100, 200, 300, 113), (64, 64, 64, 512), (2048, 128, 1000, 256)]
+    plan = ozk.Plan(shapes)
+    assert plan.info["count"] == 3
+    for i, (M, N, K, p) in enumerate(shapes):
+        assert plan.moduli(i)[: o.Params(K, p).L] == o.Params(K, p).moduli
+
+
+@pytest.mark.parametrize("args,status", [
+    ((0, 4, 4, 53), 1), ((4, 4, 4, 1), 1), ((4, -1, 4, 53), 1),
+    ((4, 4, 133001, 53), 2), ((4, 4, 4, 4096), 2),
+])
+def test_argument_errors(ozk, args, status):
+    h = C.c_void_p()
+    st = ozk.lib().ozaki2_plan_create(*args, None, C.byref(h))
+    assert st == status and not h.value
+
+
+def test_bad_options(ozk):
+    h = C.c_void_p()
+    for kw in ({"k_chunk": 100}, {"k_chunk": 2048}, {"engine": 7}, {"schedule": 9}):
+        st = ozk.lib().ozaki2_plan_create(64, 64, 64, 53, C.byref(ozk.opts(**kw)), C.byref(h))
+        assert st == 1, kw
+
+
+def test_null_pointer_errors(ozk):
+    lib = ozk.lib()
+    assert lib.ozaki2_plan_create(4, 4, 4, 53, None, None) == 1
+    assert lib.ozaki2_plan_destroy(None) == 1
+    assert lib.ozaki2_execute(None, None, None, None, None, 0, None) == 1
+    assert lib.ozaki2_check(None, None) == 1
+    assert lib.ozaki2_cache_destroy(None) == 1
+    assert lib.ozaki2_dgemm_bwd(None, None, 0, None, 0, None, 0, None) == 1
