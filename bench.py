@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the Ozaki-II multiple-precision GEMM on GB300.
+
+Workload: one M = N = K = 1024 product at p = 256 bits (256 random
+significand bits with the top bit set, random sign, exponents i.i.d. uniform
+in [-32, 32]; seeded synthetic data).  A step is one whole product: exponent
+scan, integerization + residues, the grouped plane GEMM with fused
+mod-reduce, CRT and rounding.  `value` is whole-job 2MNK per second with the
+inputs resident in HBM; `e2e` times the same product through the C ABI with
+host buffers (pinned host -> device copies of A and B and the device -> host
+copy of C inside the timed region).  L2 is flushed (a 512 MiB write) between
+timed steps, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of
+the workload (the path needs no exchange); the time is the max over ranks.
+`--impl reference` times the CPU oracle (the slow, exact stage-by-stage
+restatement of the method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p-bit GEMM 2MNK/s at p=53–2048; INT8 TC util; batched vs plain speedup"
+UNIT = "2MNK/s"
+WORK = {"workload": "gemm_1024_p256", "M": 1024, "N": 1024, "K": 1024, "p": 256,
+        "exp_range": [-32, 32], "seed": 1001}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+CPU_BLOCK = 32          # oracle sample: 32 x 32 output blocks of the workload
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+
+def _oracle_block(args):
+    i0, j0 = args
+    import synth
+    from oracle import ozaki2_oracle as o
+    A, B = synth.gemm_1024_p256(WORK["seed"])
+    rows = slice(i0, i0 + CPU_BLOCK)
+    cols = slice(j0, j0 + CPU_BLOCK)
+    As = {"p": A["p"], "limbs": A["limbs"][:, rows, :].copy(), "exp": A["exp"][rows, :].copy(),
+          "sign": A["sign"][rows, :].copy()}
+    Bs = {"p": B["p"], "limbs": B["limbs"][:, :, cols].copy(), "exp": B["exp"][:, cols].copy(),
+          "sign": B["sign"][:, cols].copy()}
+    t = time.perf_counter()
+    o.ozaki2_full(As, Bs, WORK["p"])
+    return time.perf_counter() - t
+
+
+def cpu_oracle_rate(rounds: int = 2):
+    """Time the CPU oracle (stage-by-stage method, exact integers) on a bounded
+    sample: `cores * rounds` blocks of 32 x 32 outputs (full K) of the
+    workload, one spawn-pool process per host core."""
+    cores = os.cpu_count() or 1
+    nblk = cores * rounds
+    offs = [((b * 97) % (WORK["M"] // CPU_BLOCK) * CPU_BLOCK, (b * 61) % (WORK["N"] // CPU_BLOCK) * CPU_BLOCK)
+            for b in range(nblk)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_block, offs, chunksize=1)
+    wall = time.perf_counter() - t0
+    work = nblk * 2 * CPU_BLOCK * CPU_BLOCK * WORK["K"]
+    sample = (f"oracle ozaki2_full on {nblk} blocks of {CPU_BLOCK}x{CPU_BLOCK} outputs (full K=1024) of "
+              f"the 1024^3 p=256 workload, spawn pool of {cores} processes, wall {wall:.1f} s "
+              f"incl. input regeneration")
+    return work / wall, cores, sample
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as ozk
+
+    world, rank, local = dist_info()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    # the CPU baseline's spawn pool runs before the first CUDA call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(args.cpu_rounds)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    M, N, K, p = WORK["M"], WORK["N"], WORK["K"], WORK["p"]
+    A, B = synth.gemm_1024_p256(WORK["seed"])
+    dA, dB = ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev)
+    dC = ozk.MPMatrix.empty(M, N, p, dev)
+    plan = ozk.Plan((M, N, K, p), timing=1)
+    ws = plan.workspace(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan.execute(dA, dB, dC, ws)
+    plan.check()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = []
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    clk = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-")
+                       else (str(uuid) if uuid is not None else local))
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        starts[s].record(stream)
+        plan.execute(dA, dB, dC, ws)
+        ends[s].record(stream)
+        stage.append(plan.timings())
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    plan.check()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    work = 2.0 * M * N * K
+    value = world * work / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers
+    hA = {k: torch.from_numpy(np.ascontiguousarray(A[k]).view(np.int64) if k == "limbs" else
+                              np.ascontiguousarray(A[k])).pin_memory() for k in ("limbs", "exp", "sign")}
+    hB = {k: torch.from_numpy(np.ascontiguousarray(B[k]).view(np.int64) if k == "limbs" else
+                              np.ascontiguousarray(B[k])).pin_memory() for k in ("limbs", "exp", "sign")}
+    hC = {"limbs": torch.empty(dC.limbs.shape, dtype=torch.int64).pin_memory(),
+          "exp": torch.empty(dC.exp.shape, dtype=torch.int32).pin_memory(),
+          "sign": torch.empty(dC.sign.shape, dtype=torch.int8).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in list(hA.values()) + list(hB.values()))
+    d2h = sum(v.numel() * v.element_size() for v in hC.values())
+    e_st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_((s + 7) & 0xff)
+        e_st[s].record(stream)
+        dA.limbs.copy_(hA["limbs"], non_blocking=True)
+        dA.exp.copy_(hA["exp"], non_blocking=True)
+        dA.sign.copy_(hA["sign"], non_blocking=True)
+        dB.limbs.copy_(hB["limbs"], non_blocking=True)
+        dB.exp.copy_(hB["exp"], non_blocking=True)
+        dB.sign.copy_(hB["sign"], non_blocking=True)
+        plan.execute(dA, dB, dC, ws)
+        hC["limbs"].copy_(dC.limbs, non_blocking=True)
+        hC["exp"].copy_(dC.exp, non_blocking=True)
+        hC["sign"].copy_(dC.sign, non_blocking=True)
+        e_en[s].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e_st, e_en)) / args.steps
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel (library stage events on the launch stream)
+    med = {k: statistics.median(s_[k] for s_ in stage) for k in stage[0]}
+    peaks, peak_src = load_peaks()
+    info = plan.info
+    G, L = info["G"], info["L"]
+    nl = (p + 63) // 64
+    in_bytes = (M * K + K * N) * (8 * nl + 4 + 1)
+    plane_bytes = 2 * G * (M + N) * K
+    stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
+    dom = max(stages, key=stages.get)
+    if dom == "gemm":
+        flops = 2.0 * M * N * K * G
+        ach = flops / (stages["gemm"] / 1e3) / 1e12
+        pk = peaks["bf16_tflops"]
+        roof = {"kernel": "k_gemm_tc (plane GEMMs + fused mod-reduce)", "bound": "tensor",
+                "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
+                "peak_source": f"bf16_tflops burst, {peak_src}"}
+    else:
+        if dom == "residues":
+            alg = in_bytes + plane_bytes
+            kern = "k_residue (integerize + centered residues + plane writes)"
+        elif dom == "crt":
+            alg = 2 * L * M * N + M * N * (8 * nl + 5)
+            kern = "k_crt (direct CRT + rounding)"
+        else:
+            alg = in_bytes
+            kern = "k_scan"
+        ach = alg / (stages[dom] / 1e3) / 1e9
+        pk = peaks["hbm_gbs"]
+        roof = {"kernel": kern, "bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
+                "frac": round(ach / pk, 4), "peak_source": f"hbm_gbs, {peak_src}"}
+    roof["traffic"] = None
+    roof["stage_ms"] = {k: round(v, 4) for k, v in stages.items()}
+    # plane-GEMM rate against the bf16 tensor peak (the engine: see the design notes)
+    gemm_tflops = 2.0 * M * N * K * G / (stages["gemm"] / 1e3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-int (exact integer planes on tcgen05 kind::f16)",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": WORK["workload"], "M": M, "N": N, "K": K, "p": p,
+                   "exp_range": WORK["exp_range"], "t": info["t"], "moduli": L, "gemms": G,
+                   "parallelism": f"replicas{world}", "l2": "flushed (512 MiB write between steps)"},
+        "e2e": {"value": world * work / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "plane_gemm_tflops": round(gemm_tflops, 1),
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        rate, cores, sample = cpu
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        _oracle_block((0, 0))
+    rates = []
+    for _ in range(args.steps):
+        rate, cores, sample = cpu_oracle_rate(1)
+        rates.append(rate)
+    value = statistics.median(rates)
+    ms = 2.0 * WORK["M"] * WORK["N"] * WORK["K"] / value * 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "exact integers (Python)", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORK["workload"], "M": WORK["M"], "N": WORK["N"], "K": WORK["K"],
+                   "p": WORK["p"], "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rounds", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -373,6 +373,7 @@ class Params:
         self.t = internal_width(p, q, g)
         self.moduli = select_moduli(self.t, self.t, q)
         self.L = len(self.moduli)
+        self.L1 = sum(1 for m in self.moduli if m <= ONE_LIMB_MAX)
         self.G = gemm_count(self.moduli)
         self.tab = CrtTables(self.moduli)
 
@@ -591,7 +592,7 @@ def f64_exponents(X: np.ndarray, axis: int) -> np.ndarray:
     """MPFR exponent max over the nonzero entries of each row (axis=1 reduces
     over columns) or column (axis=0); None for an all-zero line."""
     m, e = np.frexp(X)            # X = m 2^e, |m| in [0.5, 1): MPFR exponent e
-    e = np.where(X != 0, e, np.iinfo(np.int64).min)
+    e = np.where(X != 0, e.astype(np.int64), np.iinfo(np.int64).min)
     best = e.max(axis=axis)
     return [None if b == np.iinfo(np.int64).min else int(b) for b in best]
 
