@@ -372,19 +372,24 @@ struct Builder {
   }
 };
 
-static int upload(ozaki2_plan_s* pl) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return OZ2_ENODEV;
+// Offsets of the device tables inside one image (see upload()).
+struct TableImage {
+  Builder b;
+  size_t o_mods = 0, o_t16 = 0, o_pool = 0, o_units = 0, o_ordered = 0, o_ctag = 0, o_ctap = 0,
+         o_srows = 0, o_scols = 0, o_simt = 0, o_status = 0;
+  size_t o_res[6] = {0}, o_crt[7] = {0};
+  int n_srows = 0, n_scols = 0, n_simt = 0, n_res[6] = {0}, n_crt[7] = {0};
+  int res_l[6] = {0}, crt_l[7] = {0};
+  int grid = 0;
+};
+
+// Host side of the device upload: modulus constants, residue digit tables,
+// CRT tables, the unit schedule and the block lists of every stage, as one
+// byte image.  Fills the plan's host-side launch facts (grid, plain
+// segments, CRT offsets).
+static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   DevState& d = pl->dev;
-  if (d.mem) return d.device == dev ? OZ2_OK : OZ2_EINVAL;
-  int major = 0;
-  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return OZ2_ENODEV;
-  if (major != 10) return OZ2_ENODEV;
-  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
-      init_crt_attributes() != cudaSuccess)
-    return OZ2_ECUDA;
-  if (!get_encode()) return OZ2_ECUDA;
-  cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  d.sms = sms;
   const int count = (int)pl->probs.size();
   const auto& ml = modulus_list();
 
@@ -468,7 +473,6 @@ static int upload(ozaki2_plan_s* pl) {
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
   std::vector<std::vector<int4>> res(6), crt(7);
-  int res_l[6] = {0}, crt_l[7] = {0};
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -483,12 +487,12 @@ static int upload(ozaki2_plan_s* pl) {
       for (int64_t r = 0; r < R; r += 8)
         for (int64_t k = 0; k < h.K; k += 32) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
-    res_l[h.res_cls] = std::max(res_l[h.res_cls], h.L);
+    ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
     const int epb = crt_class_elems_per_block(h.crt_cls);
     const int64_t nb = (h.M * h.N + epb - 1) / epb;
     if (nb > INT_MAX) return OZ2_ERANGE;
     for (int64_t bb = 0; bb < nb; ++bb) crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
-    crt_l[h.crt_cls] = std::max(crt_l[h.crt_cls], h.L);
+    ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
   }
   for (int u = 0; u < nunits; ++u) {
     const ProbHost& h = pl->probs[units[u].prob];
@@ -498,52 +502,82 @@ static int upload(ozaki2_plan_s* pl) {
         if (r0 + 32 * sy < h.M && c0 + 32 * sx < h.N) simt.push_back(make_int4(u, sy, sx, 0));
   }
 
-  Builder b;
-  const size_t o_mods = b.add(mods.data(), mods.size() * sizeof(ModConst));
-  const size_t o_t16 = b.add(t16.data(), t16.size() * 4);
-  const size_t o_pool = b.add(pool.data(), pool.size() * 4);
-  const size_t o_units = b.add(units.data(), units.size() * sizeof(Unit));
-  const size_t o_ordered = b.add(ordered.data(), ordered.size() * sizeof(Unit));
-  const size_t o_ctag = b.add(cta_g.data(), cta_g.size() * 4);
-  const size_t o_ctap = b.add(cta_p.data(), cta_p.size() * 4);
-  const size_t o_srows = b.add(scan_rows.data(), scan_rows.size() * 16);
-  const size_t o_scols = b.add(scan_cols.data(), scan_cols.size() * 16);
-  const size_t o_simt = b.add(simt.data(), simt.size() * 16);
-  size_t o_res[6], o_crt[7];
-  for (int i = 0; i < 6; ++i) o_res[i] = b.add(res[i].data(), res[i].size() * 16);
-  for (int i = 0; i < 7; ++i) o_crt[i] = b.add(crt[i].data(), crt[i].size() * 16);
-  const size_t o_status = b.add(nullptr, 256);
+  ti.o_mods = ti.b.add(mods.data(), mods.size() * sizeof(ModConst));
+  ti.o_t16 = ti.b.add(t16.data(), t16.size() * 4);
+  ti.o_pool = ti.b.add(pool.data(), pool.size() * 4);
+  ti.o_units = ti.b.add(units.data(), units.size() * sizeof(Unit));
+  ti.o_ordered = ti.b.add(ordered.data(), ordered.size() * sizeof(Unit));
+  ti.o_ctag = ti.b.add(cta_g.data(), cta_g.size() * 4);
+  ti.o_ctap = ti.b.add(cta_p.data(), cta_p.size() * 4);
+  ti.o_srows = ti.b.add(scan_rows.data(), scan_rows.size() * 16);
+  ti.o_scols = ti.b.add(scan_cols.data(), scan_cols.size() * 16);
+  ti.o_simt = ti.b.add(simt.data(), simt.size() * 16);
+  for (int i = 0; i < 6; ++i) ti.o_res[i] = ti.b.add(res[i].data(), res[i].size() * 16);
+  for (int i = 0; i < 7; ++i) ti.o_crt[i] = ti.b.add(crt[i].data(), crt[i].size() * 16);
+  ti.o_status = ti.b.add(nullptr, 256);
+  ti.n_srows = (int)scan_rows.size();
+  ti.n_scols = (int)scan_cols.size();
+  ti.n_simt = (int)simt.size();
+  for (int i = 0; i < 6; ++i) ti.n_res[i] = (int)res[i].size();
+  for (int i = 0; i < 7; ++i) ti.n_crt[i] = (int)crt[i].size();
+  ti.grid = grid;
+  return OZ2_OK;
+}
+
+// Point the plan's device state at a copy of the image at `base`.
+static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t* base) {
+  DevState& d = pl->dev;
+  const int count = (int)pl->probs.size();
+  d.tab = DevTables{};
+  d.tab.mods = reinterpret_cast<const ModConst*>(base + ti.o_mods);
+  d.tab.t16 = reinterpret_cast<const uint32_t*>(base + ti.o_t16);
+  d.tab.w16max = pl->w16max;
+  d.tab.lmax = pl->lmax;
+  d.tab.crt_pool = reinterpret_cast<const uint32_t*>(base + ti.o_pool);
+  d.tab.units = reinterpret_cast<const Unit*>(base + ti.o_ordered);
+  d.tab.cta_begin = reinterpret_cast<const int32_t*>(base + ti.o_ctag);
+  d.tab.status = reinterpret_cast<int32_t*>(base + ti.o_status);
+  d.tab.count = count;
+  d.unsorted = reinterpret_cast<const Unit*>(base + ti.o_units);
+  d.grid = ti.grid;
+  d.cta_grouped = reinterpret_cast<const int32_t*>(base + ti.o_ctag);
+  d.cta_plain = reinterpret_cast<const int32_t*>(base + ti.o_ctap);
+  d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_srows), ti.n_srows, 0, 0};
+  d.scan_cols = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_scols), ti.n_scols, 0, 0};
+  d.simt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_simt), ti.n_simt, 0, 0};
+  for (int i = 0; i < 6; ++i)
+    d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_res[i]), ti.n_res[i],
+                       ti.res_l[i] * residue_class_w16(i) * 4, ti.res_l[i]};
+  for (int i = 0; i < 7; ++i)
+    d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_crt[i]), ti.n_crt[i], 0, ti.crt_l[i]};
+}
+
+static int upload(ozaki2_plan_s* pl) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OZ2_ENODEV;
+  DevState& d = pl->dev;
+  if (d.mem) return d.device == dev ? OZ2_OK : OZ2_EINVAL;
+  int major = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return OZ2_ENODEV;
+  if (major != 10) return OZ2_ENODEV;
+  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
+      init_crt_attributes() != cudaSuccess)
+    return OZ2_ECUDA;
+  if (!get_encode()) return OZ2_ECUDA;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TableImage ti;
+  int rc = build_table_image(pl, sms, ti);
+  if (rc) return rc;
   void* mem = nullptr;
-  if (cudaMalloc(&mem, b.img.size()) != cudaSuccess) return OZ2_ENOMEM;
-  if (cudaMemcpy(mem, b.img.data(), b.img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMalloc(&mem, ti.b.img.size()) != cudaSuccess) return OZ2_ENOMEM;
+  if (cudaMemcpy(mem, ti.b.img.data(), ti.b.img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(mem);
     return OZ2_ECUDA;
   }
   d.mem = mem;
   d.device = dev;
-  auto* base = static_cast<uint8_t*>(mem);
-  d.tab = DevTables{};
-  d.tab.mods = reinterpret_cast<const ModConst*>(base + o_mods);
-  d.tab.t16 = reinterpret_cast<const uint32_t*>(base + o_t16);
-  d.tab.w16max = pl->w16max;
-  d.tab.lmax = pl->lmax;
-  d.tab.crt_pool = reinterpret_cast<const uint32_t*>(base + o_pool);
-  d.tab.units = reinterpret_cast<const Unit*>(base + o_ordered);
-  d.tab.cta_begin = reinterpret_cast<const int32_t*>(base + o_ctag);
-  d.tab.status = reinterpret_cast<int32_t*>(base + o_status);
-  d.tab.count = count;
-  d.unsorted = reinterpret_cast<const Unit*>(base + o_units);
-  d.grid = grid;
-  d.cta_grouped = reinterpret_cast<const int32_t*>(base + o_ctag);
-  d.cta_plain = reinterpret_cast<const int32_t*>(base + o_ctap);
-  d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + o_srows), (int)scan_rows.size(), 0, 0};
-  d.scan_cols = ListRef{reinterpret_cast<const int32_t*>(base + o_scols), (int)scan_cols.size(), 0, 0};
-  d.simt = ListRef{reinterpret_cast<const int32_t*>(base + o_simt), (int)simt.size(), 0, 0};
-  for (int i = 0; i < 6; ++i)
-    d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + o_res[i]), (int)res[i].size(),
-                       res_l[i] * residue_class_w16(i) * 4, res_l[i]};
-  for (int i = 0; i < 7; ++i)
-    d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + o_crt[i]), (int)crt[i].size(), 0, crt_l[i]};
+  install_table_image(pl, ti, static_cast<uint8_t*>(mem));
   if (pl->opts.timing) {
     for (auto& e : pl->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return OZ2_ECUDA;
@@ -1034,3 +1068,4 @@ int ozaki2_release_cache(void) {
 }
 
 }  // extern "C"
+
