@@ -196,6 +196,26 @@ OZ2_API int ozaki2_graph_destroy(ozaki2_graph g);
 OZ2_API int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
                 ozaki2_mat* C, const ozaki2_opts* opts, void* stream);
 
+/* C = A * B at p bits, like ozaki2_gemm, for callers that cannot allocate
+   device memory (a memory-capped or custom-allocator setting, or a thread
+   that must not call cudaMalloc/cudaFree because they synchronise the
+   device).  The paper has no counterpart: this is a deployment variant.
+   Nothing is allocated on the device: the intermediates (exponents, residue
+   planes, reduced products) live in a fixed 64 MiB array and the tables,
+   schedule, problem descriptor and TMA descriptors in a fixed 4 MiB array,
+   both static device memory of this library that every GPU loading the
+   library holds until the process exits.  Products whose intermediates need
+   more (ozaki2_info.workspace_bytes of the same shape above 64 MiB, e.g.
+   1024^3 at p = 256) are rejected with OZ2_ERANGE before any device work.
+   The first call on a device looks up the arrays' device addresses (once per
+   device, with that device current); make that first call before any stream
+   capture.  Every call shares the arrays and rewrites them: calls that
+   overlap on the GPU (different streams, or concurrent host threads) race,
+   so order them on one stream.  Default options; the device status word of
+   this path is not readable through ozaki2_check. */
+OZ2_API int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A,
+                                const ozaki2_mat* B, ozaki2_mat* C, void* stream);
+
 /* Convenience batched call (library-owned plan and workspace). */
 OZ2_API int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts,
                         void* stream);

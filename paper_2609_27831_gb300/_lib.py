@@ -74,6 +74,8 @@ _SIGS = {
     "ozaki2_gemm": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.POINTER(Mat),
                                C.POINTER(Mat), C.POINTER(Mat), C.POINTER(Opts), C.c_void_p]),
     "ozaki2_gemm_batched": (C.c_int, [C.c_int, C.POINTER(Problem), C.POINTER(Opts), C.c_void_p]),
+    "ozaki2_gemm_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.POINTER(Mat),
+                                       C.POINTER(Mat), C.POINTER(Mat), C.c_void_p]),
     "ozaki2_release_cache": (C.c_int, []),
     "ozaki2_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ozaki2_last_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),

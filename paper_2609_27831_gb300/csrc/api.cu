@@ -1069,3 +1069,117 @@ int ozaki2_release_cache(void) {
 
 }  // extern "C"
 
+// ===========================================================================
+// Entry point that allocates no device memory
+// ===========================================================================
+// Some callers cannot allocate device memory while they run: code that
+// executes inside a memory-capped region, a custom allocator that owns every
+// byte of the GPU, or a host thread that must not call cudaMalloc/cudaFree
+// (they synchronise the device).  ozaki2_gemm_noalloc serves them: every
+// intermediate of the product lives in fixed arrays in the library's own
+// device memory, reserved when the library's device code is loaded on a GPU
+// and held until the process exits.
+static __device__ __align__(256) uint8_t ozaki2_noalloc_scratch[64u << 20];   // exponents, planes, reduced products
+static __device__ __align__(256) uint8_t ozaki2_noalloc_tables[4u << 20];     // tables, schedule, descriptor, tensor maps
+
+namespace {
+
+struct NoAllocDevice {
+  uint8_t* scratch = nullptr;
+  uint8_t* tables = nullptr;
+  int state = 0;   // 0: not set up, 1: ready, 2: set-up failed
+};
+NoAllocDevice g_noalloc_dev[64];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: the device addresses of the two
+// arrays (in host code their names are only host-side stand-ins).
+int noalloc_setup(int dev, NoAllocDevice** out) {
+  if (dev < 0 || dev >= 64) return OZ2_ENODEV;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (d.state == 0) {
+    void* s = nullptr;
+    void* t = nullptr;
+    const cudaError_t e1 = cudaGetSymbolAddress(&s, ozaki2_noalloc_scratch);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaGetSymbolAddress(&t, ozaki2_noalloc_tables) : e1;
+    if (e1 == cudaSuccess && e2 == cudaSuccess && s && t) {
+      d.scratch = static_cast<uint8_t*>(s);
+      d.tables = static_cast<uint8_t*>(t);
+      d.state = 1;
+    } else {
+      d.state = 2;
+    }
+  }
+  *out = &d;
+  return d.state == 1 ? OZ2_OK : OZ2_ECUDA;
+}
+
+int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
+                ozaki2_mat* C, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OZ2_ENODEV;
+  int major = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major != 10)
+    return OZ2_ENODEV;
+  NoAllocDevice* nd = nullptr;
+  int rc = noalloc_setup(dev, &nd);
+  if (rc) return rc;
+  // host-side plan with the default options (no device memory is touched)
+  ozaki2_opts o;
+  ozaki2_opts_default(&o);
+  ozaki2_plan_s* pl = nullptr;
+  rc = new_plan(&o, &pl);
+  if (rc) return rc;
+  struct Release {
+    ozaki2_plan_s* p;
+    ~Release() { delete p; }   // host object only: its device pointers point into the static arrays
+  } release{pl};
+  rc = build_problem(pl, M, N, K, p);
+  if (rc) return rc;
+  layout_workspace(pl);
+  if (pl->ws_bytes > sizeof(ozaki2_noalloc_scratch)) return OZ2_ERANGE;
+  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
+      init_crt_attributes() != cudaSuccess || !get_encode())
+    return OZ2_ECUDA;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TableImage ti;
+  rc = build_table_image(pl, sms, ti);
+  if (rc) return rc;
+  const size_t lb_off = align_up(ti.b.img.size(), 256);
+  const size_t probs_bytes = align_up(sizeof(ProbDev), 128);
+  const size_t lb_bytes = probs_bytes + 2 * sizeof(CUtensorMap);
+  if (lb_off + lb_bytes > sizeof(ozaki2_noalloc_tables)) return OZ2_ERANGE;
+  install_table_image(pl, ti, nd->tables);
+  const ozaki2_problem q{M, N, K, p, *A, *B, *C};
+  std::vector<uint8_t> lbimg;
+  rc = build_image(pl, &q, nd->scratch, lbimg, probs_bytes, lb_bytes);
+  if (rc) return rc;
+  // one image: tables (status word zeroed) + problem descriptor + tensor maps;
+  // copied from pageable host memory, stream-ordered behind earlier calls
+  std::vector<uint8_t>& img = ti.b.img;
+  img.resize(lb_off + lb_bytes, 0);
+  std::memcpy(img.data() + lb_off, lbimg.data(), lb_bytes);
+  if (cudaMemcpyAsync(nd->tables, img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OZ2_ECUDA;
+  LaunchBlock lb;                       // not allocated: points into the static table array
+  lb.d_mem = nd->tables + lb_off;
+  lb.tmap_off = probs_bytes;
+  lb.bytes = lb_bytes;
+  rc = enqueue(pl, lb, nd->scratch, s, false);
+  lb.d_mem = nullptr;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A,
+                                   const ozaki2_mat* B, ozaki2_mat* C, void* stream) {
+  if (!A || !B || !C) return OZ2_EINVAL;
+  try {
+    return noalloc_run(M, N, K, p, A, B, C, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
