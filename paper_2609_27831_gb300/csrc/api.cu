@@ -181,7 +181,7 @@ struct DevState {
   DevTables tab{};
   const Unit* unsorted = nullptr;
   ListRef scan_rows, scan_cols, simt;
-  ListRef res[6], crt[7];
+  ListRef res[6], crt[kCrtClassCount];
   const int32_t* cta_grouped = nullptr;
   int grid = 0;
   const int32_t* cta_plain = nullptr;
@@ -377,9 +377,9 @@ struct TableImage {
   Builder b;
   size_t o_mods = 0, o_t16 = 0, o_pool = 0, o_units = 0, o_ordered = 0, o_ctag = 0, o_ctap = 0,
          o_srows = 0, o_scols = 0, o_simt = 0, o_status = 0;
-  size_t o_res[6] = {0}, o_crt[7] = {0};
-  int n_srows = 0, n_scols = 0, n_simt = 0, n_res[6] = {0}, n_crt[7] = {0};
-  int res_l[6] = {0}, crt_l[7] = {0};
+  size_t o_res[6] = {0}, o_crt[kCrtClassCount] = {0};
+  int n_srows = 0, n_scols = 0, n_simt = 0, n_res[6] = {0}, n_crt[kCrtClassCount] = {0};
+  int res_l[6] = {0}, crt_l[kCrtClassCount] = {0};
   int grid = 0;
 };
 
@@ -472,7 +472,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
 
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
-  std::vector<std::vector<int4>> res(6), crt(7);
+  std::vector<std::vector<int4>> res(6), crt(kCrtClassCount);
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -485,7 +485,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       for (int64_t r = 0; r < R; r += 8)
-        for (int64_t k = 0; k < h.K; k += 32) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
+        for (int64_t k = 0; k < h.K; k += 64) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
     ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
     const int epb = crt_class_elems_per_block(h.crt_cls);
@@ -513,13 +513,13 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.o_scols = ti.b.add(scan_cols.data(), scan_cols.size() * 16);
   ti.o_simt = ti.b.add(simt.data(), simt.size() * 16);
   for (int i = 0; i < 6; ++i) ti.o_res[i] = ti.b.add(res[i].data(), res[i].size() * 16);
-  for (int i = 0; i < 7; ++i) ti.o_crt[i] = ti.b.add(crt[i].data(), crt[i].size() * 16);
+  for (int i = 0; i < kCrtClassCount; ++i) ti.o_crt[i] = ti.b.add(crt[i].data(), crt[i].size() * 16);
   ti.o_status = ti.b.add(nullptr, 256);
   ti.n_srows = (int)scan_rows.size();
   ti.n_scols = (int)scan_cols.size();
   ti.n_simt = (int)simt.size();
   for (int i = 0; i < 6; ++i) ti.n_res[i] = (int)res[i].size();
-  for (int i = 0; i < 7; ++i) ti.n_crt[i] = (int)crt[i].size();
+  for (int i = 0; i < kCrtClassCount; ++i) ti.n_crt[i] = (int)crt[i].size();
   ti.grid = grid;
   return OZ2_OK;
 }
@@ -547,8 +547,8 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   d.simt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_simt), ti.n_simt, 0, 0};
   for (int i = 0; i < 6; ++i)
     d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_res[i]), ti.n_res[i],
-                       ti.res_l[i] * residue_class_w16(i) * 4, ti.res_l[i]};
-  for (int i = 0; i < 7; ++i)
+                       ti.res_l[i] * (residue_class_w16(i) + 4) * 4, ti.res_l[i]};
+  for (int i = 0; i < kCrtClassCount; ++i)
     d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_crt[i]), ti.n_crt[i], 0, ti.crt_l[i]};
 }
 
@@ -704,7 +704,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     }
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
-  for (int c = 0; c < 7; ++c)
+  for (int c = 0; c < kCrtClassCount; ++c)
     if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[4], s));
   return OZ2_OK;

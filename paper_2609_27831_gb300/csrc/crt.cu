@@ -276,9 +276,243 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// One lane per output element (CRT accumulators of up to 40 digits).  The
+// warps of a block cooperate on the staging: the reduced products of 128
+// consecutive outputs are read coalesced and turned into v_l, and the digit
+// table M_l and the quotient constants are staged in shared memory, where
+// every lane of a warp reads the same word (broadcast).  Each lane then runs
+// the whole CRT and rounding of its output with the digits in registers and
+// sequential exact carries.
+// ---------------------------------------------------------------------------
+constexpr int kEpb1 = 128;
+
+template <int ND>
+__global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restrict__ blk) {
+  extern __shared__ __align__(16) uint32_t s1[];
+  const int4 b = blk[blockIdx.x];
+  const ProbDev& P = T.probs[b.x];
+  const int64_t MN = (int64_t)P.M * P.N;
+  const int64_t e0 = (int64_t)b.y * kEpb1;
+  const int L = P.L;
+  const int D = P.D32;
+  const CrtView cv = crt_view(T.crt_pool, P);
+  uint16_t* s_v = reinterpret_cast<uint16_t*>(s1);          // [L][kEpb1] (16-byte rows)
+  uint32_t* s_M = s1 + L * (kEpb1 / 2);                       // [L][ND]
+  uint32_t* s_mu = s_M + L * ND;                              // [L]
+  uint32_t* s_tab = s_mu + L;                                 // [3][ND]: negP, negH1, P
+  uint32_t* s_mag = s_tab + 3 * ND;                           // [ND][kEpb1]
+  for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
+  for (int i = threadIdx.x; i < ND; i += kEpb1) {
+    s_tab[i] = __ldg(cv.negP + i);
+    s_tab[ND + i] = __ldg(cv.negH1 + i);
+    s_tab[2 * ND + i] = __ldg(cv.P + i);
+  }
+  // v_l = u_l M_l^{-1} mod m_l: 16-byte loads of 8 reduced products; a block
+  // covers 16 x 8 = 128 outputs of 8 moduli per pass, independent loads first
+  {
+    const int lane8 = threadIdx.x & 15;                       // which 8 outputs
+    const int lrow = threadIdx.x >> 4;                        // modulus within the pass
+    const bool full = e0 + kEpb1 <= MN && (MN & 7) == 0;
+    for (int l0 = 0; l0 < L; l0 += 8 * 4) {
+      uint4 w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int l = l0 + 8 * j + lrow;
+        w[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (l < L) {
+          const uint16_t* src = P.u + (int64_t)l * MN + e0 + 8 * lane8;
+          if (full) {
+            w[j] = __ldg(reinterpret_cast<const uint4*>(src));
+          } else {
+            uint16_t tmp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tmp[q] = (e0 + 8 * lane8 + q < MN) ? src[q] : (uint16_t)0;
+            w[j].x = tmp[0] | ((uint32_t)tmp[1] << 16); w[j].y = tmp[2] | ((uint32_t)tmp[3] << 16);
+            w[j].z = tmp[4] | ((uint32_t)tmp[5] << 16); w[j].w = tmp[6] | ((uint32_t)tmp[7] << 16);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int l = l0 + 8 * j + lrow;
+        if (l >= L) continue;
+        const ModConst mc = T.mods[l];
+        const uint32_t inv = __ldg(cv.Minv + l);
+        const uint32_t in[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t lo = barrett32((in[q] & 0xffffu) * inv, mc.m, mc.mu);
+          const uint32_t hi = barrett32((in[q] >> 16) * inv, mc.m, mc.mu);
+          o[q] = lo | (hi << 16);
+        }
+        *reinterpret_cast<uint4*>(s_v + l * kEpb1 + 8 * lane8) = make_uint4(o[0], o[1], o[2], o[3]);
+        if (lane8 == 0) s_mu[l] = mc.mu;
+      }
+    }
+  }
+  __syncthreads();
+  const int e = threadIdx.x;
+  const int64_t idx = e0 + e;
+  if (idx >= MN) return;
+
+  // quotient estimate alpha~ in {alpha - 1, alpha}
+  uint64_t sig = 0;
+  for (int l = 0; l < L; ++l) sig += (uint64_t)(uint32_t)s_v[l * kEpb1 + e] * s_mu[l];
+  const uint32_t alpha = (uint32_t)(sig >> 32);
+
+  // R = S + alpha~ (2^(32 D) - P) mod 2^(32 D)
+  uint64_t acc[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) acc[d] = (uint64_t)alpha * s_tab[d];
+  for (int l = 0; l < L; ++l) {
+    const uint32_t v = s_v[l * kEpb1 + e];
+    const uint4* mrow = reinterpret_cast<const uint4*>(s_M + l * ND);
+#pragma unroll
+    for (int q = 0; q < ND / 4; ++q) {
+      const uint4 m4 = mrow[q];
+      acc[4 * q + 0] += (uint64_t)v * m4.x;
+      acc[4 * q + 1] += (uint64_t)v * m4.y;
+      acc[4 * q + 2] += (uint64_t)v * m4.z;
+      acc[4 * q + 3] += (uint64_t)v * m4.w;
+    }
+  }
+  uint32_t R[ND];
+  {
+    uint64_t c = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = acc[d] + c;            // acc < 2^63, c < 2^32
+      R[d] = d < D ? (uint32_t)x : 0u;
+      c = x >> 32;
+    }
+  }
+  // carry out of digit D-1 of (R + Y) for a table Y of D digits
+  auto carry_out = [&](const uint32_t* Y, uint32_t (&out)[ND], uint32_t cin) -> uint32_t {
+    uint64_t c = cin;
+    uint32_t co = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = (uint64_t)R[d] + Y[d] + c;
+      out[d] = d < D ? (uint32_t)x : 0u;
+      c = x >> 32;
+      if (d == D - 1) co = (uint32_t)c;
+    }
+    return co;
+  };
+  uint32_t W[ND];
+  // R in [0, 2P): subtract P once if R >= P
+  if (carry_out(s_tab, W, 0u)) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) R[d] = W[d];
+  }
+  if (carry_out(s_tab, W, 0u)) atomicOr(T.status, kStatusCrtRange);     // x0 < P must hold
+  const bool neg = carry_out(s_tab + ND, W, 0u) != 0u;                  // x0 > floor(P/2)
+  if (neg) {
+    // |c_hat| = P - x0 = P + ~x0 + 1 (mod 2^(32 D))
+    uint64_t c = 1;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = (uint64_t)s_tab[2 * ND + d] + (uint32_t)~R[d] + c;
+      c = x >> 32;
+      R[d] = d < D ? (uint32_t)x : 0u;
+    }
+  }
+  if (P.dbg_chat != nullptr) {
+    uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
+    dst[0] = neg;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if (d < D) dst[1 + d] = R[d];
+  }
+  int top = -1;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    s_mag[d * kEpb1 + e] = R[d];
+    if (R[d]) top = d;
+  }
+  const int64_t row = idx / P.N, col = idx - row * P.N;
+  auto mag_word = [&](int w) -> uint32_t {
+    return (w >= 0 && w < ND) ? s_mag[w * kEpb1 + e] : 0u;
+  };
+  const int p = P.p, nl = P.nl;
+  if (top < 0) {
+    if (P.kind == 1) {
+      P.c_f64[row * P.c_f64_ld + col] = 0.0;
+    } else {
+      const int64_t coff = row * P.c_ld + col;
+      for (int q = 0; q < nl; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
+      P.c_exp[coff] = 0;
+      P.c_sign[coff] = 0;
+    }
+    return;
+  }
+  int n = 32 * top + 32 - __clz(mag_word(top));
+  const int sh = n - p, rpos = sh - 1;
+  uint32_t up = 0;
+  if (rpos >= 0) {
+    const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
+    const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
+    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
+    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
+    up = rb & ((sticky != 0u) | lsb);
+  }
+  // F = floor(|c_hat| 2^(64 nl - n)), low 64 nl - p bits cleared, plus the
+  // rounding increment at bit 64 nl - p
+  const int base = n - 64 * nl;
+  const int q0 = base >> 5, bs = base & 31;
+  const int lowb = 64 * nl - p;
+  uint32_t F[ND];
+  uint64_t c = 0;
+  bool ovf = false;
+#pragma unroll
+  for (int w = 0; w < ND; ++w) {
+    uint32_t f = 0u;
+    if (w < 2 * nl) {
+      f = __funnelshift_r(mag_word(q0 + w), mag_word(q0 + w + 1), bs);
+      if (32 * w + 32 <= lowb) f = 0u;
+      else if (32 * w < lowb) f &= ~((1u << (lowb - 32 * w)) - 1u);
+    }
+    const uint64_t x = (uint64_t)f + (uint64_t)((up && w == (lowb >> 5)) ? (1u << (lowb & 31)) : 0u) + c;
+    F[w] = (uint32_t)x;
+    c = (w < 2 * nl) ? (x >> 32) : 0u;
+    if (w == 2 * nl - 1 && c) ovf = true;    // rounded up to 2^p
+  }
+  if (ovf) {
+#pragma unroll
+    for (int w = 0; w < ND; ++w) F[w] = (w == 2 * nl - 1) ? 0x80000000u : 0u;
+    n += 1;
+  }
+  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
+  if (P.kind == 1) {
+    const uint64_t limb = ((uint64_t)F[1] << 32) | F[0];
+    double out;
+    const int bexp = eo - 1 + 1023;
+    const uint64_t sgn = neg ? (1ull << 63) : 0ull;
+    if (bexp >= 1 && bexp <= 2046) {
+      out = __longlong_as_double((long long)(sgn | ((uint64_t)bexp << 52) | ((limb >> 11) & ((1ull << 52) - 1))));
+    } else {
+      out = ldexp((double)(limb >> 11), eo - 53);
+      if (neg) out = -out;
+    }
+    P.c_f64[row * P.c_f64_ld + col] = out;
+    return;
+  }
+  const int64_t coff = row * P.c_ld + col;
+#pragma unroll
+  for (int q = 0; q < ND / 2; ++q)
+    if (q < nl) P.c_limbs[(int64_t)q * P.c_ps + coff] = ((uint64_t)F[2 * q + 1] << 32) | F[2 * q];
+  P.c_exp[coff] = eo;
+  P.c_sign[coff] = neg ? 1 : 0;
+}
+
+// Classes 0..8: one lane per output with ND = 8, 12, ..., 40 digits;
+// classes 9..11: lane groups (GL lanes x DPL digits) for larger accumulators.
 struct CrtClass { int gl, dpl; };
-const CrtClass kCrtClasses[] = {{4, 3}, {8, 2}, {8, 3}, {8, 5}, {16, 4}, {16, 6}, {32, 5}};
-constexpr int kNumCrtClasses = 7;
+const CrtClass kCrtClasses[] = {{1, 8},  {1, 12}, {1, 16}, {1, 20}, {1, 24}, {1, 28},
+                                {1, 32}, {1, 36}, {1, 40}, {16, 4}, {16, 6}, {32, 5}};
+constexpr int kNumCrtClasses = 12;
 
 template <int GL, int DPL>
 cudaError_t launch_crt_t(const DevTables& t, const int4* blk, int nblk, int smem, cudaStream_t s) {
@@ -291,13 +525,30 @@ cudaError_t crt_attr() {
   return cudaFuncSetAttribute(k_crt<GL, DPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
+template <int ND>
+cudaError_t crt1_attr() {
+  return cudaFuncSetAttribute(k_crt1<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <int ND>
+cudaError_t launch_crt1_t(const DevTables& t, const int4* blk, int nblk, int lmax, cudaStream_t s) {
+  const int smem = lmax * ND * 4 + lmax * 4 + 3 * ND * 4 + ND * kEpb1 * 4 + lmax * kEpb1 * 2 + 16;
+  k_crt1<ND><<<nblk, kEpb1, smem, s>>>(t, blk);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t init_crt_attributes() {
-  cudaError_t e = crt_attr<4, 3>();
-  if (e == cudaSuccess) e = crt_attr<8, 2>();
-  if (e == cudaSuccess) e = crt_attr<8, 3>();
-  if (e == cudaSuccess) e = crt_attr<8, 5>();
+  cudaError_t e = crt1_attr<8>();
+  if (e == cudaSuccess) e = crt1_attr<12>();
+  if (e == cudaSuccess) e = crt1_attr<16>();
+  if (e == cudaSuccess) e = crt1_attr<20>();
+  if (e == cudaSuccess) e = crt1_attr<24>();
+  if (e == cudaSuccess) e = crt1_attr<28>();
+  if (e == cudaSuccess) e = crt1_attr<32>();
+  if (e == cudaSuccess) e = crt1_attr<36>();
+  if (e == cudaSuccess) e = crt1_attr<40>();
   if (e == cudaSuccess) e = crt_attr<16, 4>();
   if (e == cudaSuccess) e = crt_attr<16, 6>();
   if (e == cudaSuccess) e = crt_attr<32, 5>();
@@ -305,11 +556,16 @@ cudaError_t init_crt_attributes() {
 }
 
 int crt_class_for(int d32) {
-  for (int i = 0; i < kNumCrtClasses; ++i)
-    if (d32 + 1 <= kCrtClasses[i].gl * kCrtClasses[i].dpl) return i;
+  for (int i = 0; i < kNumCrtClasses; ++i) {
+    const CrtClass& c = kCrtClasses[i];
+    // one-lane classes hold exactly D digits; lane groups need digit D as the carry slot
+    if (c.gl == 1 ? d32 <= c.dpl : d32 + 1 <= c.gl * c.dpl) return i;
+  }
   return -1;
 }
-int crt_class_elems_per_block(int cls) { return 256 / kCrtClasses[cls].gl; }
+int crt_class_elems_per_block(int cls) {
+  return kCrtClasses[cls].gl == 1 ? kEpb1 : 256 / kCrtClasses[cls].gl;
+}
 int crt_class_digits(int cls) { return kCrtClasses[cls].gl * kCrtClasses[cls].dpl; }
 
 cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int nblk, int lmax,
@@ -319,13 +575,18 @@ cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int
   const int4* blk = reinterpret_cast<const int4*>(blk_list);
   const int smem = lmax * crt_class_elems_per_block(cls) * 2;
   switch (cls) {
-    case 0: return launch_crt_t<4, 3>(t, blk, nblk, smem, s);
-    case 1: return launch_crt_t<8, 2>(t, blk, nblk, smem, s);
-    case 2: return launch_crt_t<8, 3>(t, blk, nblk, smem, s);
-    case 3: return launch_crt_t<8, 5>(t, blk, nblk, smem, s);
-    case 4: return launch_crt_t<16, 4>(t, blk, nblk, smem, s);
-    case 5: return launch_crt_t<16, 6>(t, blk, nblk, smem, s);
-    case 6: return launch_crt_t<32, 5>(t, blk, nblk, smem, s);
+    case 0: return launch_crt1_t<8>(t, blk, nblk, lmax, s);
+    case 1: return launch_crt1_t<12>(t, blk, nblk, lmax, s);
+    case 2: return launch_crt1_t<16>(t, blk, nblk, lmax, s);
+    case 3: return launch_crt1_t<20>(t, blk, nblk, lmax, s);
+    case 4: return launch_crt1_t<24>(t, blk, nblk, lmax, s);
+    case 5: return launch_crt1_t<28>(t, blk, nblk, lmax, s);
+    case 6: return launch_crt1_t<32>(t, blk, nblk, lmax, s);
+    case 7: return launch_crt1_t<36>(t, blk, nblk, lmax, s);
+    case 8: return launch_crt1_t<40>(t, blk, nblk, lmax, s);
+    case 9: return launch_crt_t<16, 4>(t, blk, nblk, smem, s);
+    case 10: return launch_crt_t<16, 6>(t, blk, nblk, smem, s);
+    case 11: return launch_crt_t<32, 5>(t, blk, nblk, smem, s);
   }
   return cudaErrorInvalidValue;
 }
