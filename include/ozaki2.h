@@ -95,6 +95,9 @@ typedef struct {
   int grid;       /* persistent CTAs of the grouped GEMM; 0 = one per SM */
   int schedule;   /* OZ2_SCHED_* */
   int timing;     /* nonzero: record per-stage CUDA events (ozaki2_last_timings) */
+  int crt_engine; /* 0: CRT on the CUDA cores (default); 1: CRT column sums as an exact bf16
+                     GEMM on the tensor cores where 2L <= 256, the accumulator has <= 40 digits
+                     and the tables fit in shared memory (CUDA cores otherwise) */
 } ozaki2_opts;
 
 /* Facts about a plan (all computed on the host at plan creation). */
@@ -162,7 +165,8 @@ OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digit
      off[1] column exponents f int32 [N]
      off[2] A planes  bf16 [G][M][Kp]   (Kp = K rounded up to 8; K-major)
      off[3] B planes  bf16 [G][N][Kp]   (transposed: column j of B is row j)
-     off[4] reduced products u  uint16 [L][M][N]
+     off[4] reduced products u  uint16 [L][MNp], MNp = M*N rounded up to a multiple of 8
+            (row-major (i, j) within each modulus row)
    and *kp = Kp.  Plane order: one-limb moduli in plane order, then for each
    two-limb modulus the planes r0, r1, r0 + r1 (balanced base-128 split). */
 OZ2_API int ozaki2_plan_layout(ozaki2_plan plan, int prob, size_t off[5], int64_t* kp);

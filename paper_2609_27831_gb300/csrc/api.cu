@@ -143,6 +143,10 @@ struct CrtHost {
   int L, D32, DS, cls;
   Big P;
   std::vector<uint32_t> words;   // pool layout (see CrtView), DS-padded
+  // tensor-core CRT table B [npad][kpad] (bf16 bits): B[j][2l] = M_l[j],
+  // B[j][2l+1] = M_l[j-1], M_l[j] the 7-bit pieces of M_l
+  int kpad = 0, npad = 0, np = 0;
+  std::vector<uint16_t> tc_table;
 };
 
 struct ProbHost {
@@ -153,6 +157,8 @@ struct ProbHost {
   size_t off_e, off_f, off_pa, off_pb, off_u;   // workspace offsets
   int kind;                    // 0: limb output; 1: binary64 output
   bool skip_a, skip_b;         // planes of that side are written by the caller
+  int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls)
+  int crt_kpad, crt_npad, crt_np;
 };
 
 struct ListRef {
@@ -187,6 +193,9 @@ struct DevState {
   const int32_t* cta_plain = nullptr;
   std::vector<PlainSeg> plain;
   std::vector<int> crt_off;    // per problem, uint32 offset in the pool
+  ListRef tct[9];               // tensor-core CRT tile lists (smem = kpad_max, lmax = L max)
+  int tct_npad[9] = {0};
+  std::vector<void*> crt_tab;   // per problem: device address of its tensor-core CRT table
 };
 
 static void free_launch_block(LaunchBlock& lb) {
@@ -308,6 +317,44 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     key = (int)pl->crts.size() - 1;
   }
   h.crt_key = key;
+  {
+    CrtHost& c = pl->crts[key];
+    const int np = (big_bitlen(c.P) + 6) / 7 + 1;
+    const int kpad = (int)align_up((size_t)2 * L, 64);
+    const int npad = (int)align_up((size_t)np, 16);
+    const bool tc_ok = o.crt_engine == 1 && h.crt_cls <= 8 && kpad <= 256 && npad <= 256 &&
+                       crt_tc_smem_bytes(h.crt_cls, kpad, npad, L, 1) <= 227 * 1024;
+    h.crt_mode = tc_ok ? 1 : 0;
+    h.crt_kpad = kpad;
+    h.crt_npad = npad;
+    h.crt_np = np;
+    if (tc_ok && c.tc_table.empty()) {
+      c.kpad = kpad; c.npad = npad; c.np = np;
+      c.tc_table.assign((size_t)npad * kpad, 0);
+      const auto& mlist = modulus_list();
+      auto bf = [](uint32_t x) -> uint16_t {   // exact for x <= 256
+        float f = (float)x;
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return (uint16_t)(u >> 16);
+      };
+      for (int l = 0; l < L; ++l) {
+        Big Ml;
+        big_divmod_small(c.P, mlist[l], &Ml);
+        std::vector<uint32_t> piece(np + 1, 0u);
+        for (int j = 0; j < np; ++j) {
+          const int bit = 7 * j, w = bit / 32, sh = bit % 32;
+          uint64_t x = w < (int)Ml.size() ? Ml[w] : 0u;
+          if (w + 1 < (int)Ml.size()) x |= (uint64_t)Ml[w + 1] << 32;
+          piece[j] = (uint32_t)(x >> sh) & 127u;
+        }
+        for (int j = 0; j < np; ++j) {
+          c.tc_table[(size_t)j * kpad + 2 * l] = bf(piece[j]);
+          c.tc_table[(size_t)j * kpad + 2 * l + 1] = j ? bf(piece[j - 1]) : 0;
+        }
+      }
+    }
+  }
   pl->probs.push_back(h);
   pl->lmax = std::max(pl->lmax, L);
   pl->w16max = std::max(pl->w16max, residue_class_w16(h.res_cls));
@@ -324,7 +371,7 @@ static void layout_workspace(ozaki2_plan_s* pl) {
   for (auto& h : pl->probs) {
     h.off_pa = off; off += align_up(2 * (size_t)h.G * h.M * h.Kp, 256);
     h.off_pb = off; off += align_up(2 * (size_t)h.G * h.N * h.Kp, 256);
-    h.off_u = off; off += align_up(2 * (size_t)h.L * h.M * h.N, 256);
+    h.off_u = off; off += align_up(2 * (size_t)h.L * align_up((size_t)(h.M * h.N), 8), 256);
   }
   pl->ws_bytes = off;
 }
@@ -337,7 +384,8 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   const ozaki2_opts& o = pl->opts;
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
-      (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN)) {
+      (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
+      (o.crt_engine != 0 && o.crt_engine != 1)) {
     delete pl;
     return OZ2_EINVAL;
   }
@@ -381,6 +429,10 @@ struct TableImage {
   int n_srows = 0, n_scols = 0, n_simt = 0, n_res[6] = {0}, n_crt[kCrtClassCount] = {0};
   int res_l[6] = {0}, crt_l[kCrtClassCount] = {0};
   int grid = 0;
+  // tensor-core CRT: tile lists per one-lane class, table offsets per CRT key
+  size_t o_tct[9] = {0};
+  int n_tct[9] = {0}, tct_kpad[9] = {0}, tct_npad[9] = {0}, tct_l[9] = {0};
+  std::vector<size_t> o_tctab;
 };
 
 // Host side of the device upload: modulus constants, residue digit tables,
@@ -472,7 +524,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
 
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
-  std::vector<std::vector<int4>> res(6), crt(kCrtClassCount);
+  std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -488,11 +540,20 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
         for (int64_t k = 0; k < h.K; k += 64) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
     ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
-    const int epb = crt_class_elems_per_block(h.crt_cls);
-    const int64_t nb = (h.M * h.N + epb - 1) / epb;
-    if (nb > INT_MAX) return OZ2_ERANGE;
-    for (int64_t bb = 0; bb < nb; ++bb) crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
-    ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
+    if (h.crt_mode == 1) {
+      const int64_t nt = (h.M * h.N + 127) / 128;
+      if (nt > INT_MAX) return OZ2_ERANGE;
+      for (int64_t tt = 0; tt < nt; ++tt) tct[h.crt_cls].push_back(make_int4(pi, (int)tt, 0, 0));
+      ti.tct_kpad[h.crt_cls] = std::max(ti.tct_kpad[h.crt_cls], h.crt_kpad);
+      ti.tct_npad[h.crt_cls] = std::max(ti.tct_npad[h.crt_cls], h.crt_npad);
+      ti.tct_l[h.crt_cls] = std::max(ti.tct_l[h.crt_cls], h.L);
+    } else {
+      const int epb = crt_class_elems_per_block(h.crt_cls);
+      const int64_t nb = (h.M * h.N + epb - 1) / epb;
+      if (nb > INT_MAX) return OZ2_ERANGE;
+      for (int64_t bb = 0; bb < nb; ++bb) crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
+      ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
+    }
   }
   for (int u = 0; u < nunits; ++u) {
     const ProbHost& h = pl->probs[units[u].prob];
@@ -515,6 +576,14 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   for (int i = 0; i < 6; ++i) ti.o_res[i] = ti.b.add(res[i].data(), res[i].size() * 16);
   for (int i = 0; i < kCrtClassCount; ++i) ti.o_crt[i] = ti.b.add(crt[i].data(), crt[i].size() * 16);
   ti.o_status = ti.b.add(nullptr, 256);
+  for (int i = 0; i < 9; ++i) {
+    ti.o_tct[i] = ti.b.add(tct[i].data(), tct[i].size() * 16);
+    ti.n_tct[i] = (int)tct[i].size();
+  }
+  ti.o_tctab.assign(pl->crts.size(), 0);
+  for (size_t i = 0; i < pl->crts.size(); ++i)
+    if (!pl->crts[i].tc_table.empty())
+      ti.o_tctab[i] = ti.b.add(pl->crts[i].tc_table.data(), pl->crts[i].tc_table.size() * 2, 1024);
   ti.n_srows = (int)scan_rows.size();
   ti.n_scols = (int)scan_cols.size();
   ti.n_simt = (int)simt.size();
@@ -548,6 +617,13 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   for (int i = 0; i < 6; ++i)
     d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_res[i]), ti.n_res[i],
                        ti.res_l[i] * (residue_class_w16(i) + 4) * 4, ti.res_l[i]};
+  for (int i = 0; i < 9; ++i) {
+    d.tct[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_tct[i]), ti.n_tct[i], ti.tct_kpad[i], ti.tct_l[i]};
+    d.tct_npad[i] = ti.tct_npad[i];
+  }
+  d.crt_tab.assign(pl->probs.size(), nullptr);
+  for (size_t i = 0; i < pl->probs.size(); ++i)
+    if (pl->probs[i].crt_mode == 1) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
   for (int i = 0; i < kCrtClassCount; ++i)
     d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_crt[i]), ti.n_crt[i], 0, ti.crt_l[i]};
 }
@@ -588,7 +664,7 @@ static int upload(ozaki2_plan_s* pl) {
 static int alloc_launch_block(LaunchBlock& lb, int count) {
   const size_t probs_bytes = align_up(sizeof(ProbDev) * count, 128);
   lb.tmap_off = probs_bytes;
-  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 2 * count;
+  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 4 * count;   // A planes, B planes, CRT table, u tiles
   if (cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) { lb.d_mem = nullptr; return OZ2_ENOMEM; }
   if (cudaMallocHost(&lb.h_stage, lb.bytes) != cudaSuccess) { lb.h_stage = nullptr; return OZ2_ENOMEM; }
   if (cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming) != cudaSuccess) return OZ2_ECUDA;
@@ -647,10 +723,33 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     }
     P.DS = h.DS;
     P.dbg_chat = pl->dbg_chat.empty() ? nullptr : pl->dbg_chat[i];
+    P.upitch = (int64_t)align_up((size_t)(h.M * h.N), 8);
+    P.crt_mode = h.crt_mode;
+    P.crt_kpad = h.crt_kpad;
+    P.crt_npad = h.crt_npad;
+    P.crt_np = h.crt_np;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
     if (rc) return rc;
     rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);
     if (rc) return rc;
+    if (h.crt_mode == 1) {
+      const cuuint64_t dims[2] = {(cuuint64_t)h.crt_kpad, (cuuint64_t)h.crt_npad};
+      const cuuint64_t strides[1] = {(cuuint64_t)h.crt_kpad * 2};
+      const cuuint32_t box[2] = {64u, (cuuint32_t)h.crt_npad};
+      const cuuint32_t es[2] = {1u, 1u};
+      if (get_encode()(&tm[2 * count + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.crt_tab[i], dims, strides,
+                       box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return OZ2_ECUDA;
+      // u tiles: [L][upitch] uint16, boxes of 128 outputs x L moduli
+      const cuuint64_t udims[2] = {(cuuint64_t)P.upitch, (cuuint64_t)h.L};
+      const cuuint64_t ustr[1] = {(cuuint64_t)P.upitch * 2};
+      const cuuint32_t ubox[2] = {128u, (cuuint32_t)h.L};
+      if (get_encode()(&tm[3 * count + i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, P.u, udims, ustr, ubox, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return OZ2_ECUDA;
+    }
   }
   return OZ2_OK;
 }
@@ -706,6 +805,10 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
   for (int c = 0; c < kCrtClassCount; ++c)
     if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
+  for (int c = 0; c < 9; ++c)
+    if (d.tct[c].n)
+      OZ2_CU(launch_crt_tc(tab, c, d.tct[c].ptr, d.tct[c].n, d.tct[c].smem, d.tct_npad[c], d.tct[c].lmax,
+                           std::min(d.sms, d.tct[c].n), s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[4], s));
   return OZ2_OK;
 }
@@ -777,6 +880,7 @@ int ozaki2_opts_default(ozaki2_opts* o) {
   o->grid = 0;
   o->schedule = OZ2_SCHED_GROUPED;
   o->timing = 0;
+  o->crt_engine = 0;
   return OZ2_OK;
 }
 
@@ -1005,7 +1109,8 @@ std::map<std::vector<int64_t>, Cached> g_cache;
 std::vector<int64_t> cache_key(int count, const ozaki2_problem* probs, const ozaki2_opts& o) {
   int dev = -1;
   cudaGetDevice(&dev);
-  std::vector<int64_t> k{dev, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule, o.timing, count};
+  std::vector<int64_t> k{dev, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule, o.timing,
+                         o.crt_engine, count};
   for (int i = 0; i < count; ++i) {
     k.push_back(probs[i].M);
     k.push_back(probs[i].N);
@@ -1149,7 +1254,7 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   if (rc) return rc;
   const size_t lb_off = align_up(ti.b.img.size(), 256);
   const size_t probs_bytes = align_up(sizeof(ProbDev), 128);
-  const size_t lb_bytes = probs_bytes + 2 * sizeof(CUtensorMap);
+  const size_t lb_bytes = probs_bytes + 4 * sizeof(CUtensorMap);
   if (lb_off + lb_bytes > sizeof(ozaki2_noalloc_tables)) return OZ2_ERANGE;
   install_table_image(pl, ti, nd->tables);
   const ozaki2_problem q{M, N, K, p, *A, *B, *C};

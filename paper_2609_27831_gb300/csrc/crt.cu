@@ -20,6 +20,7 @@
 #include <climits>
 
 #include "oz2_internal.h"
+#include "tc_ptx.cuh"
 
 namespace oz2 {
 
@@ -31,6 +32,11 @@ __device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t m, uint32_t m
   uint32_t q = __umulhi(x, mu);
   uint32_t r = x - q * m;
   return r >= m ? r - m : r;
+}
+
+// two small non-negative integers (<= 256) as a packed bf16 pair (low, high)
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
+  return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
 }
 
 template <int GL>
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   for (int i = threadIdx.x; i < L * EPB; i += 256) {
     const int l = i / EPB, e = i - l * EPB;
     const int64_t idx = e0 + e;
-    const uint32_t uu = idx < MN ? (uint32_t)P.u[(int64_t)l * MN + idx] : 0u;
+    const uint32_t uu = idx < MN ? (uint32_t)P.u[(int64_t)l * P.upitch + idx] : 0u;
     const ModConst& mc = T.mods[l];
     s_v[i] = (uint16_t)barrett32(uu * __ldg(cv.Minv + l), mc.m, mc.mu);
   }
@@ -276,6 +282,154 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   }
 }
 
+// The CRT and rounding of one output from R = (S + alpha~ (2^(32 D) - P)) mod
+// 2^(32 D), i.e. R in [0, 2P) (Sec. 4.4): subtract P once if R >= P, take the
+// signed representative, round |c_hat| 2^(e_i + f_j - 2t) to p bits and write
+// the output.  tab: [3][ND] digits of 2^(32 D) - P, 2^(32 D) - (floor(P/2) + 1)
+// and P.  s_mag: scratch column e of a [ND][ldm] digit array.
+template <int ND>
+__device__ __forceinline__ int compare_digits(const uint32_t (&R)[ND], const uint32_t* Y) {
+  // sign of R - Y over ND digits, decided at the most significant differing digit
+  int cmp = 0;
+#pragma unroll
+  for (int d = ND - 1; d >= 0; --d) {
+    const uint32_t y = Y[d];
+    cmp = cmp ? cmp : (R[d] > y ? 1 : (R[d] < y ? -1 : 0));
+  }
+  return cmp;
+}
+
+template <int ND>
+__device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], const uint32_t* s_tab,
+                                           uint32_t* s_mag, int ldm, int e, int64_t idx, int32_t* status) {
+  const int D = P.D32;
+  const uint32_t* Pd = s_tab + 2 * ND;
+  // R in [0, 2P): subtract P once if R >= P
+  if (compare_digits<ND>(R, Pd) >= 0) {
+    uint32_t br = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = (uint64_t)R[d] - Pd[d] - br;
+      R[d] = (uint32_t)x;
+      br = (uint32_t)(x >> 63);
+    }
+    if (compare_digits<ND>(R, Pd) >= 0) atomicOr(status, kStatusCrtRange);   // x0 < P must hold
+  }
+  // signed representative: x0 > floor(P/2) means c_hat = x0 - P < 0, |c_hat| = P - x0.
+  // floor(P/2) + 1 is stored as its complement 2^(32 D) - (floor(P/2) + 1) in s_tab + ND;
+  // x0 > floor(P/2) <=> x0 >= floor(P/2) + 1 <=> x0 + complement carries out of digit D-1
+  bool neg;
+  {
+    const uint32_t* negH1 = s_tab + ND;
+    uint64_t c = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = (uint64_t)R[d] + (d < D ? negH1[d] : 0u) + c;
+      c = (d < D) ? (x >> 32) : c;
+    }
+    neg = c != 0;
+  }
+  if (neg) {
+    uint32_t br = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const uint64_t x = (uint64_t)Pd[d] - R[d] - br;
+      R[d] = (uint32_t)x;
+      br = (uint32_t)(x >> 63);
+    }
+  }
+  if (P.dbg_chat != nullptr) {
+    uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
+    dst[0] = neg;
+#pragma unroll
+    for (int d = 0; d < ND; ++d)
+      if (d < D) dst[1 + d] = R[d];
+  }
+  int top = -1;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    s_mag[d * ldm + e] = R[d];
+    if (R[d]) top = d;
+  }
+  const int64_t row = idx / P.N, col = idx - row * P.N;
+  auto mag_word = [&](int w) -> uint32_t {
+    return (w >= 0 && w < ND) ? s_mag[w * ldm + e] : 0u;
+  };
+  const int p = P.p, nl = P.nl;
+  if (top < 0) {
+    if (P.kind == 1) {
+      P.c_f64[row * P.c_f64_ld + col] = 0.0;
+    } else {
+      const int64_t coff = row * P.c_ld + col;
+      for (int q = 0; q < nl; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
+      P.c_exp[coff] = 0;
+      P.c_sign[coff] = 0;
+    }
+    return;
+  }
+  int n = 32 * top + 32 - __clz(mag_word(top));
+  const int sh = n - p, rpos = sh - 1;
+  uint32_t up = 0;
+  if (rpos >= 0) {
+    const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
+    const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
+    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
+    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
+    up = rb & ((sticky != 0u) | lsb);
+  }
+  // the 2 nl output words: F = floor(|c_hat| 2^(64 nl - n)) with the low
+  // 64 nl - p bits cleared, plus the rounding increment at bit 64 nl - p
+  const int base = n - 64 * nl;
+  const int q0 = base >> 5, bs = base & 31;
+  const int lowb = 64 * nl - p;
+  const bool kind1 = P.kind == 1;
+  const int64_t coff = row * P.c_ld + col;
+  uint64_t c = 0;
+  uint32_t prev = 0;
+  uint64_t limb0 = 0;
+  bool ovf = false;
+  for (int w = 0; w < 2 * nl; ++w) {
+    uint32_t f = __funnelshift_r(mag_word(q0 + w), mag_word(q0 + w + 1), bs);
+    if (32 * w + 32 <= lowb) f = 0u;
+    else if (32 * w < lowb) f &= ~((1u << (lowb - 32 * w)) - 1u);
+    const uint64_t x = (uint64_t)f + (uint64_t)((up && w == (lowb >> 5)) ? (1u << (lowb & 31)) : 0u) + c;
+    const uint32_t fw = (uint32_t)x;
+    c = x >> 32;
+    if (w & 1) {
+      const uint64_t limb = ((uint64_t)fw << 32) | prev;
+      if (kind1) limb0 = limb;
+      else P.c_limbs[(int64_t)(w >> 1) * P.c_ps + coff] = limb;
+    }
+    prev = fw;
+  }
+  if (c) {                                        // rounded up to 2^p: renormalise
+    ovf = true;
+    n += 1;
+    if (!kind1) {
+      for (int q = 0; q < nl - 1; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
+      P.c_limbs[(int64_t)(nl - 1) * P.c_ps + coff] = 1ull << 63;
+    }
+    limb0 = 1ull << 63;
+  }
+  (void)ovf;
+  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
+  if (kind1) {
+    double out;
+    const int bexp = eo - 1 + 1023;
+    const uint64_t sgn = neg ? (1ull << 63) : 0ull;
+    if (bexp >= 1 && bexp <= 2046) {
+      out = __longlong_as_double((long long)(sgn | ((uint64_t)bexp << 52) | ((limb0 >> 11) & ((1ull << 52) - 1))));
+    } else {
+      out = ldexp((double)(limb0 >> 11), eo - 53);
+      if (neg) out = -out;
+    }
+    P.c_f64[row * P.c_f64_ld + col] = out;
+    return;
+  }
+  P.c_exp[coff] = eo;
+  P.c_sign[coff] = neg ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // One lane per output element (CRT accumulators of up to 40 digits).  The
 // warps of a block cooperate on the staging: the reduced products of 128
@@ -313,7 +467,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   {
     const int lane8 = threadIdx.x & 15;                       // which 8 outputs
     const int lrow = threadIdx.x >> 4;                        // modulus within the pass
-    const bool full = e0 + kEpb1 <= MN && (MN & 7) == 0;
+    const bool full = e0 + kEpb1 <= MN;
     for (int l0 = 0; l0 < L; l0 += 8 * 4) {
       uint4 w[4];
 #pragma unroll
@@ -321,7 +475,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
         const int l = l0 + 8 * j + lrow;
         w[j] = make_uint4(0u, 0u, 0u, 0u);
         if (l < L) {
-          const uint16_t* src = P.u + (int64_t)l * MN + e0 + 8 * lane8;
+          const uint16_t* src = P.u + (int64_t)l * P.upitch + e0 + 8 * lane8;
           if (full) {
             w[j] = __ldg(reinterpret_cast<const uint4*>(src));
           } else {
@@ -388,123 +542,263 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
       c = x >> 32;
     }
   }
-  // carry out of digit D-1 of (R + Y) for a table Y of D digits
-  auto carry_out = [&](const uint32_t* Y, uint32_t (&out)[ND], uint32_t cin) -> uint32_t {
-    uint64_t c = cin;
-    uint32_t co = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint64_t x = (uint64_t)R[d] + Y[d] + c;
-      out[d] = d < D ? (uint32_t)x : 0u;
-      c = x >> 32;
-      if (d == D - 1) co = (uint32_t)c;
-    }
-    return co;
+  crt_finish<ND>(P, R, s_tab, s_mag, kEpb1, e, idx, T.status);
+}
+
+
+// ---------------------------------------------------------------------------
+// CRT column sums on the tensor cores.  With v_l = v0 + 128 v1 (7-bit halves)
+// and M_l = sum_j M_l[j] 128^j (7-bit pieces),
+//   S = sum_l v_l M_l = sum_j 128^j Y_j,   Y_j = sum_l (v0_l M_l[j] + v1_l M_l[j-1]),
+// which is one GEMM Y = V B with K = 2L (columns 2l, 2l+1 of V hold v0_l, v1_l)
+// and N = the number of 7-bit pieces of S.  Every product is below 2^14 and
+// every partial sum below 2L 2^14 < 2^23, so bf16 operands and the fp32 TMEM
+// accumulator are exact.
+//
+// One CTA per tile of 128 consecutive outputs, 8 warps, sized for two CTAs
+// per SM.  Thread 0 loads the piece table B and the tile's reduced products
+// u with TMA; all threads build V (two threads per output, half of the moduli
+// each) together with the quotient estimate; thread 0 issues the MMAs; the
+// epilogue splits the columns of Y between the two warps of each TMEM lane
+// quadrant, carries sum_j 128^j Y_j into 32-bit digits, merges the halves and
+// finishes the CRT and rounding of each output (crt_finish).
+// Tile list entry: {problem, tile index, 0, 0}.
+// ---------------------------------------------------------------------------
+constexpr int kCtThreads = 256;
+
+__host__ __device__ inline int crt_tc_tmem_cols(int npad) {
+  int c = 32;
+  while (c < npad) c <<= 1;
+  return c;
+}
+
+// Shared-memory layout of the tensor-core CRT (launch-wide maxima).
+struct CtLayout {
+  uint32_t b_bytes, a_region, u_region, small_off, total;
+  __host__ __device__ CtLayout(int ND, int kpad, int npad, int lmax) {
+    b_bytes = (uint32_t)npad * kpad * 2;
+    uint32_t a = (uint32_t)128 * kpad * 2;
+    if (a < (uint32_t)(2 * ND * 128 * 4)) a = (uint32_t)(2 * ND * 128 * 4);   // digit arrays reuse a V buffer
+    a_region = (a + 1023u) & ~1023u;
+    u_region = ((uint32_t)lmax * 128 * 2 + 1023u) & ~1023u;
+    small_off = b_bytes + 2 * a_region + 2 * u_region;
+    // small: s_sig [2][2][128] u64, s_pc [lmax] uint4, s_tab [3][ND], 8 barriers, tmem slot
+    total = 1024 + small_off + 4096 + (uint32_t)lmax * 16 + 3 * ND * 4 + 16 + 8 * 8 + 16;
+  }
+};
+
+template <int ND>
+__global__ void __launch_bounds__(kCtThreads, 1)
+    k_crt_tc(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, int kpad_max,
+             int npad_max, int lmax) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const CtLayout lay(ND, kpad_max, npad_max, lmax);
+  const uint32_t sB = base;                                       // table [kb][npad][128 B]
+  const uint32_t sA0 = base + lay.b_bytes;                        // V buffers [2]
+  const uint32_t sU0 = sA0 + 2 * lay.a_region;                    // u tiles [2][L][128]
+  uint8_t* small = sm + lay.small_off;
+  uint64_t* s_sig = reinterpret_cast<uint64_t*>(small);            // [slot][half][128]
+  uint4* s_pc = reinterpret_cast<uint4*>(small + 4096);            // [lmax]
+  uint32_t* s_tab = reinterpret_cast<uint32_t*>(s_pc + lmax);      // [3][ND]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_tab + 3 * ND + 4);
+  uint64_t* b_bar = bars;             // table loaded
+  uint64_t* u_bar = bars + 1;         // [2] u tile landed
+  uint64_t* m_bar = bars + 3;         // [2] MMA into slot done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int tcols = crt_tc_tmem_cols(npad_max);
+  if (t == 0) {
+    for (int i = 0; i < 5; ++i) mbar_init(bars + i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int abort_flag = 0;
+  uint32_t bcnt = 0, ucnt[2] = {0, 0}, mcnt[2] = {0, 0};
+  bool ok = true;
+
+  // u tile of tile list entry gi (problem `pr`) into buffer b (thread 0)
+  auto issue_u = [&](int gi, int b) {
+    const int4 t2 = tiles[gi];
+    const ProbDev& Q = T.probs[t2.x];
+    mbar_expect_tx(u_bar + b, (uint32_t)Q.L * 128 * 2);
+    tma_load_2d(sU0 + b * lay.u_region, T.tmaps + 3 * T.count + t2.x, smem_u32(u_bar + b), t2.y * 128, 0);
   };
-  uint32_t W[ND];
-  // R in [0, 2P): subtract P once if R >= P
-  if (carry_out(s_tab, W, 0u)) {
+
+  // epilogue of tile `tp` held in TMEM slot `s`; digit arrays in V buffer `s`
+  auto epilogue = [&](int4 tp, int s) {
+    const ProbDev& P = T.probs[tp.x];
+    const int D = P.D32, np = P.crt_np;
+    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status);
+    ++mcnt[s];
+    ok = __syncthreads_and(ok);                   // keep every thread on the same path
+    tc_fence_after();
+    uint32_t* s_dig = reinterpret_cast<uint32_t*>(sm + lay.b_bytes + s * lay.a_region);   // [ND][128]
+    uint32_t* s_part = s_dig + ND * 128;
+    const int quad = warp & 3, hh = warp >> 2;
+    const int er = quad * 32 + lane;
+    const int half = ((np + 63) / 64) * 32;
+    const int j0 = hh * half, j1 = min(np, j0 + half);
+    uint32_t* dst = hh ? s_part : s_dig;
+    if (ok) {
+      for (int dd = 0; dd < ND; ++dd) dst[dd * 128 + er] = 0u;
+      uint64_t win = 0;
+      int d = (7 * j0) >> 5;
+      const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * tcols);
+      for (int c = j0; c < j1; c += 32) {
+        uint32_t v[32];
+        tmem_ld32(trow + (uint32_t)c, v);
 #pragma unroll
-    for (int d = 0; d < ND; ++d) R[d] = W[d];
-  }
-  if (carry_out(s_tab, W, 0u)) atomicOr(T.status, kStatusCrtRange);     // x0 < P must hold
-  const bool neg = carry_out(s_tab + ND, W, 0u) != 0u;                  // x0 > floor(P/2)
-  if (neg) {
-    // |c_hat| = P - x0 = P + ~x0 + 1 (mod 2^(32 D))
-    uint64_t c = 1;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint64_t x = (uint64_t)s_tab[2 * ND + d] + (uint32_t)~R[d] + c;
-      c = x >> 32;
-      R[d] = d < D ? (uint32_t)x : 0u;
+        for (int q = 0; q < 32; ++q) {
+          const int j = c + q;
+          if (j < j1) {
+            int sh = 7 * j - 32 * d;
+            if (sh >= 32) {
+              if (d < ND) dst[d * 128 + er] = (uint32_t)win;
+              win >>= 32;
+              ++d;
+              sh -= 32;
+            }
+            // exact integer y < 2^23 held in fp32
+            const uint32_t y = __float_as_uint(__uint_as_float(v[q]) + 8388608.0f) - 0x4B000000u;
+            win += (uint64_t)y << sh;
+          }
+        }
+      }
+      for (; d < ND; ++d) {
+        dst[d * 128 + er] = (uint32_t)win;
+        win >>= 32;
+      }
     }
-  }
-  if (P.dbg_chat != nullptr) {
-    uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
-    dst[0] = neg;
+    tc_fence_before();
+    __syncthreads();
+    if (hh == 0 && ok) {
+      const uint32_t alpha =
+          (uint32_t)((s_sig[(s * 2 + 0) * 128 + er] + s_sig[(s * 2 + 1) * 128 + er]) >> 32);
+      uint32_t R[ND];
+      uint64_t cr = 0;
 #pragma unroll
-    for (int d = 0; d < ND; ++d)
-      if (d < D) dst[1 + d] = R[d];
-  }
-  int top = -1;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    s_mag[d * kEpb1 + e] = R[d];
-    if (R[d]) top = d;
-  }
-  const int64_t row = idx / P.N, col = idx - row * P.N;
-  auto mag_word = [&](int w) -> uint32_t {
-    return (w >= 0 && w < ND) ? s_mag[w * kEpb1 + e] : 0u;
+      for (int q = 0; q < ND; ++q) {
+        const uint64_t x = (uint64_t)s_dig[q * 128 + er] + s_part[q * 128 + er] + (uint64_t)alpha * s_tab[q] + cr;
+        R[q] = q < D ? (uint32_t)x : 0u;
+        cr = x >> 32;
+      }
+      const int64_t idx = (int64_t)tp.y * 128 + er;
+      if (idx < (int64_t)P.M * P.N) crt_finish<ND>(P, R, s_tab, s_dig, 128, er, idx, T.status);
+    }
+    __syncthreads();
   };
-  const int p = P.p, nl = P.nl;
-  if (top < 0) {
-    if (P.kind == 1) {
-      P.c_f64[row * P.c_f64_ld + col] = 0.0;
-    } else {
-      const int64_t coff = row * P.c_ld + col;
-      for (int q = 0; q < nl; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
-      P.c_exp[coff] = 0;
-      P.c_sign[coff] = 0;
+
+  int cur = -1;
+  int k = 0;
+  bool pending = false;
+  int4 prev = make_int4(0, 0, 0, 0);
+  for (int i = blockIdx.x;; i += gridDim.x) {
+    const bool have = i < ntiles;
+    int4 tl = have ? tiles[i] : make_int4(-1, 0, 0, 0);
+    if (!have || tl.x != cur) {
+      if (pending) {                                  // drain the previous problem
+        epilogue(prev, (k - 1) & 1);
+        pending = false;
+      }
+      if (!have || !ok) break;
+      const ProbDev& P = T.probs[tl.x];
+      const CrtView cv = crt_view(T.crt_pool, P);
+      for (int l = t; l < P.L; l += kCtThreads) {
+        const ModConst& mc = T.mods[l];
+        s_pc[l] = make_uint4(mc.m, mc.mu, __ldg(cv.Minv + l), 0u);
+      }
+      for (int d = t; d < ND; d += kCtThreads) {
+        s_tab[d] = d < P.DS ? __ldg(cv.negP + d) : 0u;
+        s_tab[ND + d] = d < P.DS ? __ldg(cv.negH1 + d) : 0u;
+        s_tab[2 * ND + d] = d < P.DS ? __ldg(cv.P + d) : 0u;
+      }
+      __syncthreads();
+      if (t == 0) {
+        const int kb = P.crt_kpad / 64;
+        const uint32_t tb = (uint32_t)P.crt_npad * 128;
+        mbar_expect_tx(b_bar, tb * kb);
+        for (int q = 0; q < kb; ++q)
+          tma_load_2d(sB + q * tb, T.tmaps + 2 * T.count + tl.x, smem_u32(b_bar), q * 64, 0);
+        issue_u(i, k & 1);
+        const int i2 = i + gridDim.x;
+        if (i2 < ntiles && tiles[i2].x == tl.x) issue_u(i2, (k + 1) & 1);
+      }
+      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status);
+      ok = __syncthreads_and(ok);
+      ++bcnt;
+      cur = tl.x;
     }
-    return;
-  }
-  int n = 32 * top + 32 - __clz(mag_word(top));
-  const int sh = n - p, rpos = sh - 1;
-  uint32_t up = 0;
-  if (rpos >= 0) {
-    const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
-    const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
-    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
-    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
-    up = rb & ((sticky != 0u) | lsb);
-  }
-  // F = floor(|c_hat| 2^(64 nl - n)), low 64 nl - p bits cleared, plus the
-  // rounding increment at bit 64 nl - p
-  const int base = n - 64 * nl;
-  const int q0 = base >> 5, bs = base & 31;
-  const int lowb = 64 * nl - p;
-  uint32_t F[ND];
-  uint64_t c = 0;
-  bool ovf = false;
-#pragma unroll
-  for (int w = 0; w < ND; ++w) {
-    uint32_t f = 0u;
-    if (w < 2 * nl) {
-      f = __funnelshift_r(mag_word(q0 + w), mag_word(q0 + w + 1), bs);
-      if (32 * w + 32 <= lowb) f = 0u;
-      else if (32 * w < lowb) f &= ~((1u << (lowb - 32 * w)) - 1u);
+    const ProbDev& P = T.probs[tl.x];
+    const int L = P.L;
+    const int b = k & 1;
+    // ---- V for this tile (two threads per output, half of the moduli each)
+    if (ok) ok = mbar_wait(u_bar + b, ucnt[b] & 1u, &abort_flag, T.status);
+    ++ucnt[b];
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    {
+      const int e = t & 127, h = t >> 7;
+      const int lh = (L + 1) >> 1;
+      const int l0 = h * lh, l1 = min(L, l0 + lh);
+      const uint16_t* s_u = reinterpret_cast<const uint16_t*>(sm + lay.b_bytes + 2 * lay.a_region + b * lay.u_region);
+      uint8_t* gA = sm + lay.b_bytes + b * lay.a_region;
+      uint64_t sig = 0;
+#pragma unroll 4
+      for (int l = l0; l < l1; ++l) {
+        const uint32_t uu = s_u[l * 128 + e];
+        const uint4 pc = s_pc[l];
+        const uint32_t v = barrett32(uu * pc.z, pc.x, pc.y);
+        sig += (uint64_t)v * pc.y;
+        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(e, 2 * l, 128)) = bf16_pair(v & 127u, v >> 7);
+      }
+      if (h == 1)
+        for (int kk = 2 * L; kk < P.crt_kpad; kk += 2)
+          *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(e, kk, 128)) = 0u;
+      s_sig[(b * 2 + h) * 128 + e] = sig;
     }
-    const uint64_t x = (uint64_t)f + (uint64_t)((up && w == (lowb >> 5)) ? (1u << (lowb & 31)) : 0u) + c;
-    F[w] = (uint32_t)x;
-    c = (w < 2 * nl) ? (x >> 32) : 0u;
-    if (w == 2 * nl - 1 && c) ovf = true;    // rounded up to 2^p
-  }
-  if (ovf) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16(128, P.crt_npad);
+      const uint32_t tb = (uint32_t)P.crt_npad * 128;
+      const uint32_t d = tmem + (uint32_t)(b * tcols);
+      for (int q = 0; q < P.crt_kpad / 64; ++q) {
+        const uint64_t da = desc_sw128(sA0 + b * lay.a_region + q * 128 * 128);
+        const uint64_t db = desc_sw128(sB + q * tb);
 #pragma unroll
-    for (int w = 0; w < ND; ++w) F[w] = (w == 2 * nl - 1) ? 0x80000000u : 0u;
-    n += 1;
-  }
-  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
-  if (P.kind == 1) {
-    const uint64_t limb = ((uint64_t)F[1] << 32) | F[0];
-    double out;
-    const int bexp = eo - 1 + 1023;
-    const uint64_t sgn = neg ? (1ull << 63) : 0ull;
-    if (bexp >= 1 && bexp <= 2046) {
-      out = __longlong_as_double((long long)(sgn | ((uint64_t)bexp << 52) | ((limb >> 11) & ((1ull << 52) - 1))));
-    } else {
-      out = ldexp((double)(limb >> 11), eo - 53);
-      if (neg) out = -out;
+        for (int kk = 0; kk < 4; ++kk) umma_bf16(d, da + 2 * kk, db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
+      }
+      umma_commit(m_bar + b);
+      const int i3 = i + 2 * gridDim.x;                // u buffer b is free again
+      if (i3 < ntiles && tiles[i3].x == tl.x) issue_u(i3, b);
     }
-    P.c_f64[row * P.c_f64_ld + col] = out;
-    return;
+    if (pending) epilogue(prev, (k - 1) & 1);
+    pending = true;
+    prev = tl;
+    ++k;
   }
-  const int64_t coff = row * P.c_ld + col;
-#pragma unroll
-  for (int q = 0; q < ND / 2; ++q)
-    if (q < nl) P.c_limbs[(int64_t)q * P.c_ps + coff] = ((uint64_t)F[2 * q + 1] << 32) | F[2 * q];
-  P.c_exp[coff] = eo;
-  P.c_sign[coff] = neg ? 1 : 0;
+  if (pending && ok) epilogue(prev, (k - 1) & 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tcols) : "memory");
+  }
 }
 
 // Classes 0..8: one lane per output with ND = 8, 12, ..., 40 digits;
@@ -537,7 +831,32 @@ cudaError_t launch_crt1_t(const DevTables& t, const int4* blk, int nblk, int lma
   return cudaGetLastError();
 }
 
+template <int ND>
+cudaError_t crt_tc_attr() {
+  return cudaFuncSetAttribute(k_crt_tc<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 }  // namespace
+
+int crt_tc_smem_bytes(int cls, int kpad, int npad, int lmax, int /*nbuf*/) {
+  return (int)CtLayout(kCrtClasses[cls].dpl, kpad, npad, lmax).total;
+}
+
+cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int ntiles, int kpad_max,
+                          int npad_max, int lmax, int grid, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int smem = crt_tc_smem_bytes(cls, kpad_max, npad_max, lmax, 2);
+  const int4* tl = reinterpret_cast<const int4*>(tiles);
+  switch (cls) {
+#define OZ2_CRT_TC(i, nd) \
+  case i: k_crt_tc<nd><<<grid, kCtThreads, smem, s>>>(t, tl, ntiles, kpad_max, npad_max, lmax); break;
+    OZ2_CRT_TC(0, 8) OZ2_CRT_TC(1, 12) OZ2_CRT_TC(2, 16) OZ2_CRT_TC(3, 20) OZ2_CRT_TC(4, 24)
+    OZ2_CRT_TC(5, 28) OZ2_CRT_TC(6, 32) OZ2_CRT_TC(7, 36) OZ2_CRT_TC(8, 40)
+#undef OZ2_CRT_TC
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t init_crt_attributes() {
   cudaError_t e = crt1_attr<8>();
@@ -549,6 +868,15 @@ cudaError_t init_crt_attributes() {
   if (e == cudaSuccess) e = crt1_attr<32>();
   if (e == cudaSuccess) e = crt1_attr<36>();
   if (e == cudaSuccess) e = crt1_attr<40>();
+  if (e == cudaSuccess) e = crt_tc_attr<8>();
+  if (e == cudaSuccess) e = crt_tc_attr<12>();
+  if (e == cudaSuccess) e = crt_tc_attr<16>();
+  if (e == cudaSuccess) e = crt_tc_attr<20>();
+  if (e == cudaSuccess) e = crt_tc_attr<24>();
+  if (e == cudaSuccess) e = crt_tc_attr<28>();
+  if (e == cudaSuccess) e = crt_tc_attr<32>();
+  if (e == cudaSuccess) e = crt_tc_attr<36>();
+  if (e == cudaSuccess) e = crt_tc_attr<40>();
   if (e == cudaSuccess) e = crt_attr<16, 4>();
   if (e == cudaSuccess) e = crt_attr<16, 6>();
   if (e == cudaSuccess) e = crt_attr<32, 5>();

@@ -68,8 +68,13 @@ struct ProbDev {
   const int32_t* ext_scale;                                  // per-line extra exponent (backward)
   int32_t ext_scale_axis, pad2;
   int32_t DS;            // digit stride of the CRT tables (digits of the kernel class)
-  int32_t pad3;
+  int32_t crt_mode;      // 0: CUDA-core CRT; 1: column sums on the tensor cores
   uint32_t* dbg_chat;    // optional: [M*N][D32+1] sign word + |c_hat| digits
+  int32_t crt_kpad;      // tensor-core CRT: K = 2L padded to a multiple of 64
+  int32_t crt_npad;      // tensor-core CRT: 7-bit pieces of S padded to a multiple of 16
+  int32_t crt_np;        // tensor-core CRT: 7-bit pieces of S (columns of Y)
+  int32_t pad4;
+  int64_t upitch;        // row pitch of u [L][upitch]: M*N rounded up to a multiple of 8
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -135,6 +140,10 @@ cudaError_t launch_gemm_simt(const DevTables& t, const int32_t* unit_list, int n
                              cudaStream_t s);
 cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int nblk, int lmax,
                        cudaStream_t s);
+// Tensor-core CRT for one-lane class `cls` (0..8): tiles of 128 outputs.
+cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int ntiles, int kpad_max,
+                          int npad_max, int lmax, int grid, cudaStream_t s);
+int crt_tc_smem_bytes(int cls, int kpad_max, int npad_max, int lmax, int nbuf);
 
 // Internal plan variants used by the binary64 mode.
 struct PlanExtra {

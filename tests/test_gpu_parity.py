@@ -46,6 +46,7 @@ def run_gpu(ozk, A, B, p, debug=True, **kw):
     torch.cuda.synchronize()
     off, kp = plan.layout()
     G, L = plan.info["G"], plan.info["L"]
+    upitch = -(-(M * N) // 8) * 8
     w = ws.cpu().numpy()
 
     def region(o_, dtype, n):
@@ -56,7 +57,7 @@ def run_gpu(ozk, A, B, p, debug=True, **kw):
         "e": region(off[0], np.int32, M), "f": region(off[1], np.int32, N),
         "pa": region(off[2], np.uint16, G * M * kp).reshape(G, M, kp)[:, :, :K],
         "pb": region(off[3], np.uint16, G * N * kp).reshape(G, N, kp)[:, :, :K],
-        "u": region(off[4], np.uint16, L * M * N).reshape(L, M, N),
+        "u": region(off[4], np.uint16, L * upitch).reshape(L, upitch)[:, :M * N].reshape(L, M, N),
     }
     if debug:
         ch = chat.cpu().numpy().view(np.uint32)
@@ -129,7 +130,7 @@ def test_engines_and_schedules_agree(ozk):
     A = synth.mp_matrix(rng, 200, 96, 300, -10, 10)
     B = synth.mp_matrix(rng, 96, 300, 300, -10, 10)
     base = run_gpu(ozk, A, B, 300, debug=False)
-    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}):
+    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}, {"crt_engine": 1}):
         other = run_gpu(ozk, A, B, 300, debug=False, **kw)
         assert np.array_equal(other["u"], base["u"]), kw
         for key in ("limbs", "exp", "sign"):
@@ -188,6 +189,20 @@ def test_zero_lines_and_tiny_shapes(ozk):
         assert_full_parity(ozk, A, B, p)
 
 
+@pytest.mark.parametrize("p", [300, 700])
+def test_crt_engines_bit_exact(ozk, p):
+    """The CUDA-core CRT (default) and the tensor-core CRT give the same CRT
+    integers and outputs, and both match the oracle."""
+    rng = np.random.Generator(np.random.PCG64(2010 + p))
+    A = synth.mp_matrix(rng, 140, 60, p, -30, 30)
+    B = synth.mp_matrix(rng, 60, 20, p, -30, 30)
+    got_tc, ref = assert_full_parity(ozk, A, B, p, truth=False)
+    got_cc = run_gpu(ozk, A, B, p, crt_engine=1)
+    assert all(got_cc["chat"][i, j] == ref["chat"][i, j] for i in range(140) for j in range(20))
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got_cc["C"][key], got_tc["C"][key])
+
+
 def test_cancellation_to_zero(ozk):
     """x * y + (-x) * y = 0 exactly: the CRT integer is 0 and the output zero."""
     rng = np.random.Generator(np.random.PCG64(2006))
@@ -231,7 +246,10 @@ def test_gemm_1024_p256_sampled(ozk):
 
 def test_batched_and_graph(ozk):
     rng = np.random.Generator(np.random.PCG64(2007))
-    shapes = [(70, 300, 90, 113), (129, 40, 200, 256), (33, 260, 17, 512), (5, 5, 5, 53)]
+    # p = 1024 needs more CRT digits than the tensor-core CRT takes: both CRT
+    # paths run in one batch
+    shapes = [(70, 300, 90, 113), (129, 40, 200, 256), (33, 260, 17, 512), (5, 5, 5, 53),
+              (40, 30, 50, 1024)]
     mats = []
     for (M, N, K, p) in shapes:
         mats.append((synth.mp_matrix(rng, M, K, p, -8, 8), synth.mp_matrix(rng, K, N, p, -8, 8)))
