@@ -326,6 +326,102 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_other(args):
+    """Measurements of the other workloads (one GPU): batched, autograd, large."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as ozk
+    from paper_2609_27831_gb300 import autograd as ag
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for s_ in range(steps):
+            flush.fill_(s_ & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "data": "synthetic", "impl": "ours"}
+    if args.workload == "batched64":
+        probs = synth.batched_problems(64, 1002)
+        shapes = [(M, N, K, p) for (M, N, K, p, _, _) in probs]
+        trip = [(ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev), ozk.MPMatrix.empty(M, N, p, dev))
+                for (M, N, K, p, A, B) in probs]
+        work = sum(2.0 * M * N * K for (M, N, K, p) in shapes)
+        plan_g = ozk.Plan(shapes)
+        ws_g = plan_g.workspace(dev)
+        s = torch.cuda.Stream(dev)
+        with torch.cuda.stream(s):
+            g = plan_g.graph(trip, ws_g, s)
+        ms_graph = timed(lambda: g.launch(stream), args.steps, args.warmup)
+        ms_grouped = timed(lambda: plan_g.execute_batched(trip, ws_g, stream), args.steps, args.warmup)
+        del ws_g
+        torch.cuda.empty_cache()
+        plan_p = ozk.Plan(shapes, schedule=1)
+        ws_p = plan_p.workspace(dev)
+        ms_plain = timed(lambda: plan_p.execute_batched(trip, ws_p, stream), args.steps, args.warmup)
+        plan_p.check()
+        out.update({"value": work / (ms_graph / 1e3), "ms_per_step": ms_graph,
+                    "config": {"workload": "batched64", "problems": 64, "M_N_K": "log-uniform [128, 2048]",
+                               "p": [113, 256, 512], "gemms": sum(1 for _ in shapes)},
+                    "batched": {"graph_ms": ms_graph, "grouped_ms": ms_grouped, "plain_ms": ms_plain,
+                                "speedup_vs_plain": ms_plain / ms_graph,
+                                "plain": "one GEMM launch per modulus per problem (other stages grouped)"}})
+    elif args.workload == "dgemm4096_autograd":
+        X, Y, G = synth.fp64_workload(4096, 1003)
+        xa = torch.tensor(X, device=dev, requires_grad=True)
+        ya = torch.tensor(Y, device=dev, requires_grad=True)
+        gt = torch.tensor(G, device=dev)
+
+        def step():
+            xa.grad = None
+            ya.grad = None
+            ag.ozaki_matmul(xa, ya).backward(gt)
+        ms = timed(step, args.steps, args.warmup)
+        n = 4096
+        out.update({"value": 3 * 2.0 * n ** 3 / (ms / 1e3), "ms_per_step": ms,
+                    "config": {"workload": "dgemm4096_autograd", "M": n, "N": n, "K": n, "p": 53,
+                               "step": "forward C = AB and backward dA, dB (3 products)"}})
+    else:
+        M, N, K, p, lo, hi = {"gemm_4096_p2048": (4096, 4096, 4096, 2048, -64, 64),
+                              "gemm_8192_p53": (8192, 8192, 8192, 53, -8, 8),
+                              "gemm_4096_p53": (4096, 4096, 4096, 53, -8, 8),
+                              "gemm_2048_p512": (2048, 2048, 2048, 512, -8, 8)}[args.workload]
+        A, B = synth.workload_single(M, N, K, p, lo, hi, 1004)
+        dA, dB = ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev)
+        del A, B
+        dC = ozk.MPMatrix.empty(M, N, p, dev)
+        plan = ozk.Plan((M, N, K, p), timing=1)
+        ws = plan.workspace(dev)
+        ms = timed(lambda: plan.execute(dA, dB, dC, ws), args.steps, args.warmup)
+        plan.check()
+        st = plan.timings()
+        out.update({"value": 2.0 * M * N * K / (ms / 1e3), "ms_per_step": ms,
+                    "config": {"workload": args.workload, "M": M, "N": N, "K": K, "p": p, "t": plan.info["t"],
+                               "moduli": plan.info["L"], "gemms": plan.info["G"],
+                               "workspace_gb": round(plan.workspace_bytes / 1e9, 2)},
+                    "stage_ms": {k: round(v, 3) for k, v in st.items()},
+                    "plane_gemm_tflops": round(2.0 * M * N * K * plan.info["G"] / (st["gemm"] / 1e3) / 1e12, 1)})
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
@@ -359,11 +455,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rounds", type=int, default=2)
+    ap.add_argument("--workload", default="gemm_1024_p256",
+                    choices=["gemm_1024_p256", "batched64", "dgemm4096_autograd", "gemm_4096_p2048",
+                             "gemm_8192_p53", "gemm_4096_p53", "gemm_2048_p512"])
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "gemm_1024_p256":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -98,6 +98,9 @@ typedef struct {
   int crt_engine; /* 0: CRT on the CUDA cores (default); 1: CRT column sums as an exact bf16
                      GEMM on the tensor cores where 2L <= 256, the accumulator has <= 40 digits
                      and the tables fit in shared memory (CUDA cores otherwise) */
+  int res_engine; /* 0: residues on the CUDA cores (default); 1: residues as an exact bf16 GEMM of
+                     the bytes of a_hat with a table of centered 2^(8b) mod m on the tensor cores
+                     where the table has <= 256 rows and <= 256 bytes (CUDA cores otherwise) */
 } ozaki2_opts;
 
 /* Facts about a plan (all computed on the host at plan creation). */

@@ -25,7 +25,7 @@ class Mat(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("guard_bits", C.c_int), ("t_bits", C.c_int), ("engine", C.c_int),
                 ("k_chunk", C.c_int), ("grid", C.c_int), ("schedule", C.c_int),
-                ("timing", C.c_int), ("crt_engine", C.c_int)]
+                ("timing", C.c_int), ("crt_engine", C.c_int), ("res_engine", C.c_int)]
 
 
 class Info(C.Structure):

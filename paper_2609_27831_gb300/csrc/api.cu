@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <tuple>
 #include <vector>
 
@@ -159,6 +160,15 @@ struct ProbHost {
   bool skip_a, skip_b;         // planes of that side are written by the caller
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls)
   int crt_kpad, crt_npad, crt_np;
+  int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
+};
+
+// Tensor-core residue table [npad][kpad] (bf16 bits): row l (one-limb) =
+// cen(2^(8 b) mod m_l); rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
+// base-128 halves of cen(2^(8 b) mod m_l).
+struct ResTable {
+  int L, kpad, npad;
+  std::vector<uint16_t> bits;
 };
 
 struct ListRef {
@@ -195,6 +205,9 @@ struct DevState {
   std::vector<int> crt_off;    // per problem, uint32 offset in the pool
   ListRef tct[9];               // tensor-core CRT tile lists (smem = kpad_max, lmax = L max)
   int tct_npad[9] = {0};
+  ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
+  int rtt_npad = 0;
+  std::vector<void*> res_tab;   // per problem: device address of its residue table
   std::vector<void*> crt_tab;   // per problem: device address of its tensor-core CRT table
 };
 
@@ -211,6 +224,7 @@ struct ozaki2_plan_s {
   ozaki2_opts opts{};
   std::vector<oz2::ProbHost> probs;
   std::vector<oz2::CrtHost> crts;
+  std::vector<oz2::ResTable> rtabs;
   int lmax = 0, w16max = 0;
   size_t ws_bytes = 0, ef_bytes = 0;
   int64_t total_units = 0, total_jobs = 0;
@@ -355,6 +369,54 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
       }
     }
   }
+  {
+    // tensor-core residues (byte GEMM); opt-in through opts.res_engine
+    const int nb = (h.t + 1 + 7) / 8;
+    const int kpad = (int)align_up((size_t)nb, 64);
+    const int npad = (int)align_up((size_t)(h.L1 + 2 * (L - h.L1)), 16);
+    h.res_mode = (o.res_engine == 1 && kpad <= 256 && npad <= 256 &&
+                  residue_tc_smem_bytes(kpad, npad, L) <= 227 * 1024) ? 1 : 0;
+    h.res_kpad = kpad;
+    h.res_npad = npad;
+    h.res_key = -1;
+    if (h.res_mode) {
+      for (size_t i = 0; i < pl->rtabs.size(); ++i)
+        if (pl->rtabs[i].L == L && pl->rtabs[i].kpad == kpad) h.res_key = (int)i;
+      if (h.res_key < 0) {
+        ResTable rt;
+        rt.L = L; rt.kpad = kpad; rt.npad = npad;
+        rt.bits.assign((size_t)npad * kpad, 0);
+        auto bf = [](int x) -> uint16_t {   // exact for |x| <= 256
+          float f = (float)x;
+          uint32_t u;
+          std::memcpy(&u, &f, 4);
+          return (uint16_t)(u >> 16);
+        };
+        const auto& mlist = modulus_list();
+        for (int l = 0; l < L; ++l) {
+          const int m = (int)mlist[l];
+          int64_t pw = 1 % m;                          // 2^(8 b) mod m
+          for (int b = 0; b < nb; ++b) {
+            int c = (int)pw;
+            if (2 * c > m) c -= m;                     // centered
+            if (l < h.L1) {
+              rt.bits[(size_t)l * kpad + b] = bf(c);
+            } else {
+              int y = c & 127;
+              const int lo = y > 64 ? y - 128 : y;
+              const int hi = (c - lo) / 128;
+              const int r0 = h.L1 + 2 * (l - h.L1);
+              rt.bits[(size_t)r0 * kpad + b] = bf(lo);
+              rt.bits[(size_t)(r0 + 1) * kpad + b] = bf(hi);
+            }
+            pw = (pw << 8) % m;
+          }
+        }
+        pl->rtabs.push_back(std::move(rt));
+        h.res_key = (int)pl->rtabs.size() - 1;
+      }
+    }
+  }
   pl->probs.push_back(h);
   pl->lmax = std::max(pl->lmax, L);
   pl->w16max = std::max(pl->w16max, residue_class_w16(h.res_cls));
@@ -385,7 +447,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
-      (o.crt_engine != 0 && o.crt_engine != 1)) {
+      (o.crt_engine != 0 && o.crt_engine != 1) || (o.res_engine != 0 && o.res_engine != 1)) {
     delete pl;
     return OZ2_EINVAL;
   }
@@ -433,6 +495,9 @@ struct TableImage {
   size_t o_tct[9] = {0};
   int n_tct[9] = {0}, tct_kpad[9] = {0}, tct_npad[9] = {0}, tct_l[9] = {0};
   std::vector<size_t> o_tctab;
+  size_t o_rtt = 0;                 // tensor-core residue tile list
+  int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
+  std::vector<size_t> o_rtab;
 };
 
 // Host side of the device upload: modulus constants, residue digit tables,
@@ -465,12 +530,20 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       c.kmul01 = c.kmul12 = c.kfin = 1u;
     }
   }
-  std::vector<uint32_t> t16((size_t)pl->lmax * pl->w16max);
+  // byte tables of the residue kernel: row l holds, packed four bytes per
+  // word, the bytes 2^(8 b) mod m_l (one-limb) or, for two-limb moduli, the
+  // low bytes of 2^(8 b) mod m_l followed by their high bytes; w16max words
+  // per row (room for 2 * (w16max / 2) packed words)
+  std::vector<uint32_t> t16((size_t)pl->lmax * pl->w16max, 0u);
   for (int l = 0; l < pl->lmax; ++l) {
-    uint64_t v = 1 % ml[l];
-    for (int dd = 0; dd < pl->w16max; ++dd) {
-      t16[(size_t)l * pl->w16max + dd] = (uint32_t)v;
-      v = (v << 16) % ml[l];
+    const uint32_t m = ml[l];
+    const int w32 = pl->w16max / 2;
+    uint64_t v = 1 % m;
+    for (int byte = 0; byte < 4 * w32; ++byte) {
+      const int w = byte >> 2, sh = 8 * (byte & 3);
+      t16[(size_t)l * pl->w16max + w] |= (uint32_t)(v & 255u) << sh;
+      if (m > 255) t16[(size_t)l * pl->w16max + w32 + w] |= (uint32_t)(v >> 8) << sh;
+      v = (v << 8) % m;
     }
   }
   std::vector<uint32_t> pool;
@@ -499,12 +572,32 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   }
   const int nunits = (int)units.size();
   const int grid = std::max(1, std::min(pl->opts.grid > 0 ? pl->opts.grid : d.sms, nunits));
+  // greedy list scheduling: every unit, in (problem, modulus, tile) order, goes
+  // to the least-loaded CTA; the cost of a unit is its accumulation jobs times
+  // (K blocks per job + a fixed epilogue share)
+  std::vector<std::vector<int>> lists(grid);
+  {
+    using Load = std::pair<int64_t, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < grid; ++c) heap.push(Load(0, c));
+    for (int u = 0; u < nunits; ++u) {
+      const ProbHost& h = pl->probs[units[u].prob];
+      const int planes = units[u].ell < h.L1 ? 1 : 3;
+      const int64_t kblocks = (std::min<int64_t>(h.K, h.kchunk) + kBK - 1) / kBK;
+      const int64_t cost = (int64_t)planes * h.nchunks * (kblocks + 4);
+      Load top = heap.top();
+      heap.pop();
+      lists[top.second].push_back(u);
+      top.first += cost;
+      heap.push(top);
+    }
+  }
   std::vector<Unit> ordered;
   ordered.reserve(2 * units.size());
   std::vector<int32_t> cta_g(grid + 1, 0);
   for (int c = 0; c < grid; ++c) {
     cta_g[c] = (int)ordered.size();
-    for (int u = c; u < nunits; u += grid) ordered.push_back(units[u]);
+    for (int u : lists[c]) ordered.push_back(units[u]);
   }
   cta_g[grid] = (int)ordered.size();
   // plain schedule: one launch per (problem, modulus), appended after the
@@ -525,6 +618,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
   std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
+  std::vector<int4> rtt;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -533,13 +627,22 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     if (!h.skip_b)
       for (int64_t c = 0; c < h.N; c += 32)
         for (int kp = 0; kp < kparts; ++kp) scan_cols.push_back(make_int4(pi, 1 | (kp << 8), (int)c, kparts));
-    for (int side = 0; side < 2; ++side) {
+    for (int side = 0; h.res_mode == 1 && side < 2; ++side) {
+      if (side == 0 ? h.skip_a : h.skip_b) continue;
+      const int64_t R = side ? h.N : h.M;
+      for (int64_t r = 0; r < R; r += 4)
+        for (int64_t k = 0; k < h.K; k += 32) rtt.push_back(make_int4(pi, side, (int)r, (int)k));
+      ti.rtt_kpad = std::max(ti.rtt_kpad, h.res_kpad);
+      ti.rtt_npad = std::max(ti.rtt_npad, h.res_npad);
+      ti.rtt_l = std::max(ti.rtt_l, h.L);
+    }
+    for (int side = 0; h.res_mode == 0 && side < 2; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       for (int64_t r = 0; r < R; r += 8)
         for (int64_t k = 0; k < h.K; k += 64) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
-    ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
+    if (h.res_mode == 0) ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
     if (h.crt_mode == 1) {
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
@@ -580,6 +683,19 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     ti.o_tct[i] = ti.b.add(tct[i].data(), tct[i].size() * 16);
     ti.n_tct[i] = (int)tct[i].size();
   }
+  // consistency of the launch sizes with the problems they serve
+  for (const ProbHost& h : pl->probs) {
+    if (h.res_mode == 0 && !(h.skip_a && h.skip_b) && ti.res_l[h.res_cls] < h.L) return OZ2_EINTERNAL;
+    if (h.res_mode == 1 && (ti.rtt_l < h.L || ti.rtt_kpad < h.res_kpad || ti.rtt_npad < h.res_npad))
+      return OZ2_EINTERNAL;
+    if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
+    if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
+  }
+  ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
+  ti.n_rtt = (int)rtt.size();
+  ti.o_rtab.assign(pl->rtabs.size(), 0);
+  for (size_t i = 0; i < pl->rtabs.size(); ++i)
+    ti.o_rtab[i] = ti.b.add(pl->rtabs[i].bits.data(), pl->rtabs[i].bits.size() * 2, 1024);
   ti.o_tctab.assign(pl->crts.size(), 0);
   for (size_t i = 0; i < pl->crts.size(); ++i)
     if (!pl->crts[i].tc_table.empty())
@@ -621,6 +737,11 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     d.tct[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_tct[i]), ti.n_tct[i], ti.tct_kpad[i], ti.tct_l[i]};
     d.tct_npad[i] = ti.tct_npad[i];
   }
+  d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
+  d.rtt_npad = ti.rtt_npad;
+  d.res_tab.assign(pl->probs.size(), nullptr);
+  for (size_t i = 0; i < pl->probs.size(); ++i)
+    if (pl->probs[i].res_mode == 1) d.res_tab[i] = base + ti.o_rtab[pl->probs[i].res_key];
   d.crt_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
     if (pl->probs[i].crt_mode == 1) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
@@ -664,7 +785,7 @@ static int upload(ozaki2_plan_s* pl) {
 static int alloc_launch_block(LaunchBlock& lb, int count) {
   const size_t probs_bytes = align_up(sizeof(ProbDev) * count, 128);
   lb.tmap_off = probs_bytes;
-  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 4 * count;   // A planes, B planes, CRT table, u tiles
+  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 5 * count;   // A planes, B planes, CRT table, u tiles, residue table
   if (cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) { lb.d_mem = nullptr; return OZ2_ENOMEM; }
   if (cudaMallocHost(&lb.h_stage, lb.bytes) != cudaSuccess) { lb.h_stage = nullptr; return OZ2_ENOMEM; }
   if (cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming) != cudaSuccess) return OZ2_ECUDA;
@@ -724,6 +845,19 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.DS = h.DS;
     P.dbg_chat = pl->dbg_chat.empty() ? nullptr : pl->dbg_chat[i];
     P.upitch = (int64_t)align_up((size_t)(h.M * h.N), 8);
+    P.res_mode = h.res_mode;
+    P.res_kpad = h.res_kpad;
+    P.res_npad = h.res_npad;
+    if (h.res_mode == 1) {
+      const cuuint64_t dims[2] = {(cuuint64_t)h.res_kpad, (cuuint64_t)h.res_npad};
+      const cuuint64_t strides[1] = {(cuuint64_t)h.res_kpad * 2};
+      const cuuint32_t box[2] = {64u, (cuuint32_t)h.res_npad};
+      const cuuint32_t es[2] = {1u, 1u};
+      if (get_encode()(&tm[4 * count + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.res_tab[i], dims, strides,
+                       box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return OZ2_ECUDA;
+    }
     P.crt_mode = h.crt_mode;
     P.crt_kpad = h.crt_kpad;
     P.crt_npad = h.crt_npad;
@@ -788,6 +922,8 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[1], s));
   for (int c = 0; c < 6; ++c)
     if (d.res[c].n) OZ2_CU(launch_residues(tab, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
+  if (d.rtt.n)
+    OZ2_CU(launch_residues_tc(tab, d.rtt.ptr, d.rtt.n, d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
   if (pl->opts.engine == OZ2_ENGINE_SIMT) {
     DevTables t2 = tab;
@@ -808,7 +944,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
   for (int c = 0; c < 9; ++c)
     if (d.tct[c].n)
       OZ2_CU(launch_crt_tc(tab, c, d.tct[c].ptr, d.tct[c].n, d.tct[c].smem, d.tct_npad[c], d.tct[c].lmax,
-                           std::min(d.sms, d.tct[c].n), s));
+                           d.sms, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[4], s));
   return OZ2_OK;
 }
@@ -881,6 +1017,7 @@ int ozaki2_opts_default(ozaki2_opts* o) {
   o->schedule = OZ2_SCHED_GROUPED;
   o->timing = 0;
   o->crt_engine = 0;
+  o->res_engine = 0;
   return OZ2_OK;
 }
 
@@ -1110,7 +1247,7 @@ std::vector<int64_t> cache_key(int count, const ozaki2_problem* probs, const oza
   int dev = -1;
   cudaGetDevice(&dev);
   std::vector<int64_t> k{dev, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule, o.timing,
-                         o.crt_engine, count};
+                         o.crt_engine, o.res_engine, count};
   for (int i = 0; i < count; ++i) {
     k.push_back(probs[i].M);
     k.push_back(probs[i].N);
@@ -1254,7 +1391,7 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   if (rc) return rc;
   const size_t lb_off = align_up(ti.b.img.size(), 256);
   const size_t probs_bytes = align_up(sizeof(ProbDev), 128);
-  const size_t lb_bytes = probs_bytes + 4 * sizeof(CUtensorMap);
+  const size_t lb_bytes = probs_bytes + 5 * sizeof(CUtensorMap);
   if (lb_off + lb_bytes > sizeof(ozaki2_noalloc_tables)) return OZ2_ERANGE;
   install_table_image(pl, ti, nd->tables);
   const ozaki2_problem q{M, N, K, p, *A, *B, *C};

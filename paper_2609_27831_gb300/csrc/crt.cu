@@ -588,7 +588,7 @@ struct CtLayout {
 };
 
 template <int ND>
-__global__ void __launch_bounds__(kCtThreads, 1)
+__global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
     k_crt_tc(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, int kpad_max,
              int npad_max, int lmax) {
   using namespace tc;
@@ -847,9 +847,20 @@ cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int
   if (ntiles == 0) return cudaSuccess;
   const int smem = crt_tc_smem_bytes(cls, kpad_max, npad_max, lmax, 2);
   const int4* tl = reinterpret_cast<const int4*>(tiles);
+  const int sms = grid;
   switch (cls) {
-#define OZ2_CRT_TC(i, nd) \
-  case i: k_crt_tc<nd><<<grid, kCtThreads, smem, s>>>(t, tl, ntiles, kpad_max, npad_max, lmax); break;
+#define OZ2_CRT_TC(i, nd)                                                                              \
+  case i: {                                                                                           \
+    int per_sm = 1;                                                                                   \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_crt_tc<nd>, kCtThreads, smem) != cudaSuccess) \
+      per_sm = 1;                                                                                     \
+    per_sm = per_sm < 1 ? 1 : per_sm;                                                                 \
+    const int cap = 512 / (2 * crt_tc_tmem_cols(npad_max));                                           \
+    per_sm = per_sm > cap ? cap : per_sm;                                                             \
+    const int g = ntiles < sms * per_sm ? ntiles : sms * per_sm;                                      \
+    k_crt_tc<nd><<<g, kCtThreads, smem, s>>>(t, tl, ntiles, kpad_max, npad_max, lmax);                \
+    break;                                                                                            \
+  }
     OZ2_CRT_TC(0, 8) OZ2_CRT_TC(1, 12) OZ2_CRT_TC(2, 16) OZ2_CRT_TC(3, 20) OZ2_CRT_TC(4, 24)
     OZ2_CRT_TC(5, 28) OZ2_CRT_TC(6, 32) OZ2_CRT_TC(7, 36) OZ2_CRT_TC(8, 40)
 #undef OZ2_CRT_TC

@@ -281,7 +281,7 @@ int ozaki2_dgemm_fwd(int64_t M, int64_t N, int64_t K, const double* A, int64_t l
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_mu);
     const std::vector<int64_t> key{dev, M, N, K, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule,
-                                    o.crt_engine};
+                                    o.crt_engine, o.res_engine};
     auto it = g_nocache.find(key);
     if (it == g_nocache.end()) {
       ozaki2_cache_s* c = nullptr;

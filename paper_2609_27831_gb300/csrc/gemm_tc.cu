@@ -58,7 +58,13 @@ __device__ __forceinline__ uint32_t fmod_small(float x, float mf, float rcp) {
   const float q = rintf(x * rcp);
   float r = fmaf(-q, mf, x);
   r = r < 0.f ? r + mf : r;
-  return static_cast<uint32_t>(r);
+  // exact float -> int of 0 <= r < 2^23 without a conversion instruction
+  return __float_as_uint(r + 8388608.0f) - 0x4B000000u;
+}
+
+// exact int -> float of 0 <= x < 2^23 without a conversion instruction
+__device__ __forceinline__ float small_u2f(uint32_t x) {
+  return __uint_as_float(0x4B000000u + x) - 8388608.0f;
 }
 
 // One accumulation job: plane `plane` of unit `u` over K chunk `chunk`.
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           for (int i = 0; i < 32; ++i) {
             uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
             if (j.kmul != 1u) r = barrett32(r * j.kmul, mc.m, mc.mu);
-            v[i] = __float_as_uint((float)r);
+            v[i] = __float_as_uint(small_u2f(r));
           }
           tmem_st32(tbase + (uint32_t)(c * 32), v);
         } else {

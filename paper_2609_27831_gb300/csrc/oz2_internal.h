@@ -75,6 +75,10 @@ struct ProbDev {
   int32_t crt_np;        // tensor-core CRT: 7-bit pieces of S (columns of Y)
   int32_t pad4;
   int64_t upitch;        // row pitch of u [L][upitch]: M*N rounded up to a multiple of 8
+  int32_t res_mode;      // 0: residues on the CUDA cores; 1: byte GEMM on the tensor cores
+  int32_t res_kpad;      // tensor-core residues: bytes of a (t+1)-bit integer, padded to 64
+  int32_t res_npad;      // tensor-core residues: table rows L1 + 2 (L - L1), padded to 16
+  int32_t pad5;
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -142,8 +146,12 @@ cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int
                        cudaStream_t s);
 // Tensor-core CRT for one-lane class `cls` (0..8): tiles of 128 outputs.
 cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int ntiles, int kpad_max,
-                          int npad_max, int lmax, int grid, cudaStream_t s);
+                          int npad_max, int lmax, int sms, cudaStream_t s);
 int crt_tc_smem_bytes(int cls, int kpad_max, int npad_max, int lmax, int nbuf);
+// Tensor-core residues: persistent tiles of 4 lines x 32 k.
+cudaError_t launch_residues_tc(const DevTables& t, const int32_t* tiles, int ntiles, int kpad_max, int npad_max,
+                               int lmax, int sms, cudaStream_t s);
+int residue_tc_smem_bytes(int kpad, int npad, int lmax);
 
 // Internal plan variants used by the binary64 mode.
 struct PlanExtra {

@@ -4,9 +4,11 @@
 // bf16 int8-range planes in the K-major layout of the plane GEMM (Sec. 4.3,
 // incl. the balanced base-128 split of two-limb residues, Eq. 4-5).
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <climits>
 
 #include "oz2_internal.h"
+#include "tc_ptx.cuh"
 
 namespace oz2 {
 
@@ -120,8 +122,14 @@ __device__ __forceinline__ bool element_digits(const uint32_t* __restrict__ limb
   return true;
 }
 
+__device__ __forceinline__ uint32_t bf16_pair_u(uint32_t lo, uint32_t hi) {   // two ints <= 256
+  return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
+}
+
 __device__ __forceinline__ uint32_t bf16_bits(int r) {
-  return __float_as_uint((float)r) >> 16;         // exact for |r| <= 256
+  // bf16 bits of a small integer (|r| <= 256, exact) without an int->float
+  // conversion: 1.5 * 2^23 + r has r in its low mantissa bits
+  return __float_as_uint(__int_as_float(0x4B400000 + r) - 12582912.0f) >> 16;
 }
 
 // Centered residue of a_hat (sign s) from |a_hat| mod m: symmetric except for
@@ -133,24 +141,61 @@ __device__ __forceinline__ int centered(uint32_t r, uint32_t m, bool neg) {
   return x;
 }
 
-// Two horizontally adjacent elements per thread (k and k + 1): the digit
-// table is read once for both, and each plane gets one 32-bit store of two
-// bf16 values.  Block: 32 x 8 threads = 64 columns x 8 rows of elements.
+// Words of |a_hat| = floor(sig 2^sh) + rnd for one element (32 bits each,
+// the round-half-even increment carried through the words).  A zero element
+// gives zero words.
+template <int W32>
+__device__ __forceinline__ void element_words(const uint32_t* __restrict__ limbs32, int64_t ps, int64_t off,
+                                              int nl, int exp_el, int e_line, int t, uint32_t (&wd)[W32]) {
+#pragma unroll
+  for (int w = 0; w < W32; ++w) wd[w] = 0u;
+  const int sh = exp_el - e_line + t - 64 * nl;   // <= t - 64 nl
+  const int B = 64 - sh;                          // bit of sig * 2^64 that is bit 0 of the magnitude
+  if (B - 1 >= 64 * nl + 64) return;              // |a| 2^(t - e) < 1/2: rounds to 0
+  const int ws = B >> 5, bs = B & 31;
+#pragma unroll
+  for (int w = 0; w < W32; ++w)
+    wd[w] = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws + w - 2), sig_word(limbs32, ps, off, nl, ws + w - 1), bs);
+  const int rbpos = B - 1;
+  const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
+  const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
+  uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
+  for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
+  uint32_t c = rb & ((sticky != 0u) | (wd[0] & 1u));
+#pragma unroll
+  for (int w = 0; w < W32; ++w) {                 // |a_hat| <= 2^t fits the W32 words
+    const uint32_t x = wd[w] + c;
+    c = (c && x == 0u) ? 1u : 0u;
+    wd[w] = x;
+  }
+}
+
+// Two horizontally adjacent elements per thread (k and k + 1).  The residue
+// of |a_hat| mod m is sum_b beta_b (2^(8 b) mod m) over its bytes beta_b
+// (Sec. 5.3's digit table, at byte granularity): one dp4a multiplies four
+// bytes of a word by four packed table bytes and accumulates in 32 bits.
+// Two-limb moduli use two byte tables (the low and high byte of
+// 2^(8 b) mod m < 2^14).  The table is read once for both elements, and each
+// plane gets one 32-bit store of two bf16 values.  Block: 32 x 8 threads =
+// 64 columns x 8 rows of elements.
 template <int W16>
 __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __restrict__ blk) {
-  extern __shared__ __align__(16) uint32_t s_t16[];   // [L][W16], then [L] x {m, mu, c24, 0}
+  constexpr int W32 = W16 / 2;
+  constexpr int RS = 2 * W32;                          // table row stride (words)
+  extern __shared__ __align__(16) uint32_t s_t8[];     // [L][RS] packed bytes, then [L] x {m, mu, 0, 0}
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
   const int side = b.y;
   const int L = P.L, L1 = P.L1;
-  uint4* s_mc = reinterpret_cast<uint4*>(s_t16 + L * W16);
-  for (int i = threadIdx.y * 32 + threadIdx.x; i < L * W16; i += 256) {
-    const int l = i / W16, d = i - l * W16;
-    s_t16[i] = T.t16[(int64_t)l * T.w16max + d];
+  uint4* s_mc = reinterpret_cast<uint4*>(s_t8 + L * RS);
+  for (int i = threadIdx.y * 32 + threadIdx.x; i < L * RS; i += 256) {
+    const int l = i / RS, d = i - l * RS;         // low bytes [0, W32), high bytes [W32, 2 W32)
+    const int src = d < W32 ? d : (T.w16max >> 1) + (d - W32);
+    s_t8[i] = T.t16[(int64_t)l * T.w16max + src];
   }
   for (int l = threadIdx.y * 32 + threadIdx.x; l < L; l += 256) {
     const ModConst mc = T.mods[l];
-    s_mc[l] = make_uint4(mc.m, mc.mu, mc.c24, 0u);
+    s_mc[l] = make_uint4(mc.m, mc.mu, 0u, 0u);
   }
   __syncthreads();
   const int R = side ? P.N : P.M;
@@ -170,27 +215,21 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
   const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
   const int e_line = side ? P.f[r] : P.e[r];
 
-  uint32_t d0[W16], d1[W16];
+  uint32_t w0[W32], w1[W32];
   bool n0 = false, n1 = false;
-  {
-    const bool nz = __ldg(limbs + (int64_t)(nl - 1) * ps + off0) != 0ull;
-    if (nz) {
-      element_digits<W16>(limbs32, ps, off0, nl, __ldg(exps + off0), e_line, P.t, d0);
-      n0 = __ldg(signs + off0) != 0;
-    } else {
+  if (__ldg(limbs + (int64_t)(nl - 1) * ps + off0) != 0ull) {
+    element_words<W32>(limbs32, ps, off0, nl, __ldg(exps + off0), e_line, P.t, w0);
+    n0 = __ldg(signs + off0) != 0;
+  } else {
 #pragma unroll
-      for (int d = 0; d < W16; ++d) d0[d] = 0u;
-    }
+    for (int w = 0; w < W32; ++w) w0[w] = 0u;
   }
-  {
-    const bool nz = two && __ldg(limbs + (int64_t)(nl - 1) * ps + off1) != 0ull;
-    if (nz) {
-      element_digits<W16>(limbs32, ps, off1, nl, __ldg(exps + off1), e_line, P.t, d1);
-      n1 = __ldg(signs + off1) != 0;
-    } else {
+  if (two && __ldg(limbs + (int64_t)(nl - 1) * ps + off1) != 0ull) {
+    element_words<W32>(limbs32, ps, off1, nl, __ldg(exps + off1), e_line, P.t, w1);
+    n1 = __ldg(signs + off1) != 0;
+  } else {
 #pragma unroll
-      for (int d = 0; d < W16; ++d) d1[d] = 0u;
-    }
+    for (int w = 0; w < W32; ++w) w1[w] = 0u;
   }
 
   uint16_t* planes = side ? P.pb : P.pa;
@@ -203,34 +242,43 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
   };
   for (int l = 0; l < L; ++l) {
     const uint4 mcv = s_mc[l];
-    struct { uint32_t m, mu, c24; } mc{mcv.x, mcv.y, mcv.z};
-    const uint4* tl = reinterpret_cast<const uint4*>(s_t16 + l * W16);
+    const uint32_t m = mcv.x, mu = mcv.y;
+    const uint2* tl = reinterpret_cast<const uint2*>(s_t8 + l * RS);
     uint32_t r0, r1;
     if (l < L1) {
-      uint32_t a0 = 0u, a1 = 0u;   // digits < 2^16, table < 2^8, <= 132 terms: < 2^32
+      uint32_t a0 = 0u, a1 = 0u;   // <= 4 W32 bytes * 255 * 255 < 2^32
 #pragma unroll
-      for (int q = 0; q < W16 / 4; ++q) {
-        const uint4 t4 = tl[q];
-        a0 += d0[4 * q] * t4.x + d0[4 * q + 1] * t4.y + d0[4 * q + 2] * t4.z + d0[4 * q + 3] * t4.w;
-        a1 += d1[4 * q] * t4.x + d1[4 * q + 1] * t4.y + d1[4 * q + 2] * t4.z + d1[4 * q + 3] * t4.w;
+      for (int q = 0; q < W32 / 2; ++q) {
+        const uint2 t2 = tl[q];
+        a0 = __dp4a(w0[2 * q], t2.x, a0);
+        a0 = __dp4a(w0[2 * q + 1], t2.y, a0);
+        a1 = __dp4a(w1[2 * q], t2.x, a1);
+        a1 = __dp4a(w1[2 * q + 1], t2.y, a1);
       }
-      r0 = barrett32(a0, mc.m, mc.mu);
-      r1 = barrett32(a1, mc.m, mc.mu);
+      r0 = barrett32(a0, m, mu);
+      r1 = barrett32(a1, m, mu);
     } else {
-      uint64_t a0 = 0ull, a1 = 0ull;   // < 2^30 * 132 < 2^38
+      // low and high table bytes: x = s_lo + 256 s_hi < 2^32
+      uint32_t l0 = 0u, l1 = 0u, h0 = 0u, h1 = 0u;
+      const uint2* th = tl + W32 / 2;
 #pragma unroll
-      for (int q = 0; q < W16 / 4; ++q) {
-        const uint4 t4 = tl[q];
-        a0 += (uint64_t)d0[4 * q] * t4.x + (uint64_t)d0[4 * q + 1] * t4.y +
-              (uint64_t)d0[4 * q + 2] * t4.z + (uint64_t)d0[4 * q + 3] * t4.w;
-        a1 += (uint64_t)d1[4 * q] * t4.x + (uint64_t)d1[4 * q + 1] * t4.y +
-              (uint64_t)d1[4 * q + 2] * t4.z + (uint64_t)d1[4 * q + 3] * t4.w;
+      for (int q = 0; q < W32 / 2; ++q) {
+        const uint2 t2 = tl[q];
+        const uint2 u2 = th[q];
+        l0 = __dp4a(w0[2 * q], t2.x, l0);
+        l0 = __dp4a(w0[2 * q + 1], t2.y, l0);
+        l1 = __dp4a(w1[2 * q], t2.x, l1);
+        l1 = __dp4a(w1[2 * q + 1], t2.y, l1);
+        h0 = __dp4a(w0[2 * q], u2.x, h0);
+        h0 = __dp4a(w0[2 * q + 1], u2.y, h0);
+        h1 = __dp4a(w1[2 * q], u2.x, h1);
+        h1 = __dp4a(w1[2 * q + 1], u2.y, h1);
       }
-      r0 = barrett32((uint32_t)(a0 >> 24) * mc.c24 + (uint32_t)(a0 & 0xffffffu), mc.m, mc.mu);
-      r1 = barrett32((uint32_t)(a1 >> 24) * mc.c24 + (uint32_t)(a1 & 0xffffffu), mc.m, mc.mu);
+      r0 = barrett32(l0 + (h0 << 8), m, mu);
+      r1 = barrett32(l1 + (h1 << 8), m, mu);
     }
-    const int x0 = centered(r0, mc.m, n0);
-    const int x1 = centered(r1, mc.m, n1);
+    const int x0 = centered(r0, m, n0);
+    const int x1 = centered(r1, m, n1);
     if (l < L1) {
       put(x0, x1);                                   // plane l
     } else {
@@ -244,6 +292,288 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
       put(lo0 + hi0, lo1 + hi1);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Residues on the tensor cores.  With the bytes beta_b of |a_hat| (with the
+// rounding increment) and the centered table T[j][b] = cen(2^(8 b) mod m_l)
+// (one-limb moduli; |T| <= 127) or its balanced base-128 halves
+// (two-limb moduli: T = T0 + 128 T1, |T0| <= 64, |T1| <= 63),
+//   Y[e][j] = sum_b beta_b T[j][b]   ==  |a_hat| (mod m_l)  (or its halves),
+// one GEMM per tile of 128 elements with K = bytes of a (t+1)-bit integer.
+// Products are below 2^15 and sums below 2^15 * K < 2^24 for K < 512 bytes,
+// so bf16 operands and the fp32 TMEM accumulator are exact.  The epilogue
+// reduces each column mod m (fp32 reciprocal + fma, exact), applies the sign,
+// centers, splits two-limb residues and writes the bf16 planes.
+//
+// Persistent CTAs, 8 warps, every warp in every phase: warps 0-3 build the
+// bytes of tile k (one element per thread), thread 0 issues its MMA into TMEM
+// slot k & 1, then all warps run the epilogue of tile k - 1 (the two warps of
+// a TMEM lane quadrant take the two halves of the columns).
+// Tile: 4 lines x 32 consecutive k (lines = rows of A or columns of B); entry
+// {problem, side, first line, first k}, tiles of one problem contiguous.
+// ---------------------------------------------------------------------------
+constexpr int kRtThreads = 256;
+
+struct RtLayout {
+  uint32_t b_bytes, a_region, small_off, total;
+  __host__ __device__ RtLayout(int kpad, int npad, int lmax) {
+    b_bytes = (uint32_t)npad * kpad * 2;
+    a_region = ((uint32_t)128 * kpad * 2 + 1023u) & ~1023u;
+    small_off = b_bytes + 2 * a_region;
+    // small: s_mc [lmax] float4 {m, 1/m, kind, 0}, s_neg [2][128] u8, 4 barriers, tmem slot
+    total = 1024 + small_off + (uint32_t)lmax * 16 + 256 + 4 * 8 + 16;
+  }
+};
+
+__host__ __device__ inline int rt_tmem_cols(int npad) {
+  int c = 32;
+  while (c < npad) c <<= 1;
+  return c;
+}
+
+// fp32 exact integer y (|y| < 2^24) -> y mod m in [0, m), as a float
+__device__ __forceinline__ float fmodf_exact(float y, float mf, float rcp) {
+  const float q = rintf(y * rcp);
+  float r = fmaf(-q, mf, y);
+  return r < 0.f ? r + mf : r;
+}
+
+__global__ void __launch_bounds__(kRtThreads, 2)
+    k_residue_tc(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, int kpad_max,
+                 int npad_max, int lmax) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const RtLayout lay(kpad_max, npad_max, lmax);
+  const uint32_t sB = base;
+  const uint32_t sA0 = base + lay.b_bytes;
+  uint8_t* small = sm + lay.small_off;
+  float4* s_mc = reinterpret_cast<float4*>(small);                       // [lmax]
+  uint8_t* s_neg = small + lmax * 16;                                    // [2][128]: 1 negative, 2 zero
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_neg + 256);
+  uint64_t* b_bar = bars;
+  uint64_t* m_bar = bars + 1;        // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int tcols = rt_tmem_cols(npad_max);
+  if (t == 0) {
+    for (int i = 0; i < 3; ++i) mbar_init(bars + i, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int abort_flag = 0;
+  uint32_t bcnt = 0, mcnt[2] = {0, 0};
+  bool ok = true;
+
+  auto epilogue = [&](int4 tp, int s) {
+    const ProbDev& P = T.probs[tp.x];
+    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status);
+    ++mcnt[s];
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    const int quad = warp & 3, hh = warp >> 2;
+    const int er = quad * 32 + lane;                  // TMEM lane = element of the tile
+    const int side = tp.y;
+    const int R = side ? P.N : P.M;
+    const int line = tp.z + quad, k = tp.w + lane;
+    const int L1 = P.L1, L = P.L;
+    const int ncols = L1 + 2 * (L - L1);
+    const int cmid = ((ncols + 63) / 64) * 32;        // never splits a two-limb column pair
+    const int c0 = hh * cmid, c1 = min(ncols, c0 + cmid);
+    const bool valid = ok && line < R && k < P.K;
+    const uint8_t fl = s_neg[s * 128 + er];
+    const bool neg = (fl & 1) != 0;
+    uint16_t* planes = side ? P.pb : P.pa;
+    const int64_t pstride = (int64_t)R * P.Kp;
+    uint16_t* dst = planes + (int64_t)line * P.Kp + k;
+    const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * tcols);
+    auto centered_bits = [&](float rf, float mf) -> float {
+      float x = (2.f * rf > mf) ? rf - mf : rf;      // (-m/2, m/2] of |a_hat| mod m
+      if (neg) x = -x;
+      if (2.f * x == -mf) x = -x;                    // tie of the even modulus stays +m/2
+      return x;
+    };
+    if (ok) {
+      for (int c = c0; c < c1; c += 32) {
+        uint32_t v[32];
+        tmem_ld32(trow + (uint32_t)c, v);
+        if (!valid) continue;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int col = c + q;
+          if (col < c1) {
+            if (col < L1) {
+              const float4 mc = s_mc[col];
+              const float x = centered_bits(fmodf_exact(__uint_as_float(v[q]), mc.x, mc.y), mc.x);
+              dst[(int64_t)col * pstride] = (uint16_t)(__float_as_uint(x) >> 16);
+            } else if (((col - L1) & 1) == 0 && q + 1 < 32) {
+              const int l = L1 + ((col - L1) >> 1);
+              const float4 mc = s_mc[l];
+              const float r0 = fmodf_exact(__uint_as_float(v[q]), mc.x, mc.y);
+              const float r1 = fmodf_exact(__uint_as_float(v[q + 1]), mc.x, mc.y);
+              const float x = centered_bits(fmodf_exact(fmaf(128.f, r1, r0), mc.x, mc.y), mc.x);
+              const int xi = (int)x;
+              const int y0 = xi & 127;
+              const int lo = y0 > 64 ? y0 - 128 : y0;  // cen(r mod 128)
+              const int hi = (xi - lo) >> 7;
+              const int64_t g = L1 + 3 * (l - L1);
+              dst[g * pstride] = (uint16_t)(__float_as_uint((float)lo) >> 16);
+              dst[(g + 1) * pstride] = (uint16_t)(__float_as_uint((float)hi) >> 16);
+              dst[(g + 2) * pstride] = (uint16_t)(__float_as_uint((float)(lo + hi)) >> 16);
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  };
+
+  int cur = -1;
+  int k = 0;
+  bool pending = false;
+  int4 prev = make_int4(0, 0, 0, 0);
+  for (int i = blockIdx.x;; i += gridDim.x) {
+    const bool have = i < ntiles;
+    const int4 tl = have ? tiles[i] : make_int4(-1, 0, 0, 0);
+    if (!have || tl.x != cur) {
+      if (pending) {
+        epilogue(prev, (k - 1) & 1);
+        pending = false;
+      }
+      if (!have || !ok) break;
+      const ProbDev& P = T.probs[tl.x];
+      for (int l = t; l < P.L; l += kRtThreads) {
+        const ModConst& mc = T.mods[l];
+        s_mc[l] = make_float4((float)mc.m, mc.rcp, 0.f, 0.f);
+      }
+      __syncthreads();
+      if (t == 0) {
+        const int kb = P.res_kpad / 64;
+        const uint32_t tb = (uint32_t)P.res_npad * 128;
+        mbar_expect_tx(b_bar, tb * kb);
+        for (int q = 0; q < kb; ++q)
+          tma_load_2d(sB + q * tb, T.tmaps + 4 * T.count + tl.x, smem_u32(b_bar), q * 64, 0);
+      }
+      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status);
+      ok = __syncthreads_and(ok);
+      ++bcnt;
+      cur = tl.x;
+      if (!ok) break;
+    }
+    const ProbDev& P = T.probs[tl.x];
+    const int b = k & 1;
+    // ---- bytes of |a_hat| for the 128 elements of this tile (warps 0-3)
+    if (t < 128) {
+      const int side = tl.y;
+      const int R = side ? P.N : P.M;
+      const int line = tl.z + (t >> 5), kk = tl.w + (t & 31);
+      uint8_t* gA = sm + lay.b_bytes + b * lay.a_region;
+      const int nw = P.res_kpad >> 2;                  // 32-bit words covering the K positions
+      uint8_t flag = 2;
+      uint32_t carry = 0;
+      int ws = 0, bs = 0, nl = P.nl;
+      const uint32_t* limbs32 = nullptr;
+      int64_t ps = 0, off = 0;
+      bool nz = false;
+      if (line < R && kk < P.K) {
+        const uint64_t* limbs = side ? P.b_limbs : P.a_limbs;
+        ps = side ? P.b_ps : P.a_ps;
+        off = side ? ((int64_t)kk * P.b_ld + line) : ((int64_t)line * P.a_ld + kk);
+        nz = __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull;
+        if (nz) {
+          const int e_line = side ? P.f[line] : P.e[line];
+          const int ex = __ldg((side ? P.b_exp : P.a_exp) + off);
+          const int sh = ex - e_line + P.t - 64 * nl;
+          const int Bb = 64 - sh;                      // bit of sig * 2^64 that is bit 0 of the magnitude
+          limbs32 = reinterpret_cast<const uint32_t*>(limbs);
+          if (Bb - 1 >= 64 * nl + 64) {
+            nz = false;                                // rounds to zero
+          } else {
+            ws = Bb >> 5;
+            bs = Bb & 31;
+            const int rbpos = Bb - 1;
+            const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
+            const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
+            uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
+            for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
+            const uint32_t w0 = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws - 2),
+                                                sig_word(limbs32, ps, off, nl, ws - 1), bs);
+            carry = rb & ((sticky != 0u) | (w0 & 1u));
+            flag = __ldg((side ? P.b_sign : P.a_sign) + off) ? 1 : 0;
+          }
+        }
+      }
+      for (int w = 0; w < nw; ++w) {
+        uint32_t x = 0u;
+        if (nz) {
+          const uint64_t y = (uint64_t)__funnelshift_r(sig_word(limbs32, ps, off, nl, ws + w - 2),
+                                                       sig_word(limbs32, ps, off, nl, ws + w - 1), bs) + carry;
+          x = (uint32_t)y;
+          carry = (uint32_t)(y >> 32);
+        }
+        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w, 128)) = bf16_pair_u(x & 0xffu, (x >> 8) & 0xffu);
+        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w + 2, 128)) = bf16_pair_u((x >> 16) & 0xffu, x >> 24);
+      }
+      s_neg[b * 128 + t] = nz ? flag : 2;
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16(128, P.res_npad);
+      const uint32_t tb = (uint32_t)P.res_npad * 128;
+      const uint32_t d = tmem + (uint32_t)(b * tcols);
+      for (int q = 0; q < P.res_kpad / 64; ++q) {
+        const uint64_t da = desc_sw128(sA0 + b * lay.a_region + q * 128 * 128);
+        const uint64_t db = desc_sw128(sB + q * tb);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) umma_bf16(d, da + 2 * kk, db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
+      }
+      umma_commit(m_bar + b);
+    }
+    if (pending) epilogue(prev, (k - 1) & 1);
+    pending = true;
+    prev = tl;
+    ++k;
+  }
+  if (pending && ok) epilogue(prev, (k - 1) & 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tcols) : "memory");
+  }
+}
+
+int residue_tc_smem_bytes(int kpad, int npad, int lmax) { return (int)RtLayout(kpad, npad, lmax).total; }
+
+cudaError_t launch_residues_tc(const DevTables& t, const int32_t* tiles, int ntiles, int kpad_max, int npad_max,
+                               int lmax, int sms, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int smem = residue_tc_smem_bytes(kpad_max, npad_max, lmax);
+  // several persistent CTAs per SM hide each other's load latency; TMEM caps them
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_residue_tc, kRtThreads, smem) != cudaSuccess)
+    per_sm = 1;
+  per_sm = std::max(1, std::min(per_sm, 512 / (2 * rt_tmem_cols(npad_max))));
+  const int grid = std::min(ntiles, sms * per_sm);
+  k_residue_tc<<<grid, kRtThreads, smem, s>>>(t, reinterpret_cast<const int4*>(tiles), ntiles, kpad_max, npad_max,
+                                              lmax);
+  return cudaGetLastError();
 }
 
 static const int kResidueW16[] = {8, 12, 20, 36, 68, 132};
@@ -281,6 +611,7 @@ cudaError_t init_prep_attributes() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residue<36>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residue<68>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residue<132>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_residue_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   return e;
 }
 

@@ -25,6 +25,8 @@ def main():
     ap.add_argument("--workload", default="gemm_1024_p256", choices=sorted(WORKLOADS))
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--schedule", type=int, default=0)
+    ap.add_argument("--res-engine", type=int, default=0)
+    ap.add_argument("--crt-engine", type=int, default=0)
     args = ap.parse_args()
     import torch
 
@@ -36,7 +38,8 @@ def main():
     A, B = synth.workload_single(M, N, K, p, lo, hi, seed)
     dA, dB = ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B)
     C = ozk.MPMatrix.empty(M, N, p)
-    plan = ozk.Plan((M, N, K, p), schedule=args.schedule)
+    plan = ozk.Plan((M, N, K, p), schedule=args.schedule, res_engine=args.res_engine,
+                    crt_engine=args.crt_engine)
     ws = plan.workspace()
     for _ in range(args.reps):
         plan.execute(dA, dB, C, ws)

@@ -130,7 +130,8 @@ def test_engines_and_schedules_agree(ozk):
     A = synth.mp_matrix(rng, 200, 96, 300, -10, 10)
     B = synth.mp_matrix(rng, 96, 300, 300, -10, 10)
     base = run_gpu(ozk, A, B, 300, debug=False)
-    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}, {"crt_engine": 1}):
+    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}, {"crt_engine": 1},
+               {"res_engine": 1}):
         other = run_gpu(ozk, A, B, 300, debug=False, **kw)
         assert np.array_equal(other["u"], base["u"]), kw
         for key in ("limbs", "exp", "sign"):
@@ -189,6 +190,15 @@ def test_zero_lines_and_tiny_shapes(ozk):
         assert_full_parity(ozk, A, B, p)
 
 
+def test_p2048_small(ozk):
+    """p = 2048 (the largest precision): 32-limb inputs, 132-digit residue
+    class, two-limb moduli, 32-lane CRT groups; every stage bit-exact."""
+    rng = np.random.Generator(np.random.PCG64(2030))
+    A = synth.mp_matrix(rng, 20, 24, 2048, -64, 64)
+    B = synth.mp_matrix(rng, 24, 18, 2048, -64, 64)
+    assert_full_parity(ozk, A, B, 2048, truth=False)
+
+
 @pytest.mark.parametrize("p", [300, 700])
 def test_crt_engines_bit_exact(ozk, p):
     """The CUDA-core CRT (default) and the tensor-core CRT give the same CRT
@@ -201,6 +211,17 @@ def test_crt_engines_bit_exact(ozk, p):
     assert all(got_cc["chat"][i, j] == ref["chat"][i, j] for i in range(140) for j in range(20))
     for key in ("limbs", "exp", "sign"):
         assert np.array_equal(got_cc["C"][key], got_tc["C"][key])
+
+
+@pytest.mark.parametrize("shape", [(130, 70, 45, 256), (33, 9, 100, 53), (64, 129, 17, 500), (5, 3, 1, 2)])
+def test_residue_engines_bit_exact(ozk, shape):
+    """Residues on the tensor cores (byte GEMM, opt-in) give the oracle's planes
+    bit for bit on both sides, with ragged tiles, zero lines and two-limb moduli."""
+    M, N, K, p = shape
+    rng = np.random.Generator(np.random.PCG64(2020 + M))
+    A = synth.zero_rows(synth.mp_matrix(rng, M, K, p, -40, 40), [1])
+    B = synth.zero_cols(synth.mp_matrix(rng, K, N, p, -40, 40), [0])
+    assert_full_parity(ozk, A, B, p, truth=False, res_engine=1)
 
 
 def test_cancellation_to_zero(ozk):
