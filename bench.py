@@ -62,6 +62,23 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dev) -> float:
+    """The largest of every rank's x (the slowest replica sets the job time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, work_per_rank: float, ms: float) -> float:
+    """Whole-job rate: every rank runs its own replica of the workload, so the
+    job does world x work in the max-over-ranks time."""
+    return world * work_per_rank / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling while the timed region runs."""
 
@@ -156,6 +173,77 @@ def cpu_oracle_rate(rounds: int = 2):
 
 
 # ---------------------------------------------------------------------------
+# roofline of each stage
+# ---------------------------------------------------------------------------
+
+# Integer-pipe rates per SM per clock used as the ALU peaks: 64 lanes of
+# 32-bit integer multiply-add per SM per clock (the FMA-heavy pipe: 4 SM
+# sub-partitions x 16 lanes); a 32 x 32 -> 64-bit multiply-add (IMAD.WIDE)
+# takes two passes, and a 4-way byte dot product (dp4a) one pass for four
+# multiply-adds.  Times 152 SMs and the maximum SM clock.
+SMS = 152
+IMAD_WIDE_PER_SM_CLK = 32
+DP4A_MACS_PER_SM_CLK = 64 * 4
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the committed kernels on the same workload; the source
+# summaries are under profiles/.  A kernel changed since its capture has None.
+NCU_TRAFFIC = {
+    "gemm_1024_p256": {"residues": 445.094912e6, "gemm": 564.684032e6, "crt": 168.133376e6},
+}
+
+
+def stage_rooflines(info, M, N, K, p, stages, workload):
+    """Achieved vs peak for each stage's kernel, from its algorithmic work.
+
+    residues: byte multiply-adds sum_b beta_b (2^(8b) mod m) over the
+      ceil((t+1)/8) bytes of each integerized entry, one per modulus for the
+      L1 one-limb moduli and two (the low and high table byte) for the L2
+      two-limb moduli: (M+N) K ceil((t+1)/8) (L1 + 2 L2), against the dp4a
+      multiply-add rate.
+    gemm: 2 M N K G flops of the G plane products, against the measured bf16
+      tensor peak (the integer planes are exact bf16 operands).
+    crt: the 32 x 32 -> 64-bit multiply-adds of sum_l v_l M_l, L per output
+      and digit of M_l: M N L ceil(bits(P)/32), against the IMAD.WIDE rate.
+    scan: the bytes of the two exponent vectors' inputs, against HBM.
+    """
+    peaks, src = load_peaks()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    L, L1, G, t = info["L"], info["L1"], info["G"], info["t"]
+    L2 = L - L1
+    md = info["crt_digits"] - 2
+    traffic = NCU_TRAFFIC.get(workload, {})
+    out = {}
+
+    def alu(name, kernel, ops, rate, what):
+        ach = ops / (stages[name] / 1e3) / 1e12
+        out[name] = {"kernel": kernel, "bound": "alu", "achieved": round(ach, 2),
+                     "peak": round(rate / 1e12, 2), "unit": f"T{what}/s", "frac": round(ach * 1e12 / rate, 4),
+                     "peak_source": f"{SMS} SMs x {rate / SMS / clk:.0f} {what}/SM/clk x "
+                                    f"{clk / 1e6:.0f} MHz (derived)",
+                     "traffic": traffic.get(name)}
+
+    res_macs = (M + N) * K * math.ceil((t + 1) / 8) * (L1 + 2 * L2)
+    alu("residues", "k_residue (integerize + byte-table residues + plane writes)", res_macs,
+        SMS * DP4A_MACS_PER_SM_CLK * clk, "byteMAC")
+    alu("crt", "k_crt1 / k_crt (direct CRT sum + quotient correction + rounding)", M * N * L * md,
+        SMS * IMAD_WIDE_PER_SM_CLK * clk, "imad64")
+    flops = 2.0 * M * N * K * G
+    ach = flops / (stages["gemm"] / 1e3) / 1e12
+    pk = float(peaks["bf16_tflops"])
+    out["gemm"] = {"kernel": "k_gemm_tc (plane GEMMs + fused mod-reduce)", "bound": "tensor",
+                   "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
+                   "peak_source": f"bf16_tflops burst, {src}", "traffic": traffic.get("gemm")}
+    scan_bytes = (M * K + K * N) * (8 + 4)      # top limb + exponent of every entry
+    ach = scan_bytes / (stages["scan"] / 1e3) / 1e9
+    pk = float(peaks["hbm_gbs"])
+    out["scan"] = {"kernel": "k_scan (shared exponents)", "bound": "hbm", "achieved": round(ach, 1),
+                   "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
+                   "peak_source": f"hbm_gbs, {src}", "traffic": traffic.get("scan")}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -221,13 +309,9 @@ def run_ours(args):
     clocks = clk.stop()
     plan.check()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
     work = 2.0 * M * N * K
-    value = world * work / (ms / 1e3)
+    value = replica_value(world, work, ms)
 
     # ---- end to end through the C ABI with host buffers
     hA = {k: torch.from_numpy(np.ascontiguousarray(A[k]).view(np.int64) if k == "limbs" else
@@ -259,47 +343,17 @@ def run_ours(args):
         e_en[s].record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e_st, e_en)) / args.steps
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e_st, e_en)) / args.steps, dev)
 
     # ---- roofline of the dominant kernel (library stage events on the launch stream)
     med = {k: statistics.median(s_[k] for s_ in stage) for k in stage[0]}
-    peaks, peak_src = load_peaks()
-    info = plan.info
-    G, L = info["G"], info["L"]
-    nl = (p + 63) // 64
-    in_bytes = (M * K + K * N) * (8 * nl + 4 + 1)
-    plane_bytes = 2 * G * (M + N) * K
     stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
+    kernels = stage_rooflines(plan.info, M, N, K, p, stages, WORK["workload"])
     dom = max(stages, key=stages.get)
-    if dom == "gemm":
-        flops = 2.0 * M * N * K * G
-        ach = flops / (stages["gemm"] / 1e3) / 1e12
-        pk = peaks["bf16_tflops"]
-        roof = {"kernel": "k_gemm_tc (plane GEMMs + fused mod-reduce)", "bound": "tensor",
-                "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
-                "peak_source": f"bf16_tflops burst, {peak_src}"}
-    else:
-        if dom == "residues":
-            alg = in_bytes + plane_bytes
-            kern = "k_residue (integerize + centered residues + plane writes)"
-        elif dom == "crt":
-            alg = 2 * L * M * N + M * N * (8 * nl + 5)
-            kern = "k_crt (direct CRT + rounding)"
-        else:
-            alg = in_bytes
-            kern = "k_scan"
-        ach = alg / (stages[dom] / 1e3) / 1e9
-        pk = peaks["hbm_gbs"]
-        roof = {"kernel": kern, "bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
-                "frac": round(ach / pk, 4), "peak_source": f"hbm_gbs, {peak_src}"}
-    roof["traffic"] = None
+    roof = dict(kernels[dom])
     roof["stage_ms"] = {k: round(v, 4) for k, v in stages.items()}
-    # plane-GEMM rate against the bf16 tensor peak (the engine: see the design notes)
-    gemm_tflops = 2.0 * M * N * K * G / (stages["gemm"] / 1e3) / 1e12
+    info = plan.info
+    gemm_tflops = 2.0 * M * N * K * info["G"] / (stages["gemm"] / 1e3) / 1e12
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -309,9 +363,10 @@ def run_ours(args):
         "config": {"workload": WORK["workload"], "M": M, "N": N, "K": K, "p": p,
                    "exp_range": WORK["exp_range"], "t": info["t"], "moduli": L, "gemms": G,
                    "parallelism": f"replicas{world}", "l2": "flushed (512 MiB write between steps)"},
-        "e2e": {"value": world * work / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": replica_value(world, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": roof,
+        "kernels": {k: v for k, v in kernels.items() if k != dom},
         "plane_gemm_tflops": round(gemm_tflops, 1),
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,

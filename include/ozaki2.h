@@ -95,9 +95,15 @@ typedef struct {
   int grid;       /* persistent CTAs of the grouped GEMM; 0 = one per SM */
   int schedule;   /* OZ2_SCHED_* */
   int timing;     /* nonzero: record per-stage CUDA events (ozaki2_last_timings) */
-  int crt_engine; /* 0: CRT on the CUDA cores (default); 1: CRT column sums as an exact bf16
+  int crt_engine; /* 0: automatic (default): engine 2 where the CRT accumulator needs more than
+                     40 32-bit digits, CUDA cores otherwise; 1: CRT column sums as an exact bf16
                      GEMM on the tensor cores where 2L <= 256, the accumulator has <= 40 digits
-                     and the tables fit in shared memory (CUDA cores otherwise) */
+                     and the tables fit in shared memory (CUDA cores otherwise); 2: the column
+                     sums of any length as an exact bf16 GEMM on the tensor cores, written as
+                     group sums to the workspace and finished on the CUDA cores, where
+                     32 <= L <= 448 and M N >= 128 (CUDA cores otherwise); the reduced-product
+                     region then holds v_l = (c mod m_l) M_l^{-1} mod m_l, M_l = P / m_l;
+                     3: the CRT on the CUDA cores only */
   int res_engine; /* 0: residues on the CUDA cores (default); 1: residues as an exact bf16 GEMM of
                      the bytes of a_hat with a table of centered 2^(8b) mod m on the tensor cores
                      where the table has <= 256 rows and <= 256 bytes (CUDA cores otherwise) */
@@ -114,6 +120,8 @@ typedef struct {
   int units;        /* (modulus, output tile) work units over all problems */
   int jobs;         /* tensor-core accumulation jobs over all problems */
   size_t workspace_bytes;
+  int crt_mode;     /* CRT path of problem 0: 0 CUDA cores, 1 tensor-core column sums in one
+                       kernel, 2 tensor-core sums of any length plus the finish (see crt_engine) */
 } ozaki2_info;
 
 typedef struct {
@@ -169,7 +177,8 @@ OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digit
      off[2] A planes  bf16 [G][M][Kp]   (Kp = K rounded up to 8; K-major)
      off[3] B planes  bf16 [G][N][Kp]   (transposed: column j of B is row j)
      off[4] reduced products u  uint16 [L][MNp], MNp = M*N rounded up to a multiple of 8
-            (row-major (i, j) within each modulus row)
+            (row-major (i, j) within each modulus row); with crt_engine 2 the
+            values v_l = u_l M_l^{-1} mod m_l instead
    and *kp = Kp.  Plane order: one-limb moduli in plane order, then for each
    two-limb modulus the planes r0, r1, r0 + r1 (balanced base-128 split). */
 OZ2_API int ozaki2_plan_layout(ozaki2_plan plan, int prob, size_t off[5], int64_t* kp);

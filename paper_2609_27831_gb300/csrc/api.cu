@@ -146,7 +146,7 @@ struct CrtHost {
   std::vector<uint32_t> words;   // pool layout (see CrtView), DS-padded
   // tensor-core CRT table B [npad][kpad] (bf16 bits): B[j][2l] = M_l[j],
   // B[j][2l+1] = M_l[j-1], M_l[j] the 7-bit pieces of M_l
-  int kpad = 0, npad = 0, np = 0;
+  int kpad = 0, npad = 0, np = 0, rows = 0;   // rows: table rows allocated (>= npad)
   std::vector<uint16_t> tc_table;
 };
 
@@ -158,8 +158,10 @@ struct ProbHost {
   size_t off_e, off_f, off_pa, off_pb, off_u;   // workspace offsets
   int kind;                    // 0: limb output; 1: binary64 output
   bool skip_a, skip_b;         // planes of that side are written by the caller
-  int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls)
-  int crt_kpad, crt_npad, crt_np;
+  int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
+                               // 2: tensor-core sums to R digits, then the finish
+  int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp;
+  size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [2][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
 };
 
@@ -205,6 +207,8 @@ struct DevState {
   std::vector<int> crt_off;    // per problem, uint32 offset in the pool
   ListRef tct[9];               // tensor-core CRT tile lists (smem = kpad_max, lmax = L max)
   int tct_npad[9] = {0};
+  ListRef cmt;                  // tensor-core CRT sum tiles (smem = largest chunk width)
+  ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = groups max)
   ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
   int rtt_npad = 0;
   std::vector<void*> res_tab;   // per problem: device address of its residue table
@@ -338,13 +342,26 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int npad = (int)align_up((size_t)np, 16);
     const bool tc_ok = o.crt_engine == 1 && h.crt_cls <= 8 && kpad <= 256 && npad <= 256 &&
                        crt_tc_smem_bytes(h.crt_cls, kpad, npad, L, 1) <= 227 * 1024;
-    h.crt_mode = tc_ok ? 1 : 0;
+    // automatic choice: the tensor-core sums where the accumulator needs more
+    // than the 40 digits of the one-lane CUDA-core CRT (lane groups otherwise)
+    const bool want_mm = o.crt_engine == 2 || (o.crt_engine == 0 && h.crt_cls > 8);
+    // sums of any length: fp32 column sums exact for 2L 127^2 < 2^24, and V
+    // for 128 outputs (kpad bf16 each) plus the rings must fit in shared memory
+    // (the u copies are boxes of 32 moduli x 128 outputs: at least that many;
+    // V takes kpad / 2 of the 512 TMEM columns, two accumulator slots the rest)
+    const bool mm_ok = want_mm && 2 * L * 127 * 127 < (1 << 24) && L >= 32 && M * N >= 128 &&
+                       kpad / 2 + 2 * 32 <= 512;
+    h.crt_mode = tc_ok ? 1 : (mm_ok ? 2 : 0);
     h.crt_kpad = kpad;
     h.crt_npad = npad;
     h.crt_np = np;
-    if (tc_ok && c.tc_table.empty()) {
-      c.kpad = kpad; c.npad = npad; c.np = np;
-      c.tc_table.assign((size_t)npad * kpad, 0);
+    h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad) : 0;
+    h.crt_nchunk = mm_ok ? (npad + h.crt_cw - 1) / h.crt_cw : 0;
+    h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
+    const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
+    if (h.crt_mode != 0 && c.tc_table.empty()) {
+      c.kpad = kpad; c.npad = npad; c.np = np; c.rows = rows;
+      c.tc_table.assign((size_t)rows * kpad, 0);
       const auto& mlist = modulus_list();
       auto bf = [](uint32_t x) -> uint16_t {   // exact for x <= 256
         float f = (float)x;
@@ -434,6 +451,13 @@ static void layout_workspace(ozaki2_plan_s* pl) {
     h.off_pa = off; off += align_up(2 * (size_t)h.G * h.M * h.Kp, 256);
     h.off_pb = off; off += align_up(2 * (size_t)h.G * h.N * h.Kp, 256);
     h.off_u = off; off += align_up(2 * (size_t)h.L * align_up((size_t)(h.M * h.N), 8), 256);
+    h.off_q = h.off_sig = off;
+    if (h.crt_mode == 2) {
+      const size_t up = align_up((size_t)(h.M * h.N), 8);
+      off += align_up(4 * (size_t)h.crt_ngrp * 9 * up, 256);
+      h.off_sig = off;
+      off += align_up(16 * up, 256);
+    }
   }
   pl->ws_bytes = off;
 }
@@ -447,7 +471,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
-      (o.crt_engine != 0 && o.crt_engine != 1) || (o.res_engine != 0 && o.res_engine != 1)) {
+      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine != 0 && o.res_engine != 1)) {
     delete pl;
     return OZ2_EINVAL;
   }
@@ -495,6 +519,8 @@ struct TableImage {
   size_t o_tct[9] = {0};
   int n_tct[9] = {0}, tct_kpad[9] = {0}, tct_npad[9] = {0}, tct_l[9] = {0};
   std::vector<size_t> o_tctab;
+  size_t o_cmt = 0, o_finl = 0;     // tensor-core CRT sum tiles; finish blocks of long accumulators
+  int n_cmt = 0, cmt_cw = 0, n_finl = 0, finl_dmax = 0, finl_gmax = 0;
   size_t o_rtt = 0;                 // tensor-core residue tile list
   int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
   std::vector<size_t> o_rtab;
@@ -618,7 +644,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
   std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
-  std::vector<int4> rtt;
+  std::vector<int4> rtt, cmt, finl;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -650,6 +676,23 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.tct_kpad[h.crt_cls] = std::max(ti.tct_kpad[h.crt_cls], h.crt_kpad);
       ti.tct_npad[h.crt_cls] = std::max(ti.tct_npad[h.crt_cls], h.crt_npad);
       ti.tct_l[h.crt_cls] = std::max(ti.tct_l[h.crt_cls], h.L);
+    } else if (h.crt_mode == 2) {
+      // sums on the tensor cores, then the finish: one-lane classes in
+      // k_crt1 (its block list), longer accumulators in k_crt_fin_long
+      const int64_t nt = (h.M * h.N + 127) / 128;
+      if (nt > INT_MAX) return OZ2_ERANGE;
+      for (int64_t tt = 0; tt < nt; ++tt) cmt.push_back(make_int4(pi, (int)tt, 0, 0));
+      ti.cmt_cw = std::max(ti.cmt_cw, h.crt_cw);
+      if (h.crt_cls <= 8) {
+        const int epb = crt_class_elems_per_block(h.crt_cls);
+        for (int64_t bb = 0; bb < (h.M * h.N + epb - 1) / epb; ++bb)
+          crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
+        ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
+      } else {
+        for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
+        ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
+        ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
+      }
     } else {
       const int epb = crt_class_elems_per_block(h.crt_cls);
       const int64_t nb = (h.M * h.N + epb - 1) / epb;
@@ -690,7 +733,18 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       return OZ2_EINTERNAL;
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
+    if (h.crt_mode == 2 && (ti.cmt_cw < h.crt_cw || h.crt_cw % 32 != 0 || h.crt_kpad / 2 + 2 * h.crt_cw > 512 ||
+                            (h.crt_cls <= 8 ? ti.crt_l[h.crt_cls] < h.L
+                                            : (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
+      return OZ2_EINTERNAL;
   }
+  if (!cmt.empty() && crt_mm_smem_bytes(ti.cmt_cw, pl->lmax, nullptr) < 0) return OZ2_EINTERNAL;
+  if (!finl.empty() && 3 * ti.finl_dmax * 4 + (ti.finl_dmax + 2 * ti.finl_gmax) * 128 * 4 > 200 * 1024)
+    return OZ2_EINTERNAL;
+  ti.o_cmt = ti.b.add(cmt.data(), cmt.size() * 16);
+  ti.n_cmt = (int)cmt.size();
+  ti.o_finl = ti.b.add(finl.data(), finl.size() * 16);
+  ti.n_finl = (int)finl.size();
   ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
   ti.n_rtt = (int)rtt.size();
   ti.o_rtab.assign(pl->rtabs.size(), 0);
@@ -737,6 +791,8 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     d.tct[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_tct[i]), ti.n_tct[i], ti.tct_kpad[i], ti.tct_l[i]};
     d.tct_npad[i] = ti.tct_npad[i];
   }
+  d.cmt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt), ti.n_cmt, ti.cmt_cw, 0};
+  d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
   d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
   d.rtt_npad = ti.rtt_npad;
   d.res_tab.assign(pl->probs.size(), nullptr);
@@ -744,7 +800,7 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     if (pl->probs[i].res_mode == 1) d.res_tab[i] = base + ti.o_rtab[pl->probs[i].res_key];
   d.crt_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
-    if (pl->probs[i].crt_mode == 1) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
+    if (pl->probs[i].crt_mode != 0) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
   for (int i = 0; i < kCrtClassCount; ++i)
     d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_crt[i]), ti.n_crt[i], 0, ti.crt_l[i]};
 }
@@ -862,14 +918,22 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_kpad = h.crt_kpad;
     P.crt_npad = h.crt_npad;
     P.crt_np = h.crt_np;
+    P.crt_nchunk = h.crt_nchunk;
+    P.crt_cw = h.crt_cw;
+    P.crt_q = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_q) : nullptr;
+    P.crt_sig = h.crt_mode == 2 ? reinterpret_cast<uint64_t*>(ws + h.off_sig) : nullptr;
+    P.crt_ngrp = h.crt_ngrp;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
     if (rc) return rc;
     rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);
     if (rc) return rc;
-    if (h.crt_mode == 1) {
-      const cuuint64_t dims[2] = {(cuuint64_t)h.crt_kpad, (cuuint64_t)h.crt_npad};
+    if (h.crt_mode != 0) {
+      // mode 1: the whole table in K blocks; mode 2: K block x cw columns of
+      // a table padded to whole chunks
+      const int rows = pl->crts[h.crt_key].rows;
+      const cuuint64_t dims[2] = {(cuuint64_t)h.crt_kpad, (cuuint64_t)rows};
       const cuuint64_t strides[1] = {(cuuint64_t)h.crt_kpad * 2};
-      const cuuint32_t box[2] = {64u, (cuuint32_t)h.crt_npad};
+      const cuuint32_t box[2] = {64u, (cuuint32_t)(h.crt_mode == 1 ? h.crt_npad : h.crt_cw)};
       const cuuint32_t es[2] = {1u, 1u};
       if (get_encode()(&tm[2 * count + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.crt_tab[i], dims, strides,
                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -878,7 +942,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
       // u tiles: [L][upitch] uint16, boxes of 128 outputs x L moduli
       const cuuint64_t udims[2] = {(cuuint64_t)P.upitch, (cuuint64_t)h.L};
       const cuuint64_t ustr[1] = {(cuuint64_t)P.upitch * 2};
-      const cuuint32_t ubox[2] = {128u, (cuuint32_t)h.L};
+      const cuuint32_t ubox[2] = {128u, h.crt_mode == 1 ? (cuuint32_t)h.L : 32u};
       if (get_encode()(&tm[3 * count + i], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, P.u, udims, ustr, ubox, es,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -939,6 +1003,9 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     }
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
+  if (d.cmt.n)
+    OZ2_CU(launch_crt_mm(tab, d.cmt.ptr, d.cmt.n, d.cmt.smem, d.sms, s));
+  if (d.finl.n) OZ2_CU(launch_crt_finish_long(tab, d.finl.ptr, d.finl.n, d.finl.smem, d.finl.lmax, s));
   for (int c = 0; c < kCrtClassCount; ++c)
     if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
   for (int c = 0; c < 9; ++c)
@@ -1095,6 +1162,7 @@ int ozaki2_plan_info(ozaki2_plan pl, ozaki2_info* out) {
   out->units = (int)std::min<int64_t>(INT_MAX, pl->total_units);
   out->jobs = (int)std::min<int64_t>(INT_MAX, pl->total_jobs);
   out->workspace_bytes = pl->ws_bytes;
+  out->crt_mode = h.crt_mode;
   return OZ2_OK;
 }
 

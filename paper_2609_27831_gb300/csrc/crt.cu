@@ -282,11 +282,6 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   }
 }
 
-// The CRT and rounding of one output from R = (S + alpha~ (2^(32 D) - P)) mod
-// 2^(32 D), i.e. R in [0, 2P) (Sec. 4.4): subtract P once if R >= P, take the
-// signed representative, round |c_hat| 2^(e_i + f_j - 2t) to p bits and write
-// the output.  tab: [3][ND] digits of 2^(32 D) - P, 2^(32 D) - (floor(P/2) + 1)
-// and P.  s_mag: scratch column e of a [ND][ldm] digit array.
 template <int ND>
 __device__ __forceinline__ int compare_digits(const uint32_t (&R)[ND], const uint32_t* Y) {
   // sign of R - Y over ND digits, decided at the most significant differing digit
@@ -299,6 +294,92 @@ __device__ __forceinline__ int compare_digits(const uint32_t (&R)[ND], const uin
   return cmp;
 }
 
+// Round |c_hat| (nd digits in column e of s_mag, highest nonzero digit `top`,
+// -1 for zero) times 2^(e_i + f_j - 2t) to p bits, round-half-even, and write
+// output idx (limbs, exponent and sign, or a binary64 value).
+__device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t* s_mag, int ldm, int e, int nd,
+                                             int top, bool neg, int64_t idx) {
+  const int64_t row = idx / P.N, col = idx - row * P.N;
+  auto mag_word = [&](int w) -> uint32_t {
+    return (w >= 0 && w < nd) ? s_mag[w * ldm + e] : 0u;
+  };
+  const int p = P.p, nl = P.nl;
+  if (top < 0) {
+    if (P.kind == 1) {
+      P.c_f64[row * P.c_f64_ld + col] = 0.0;
+    } else {
+      const int64_t coff = row * P.c_ld + col;
+      for (int q = 0; q < nl; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
+      P.c_exp[coff] = 0;
+      P.c_sign[coff] = 0;
+    }
+    return;
+  }
+  int n = 32 * top + 32 - __clz(mag_word(top));
+  const int sh = n - p, rpos = sh - 1;
+  uint32_t up = 0;
+  if (rpos >= 0) {
+    const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
+    const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
+    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
+    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
+    up = rb & ((sticky != 0u) | lsb);
+  }
+  // the 2 nl output words: F = floor(|c_hat| 2^(64 nl - n)) with the low
+  // 64 nl - p bits cleared, plus the rounding increment at bit 64 nl - p
+  const int base = n - 64 * nl;
+  const int q0 = base >> 5, bs = base & 31;
+  const int lowb = 64 * nl - p;
+  const bool kind1 = P.kind == 1;
+  const int64_t coff = row * P.c_ld + col;
+  uint64_t c = 0;
+  uint32_t prev = 0;
+  uint64_t limb0 = 0;
+  for (int w = 0; w < 2 * nl; ++w) {
+    uint32_t f = __funnelshift_r(mag_word(q0 + w), mag_word(q0 + w + 1), bs);
+    if (32 * w + 32 <= lowb) f = 0u;
+    else if (32 * w < lowb) f &= ~((1u << (lowb - 32 * w)) - 1u);
+    const uint64_t x = (uint64_t)f + (uint64_t)((up && w == (lowb >> 5)) ? (1u << (lowb & 31)) : 0u) + c;
+    const uint32_t fw = (uint32_t)x;
+    c = x >> 32;
+    if (w & 1) {
+      const uint64_t limb = ((uint64_t)fw << 32) | prev;
+      if (kind1) limb0 = limb;
+      else P.c_limbs[(int64_t)(w >> 1) * P.c_ps + coff] = limb;
+    }
+    prev = fw;
+  }
+  if (c) {                                        // rounded up to 2^p: renormalise
+    n += 1;
+    if (!kind1) {
+      for (int q = 0; q < nl - 1; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
+      P.c_limbs[(int64_t)(nl - 1) * P.c_ps + coff] = 1ull << 63;
+    }
+    limb0 = 1ull << 63;
+  }
+  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
+  if (kind1) {
+    double out;
+    const int bexp = eo - 1 + 1023;
+    const uint64_t sgn = neg ? (1ull << 63) : 0ull;
+    if (bexp >= 1 && bexp <= 2046) {
+      out = __longlong_as_double((long long)(sgn | ((uint64_t)bexp << 52) | ((limb0 >> 11) & ((1ull << 52) - 1))));
+    } else {
+      out = ldexp((double)(limb0 >> 11), eo - 53);
+      if (neg) out = -out;
+    }
+    P.c_f64[row * P.c_f64_ld + col] = out;
+    return;
+  }
+  P.c_exp[coff] = eo;
+  P.c_sign[coff] = neg ? 1 : 0;
+}
+
+// The CRT and rounding of one output from R = (S + alpha~ (2^(32 D) - P)) mod
+// 2^(32 D), i.e. R in [0, 2P) (Sec. 4.4): subtract P once if R >= P, take the
+// signed representative, round |c_hat| 2^(e_i + f_j - 2t) to p bits and write
+// the output.  tab: [3][ND] digits of 2^(32 D) - P, 2^(32 D) - (floor(P/2) + 1)
+// and P.  s_mag: scratch column e of a [ND][ldm] digit array.
 template <int ND>
 __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], const uint32_t* s_tab,
                                            uint32_t* s_mag, int ldm, int e, int64_t idx, int32_t* status) {
@@ -351,83 +432,7 @@ __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], 
     s_mag[d * ldm + e] = R[d];
     if (R[d]) top = d;
   }
-  const int64_t row = idx / P.N, col = idx - row * P.N;
-  auto mag_word = [&](int w) -> uint32_t {
-    return (w >= 0 && w < ND) ? s_mag[w * ldm + e] : 0u;
-  };
-  const int p = P.p, nl = P.nl;
-  if (top < 0) {
-    if (P.kind == 1) {
-      P.c_f64[row * P.c_f64_ld + col] = 0.0;
-    } else {
-      const int64_t coff = row * P.c_ld + col;
-      for (int q = 0; q < nl; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
-      P.c_exp[coff] = 0;
-      P.c_sign[coff] = 0;
-    }
-    return;
-  }
-  int n = 32 * top + 32 - __clz(mag_word(top));
-  const int sh = n - p, rpos = sh - 1;
-  uint32_t up = 0;
-  if (rpos >= 0) {
-    const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
-    const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
-    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
-    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
-    up = rb & ((sticky != 0u) | lsb);
-  }
-  // the 2 nl output words: F = floor(|c_hat| 2^(64 nl - n)) with the low
-  // 64 nl - p bits cleared, plus the rounding increment at bit 64 nl - p
-  const int base = n - 64 * nl;
-  const int q0 = base >> 5, bs = base & 31;
-  const int lowb = 64 * nl - p;
-  const bool kind1 = P.kind == 1;
-  const int64_t coff = row * P.c_ld + col;
-  uint64_t c = 0;
-  uint32_t prev = 0;
-  uint64_t limb0 = 0;
-  bool ovf = false;
-  for (int w = 0; w < 2 * nl; ++w) {
-    uint32_t f = __funnelshift_r(mag_word(q0 + w), mag_word(q0 + w + 1), bs);
-    if (32 * w + 32 <= lowb) f = 0u;
-    else if (32 * w < lowb) f &= ~((1u << (lowb - 32 * w)) - 1u);
-    const uint64_t x = (uint64_t)f + (uint64_t)((up && w == (lowb >> 5)) ? (1u << (lowb & 31)) : 0u) + c;
-    const uint32_t fw = (uint32_t)x;
-    c = x >> 32;
-    if (w & 1) {
-      const uint64_t limb = ((uint64_t)fw << 32) | prev;
-      if (kind1) limb0 = limb;
-      else P.c_limbs[(int64_t)(w >> 1) * P.c_ps + coff] = limb;
-    }
-    prev = fw;
-  }
-  if (c) {                                        // rounded up to 2^p: renormalise
-    ovf = true;
-    n += 1;
-    if (!kind1) {
-      for (int q = 0; q < nl - 1; ++q) P.c_limbs[(int64_t)q * P.c_ps + coff] = 0ull;
-      P.c_limbs[(int64_t)(nl - 1) * P.c_ps + coff] = 1ull << 63;
-    }
-    limb0 = 1ull << 63;
-  }
-  (void)ovf;
-  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
-  if (kind1) {
-    double out;
-    const int bexp = eo - 1 + 1023;
-    const uint64_t sgn = neg ? (1ull << 63) : 0ull;
-    if (bexp >= 1 && bexp <= 2046) {
-      out = __longlong_as_double((long long)(sgn | ((uint64_t)bexp << 52) | ((limb0 >> 11) & ((1ull << 52) - 1))));
-    } else {
-      out = ldexp((double)(limb0 >> 11), eo - 53);
-      if (neg) out = -out;
-    }
-    P.c_f64[row * P.c_f64_ld + col] = out;
-    return;
-  }
-  P.c_exp[coff] = eo;
-  P.c_sign[coff] = neg ? 1 : 0;
+  crt_round_write(P, s_mag, ldm, e, ND, top, neg, idx);
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +444,56 @@ __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], 
 // the whole CRT and rounding of its output with the digits in registers and
 // sequential exact carries.
 // ---------------------------------------------------------------------------
+// R = (sum_g Q_g 2^(224 g) + alpha~ (2^(32 D) - P)) mod 2^(32 D) from the
+// group sums of the tensor-core CRT (crt_mode 2): group g holds 9 words
+// starting at word 7 g, so word d collects word d - 7 g of group g = d / 7
+// and, for d mod 7 < 2, word d - 7 (g - 1) of the group before.  Digits in
+// registers (D <= ND).
+template <int ND>
+__device__ __forceinline__ void crt_assemble_regs(const ProbDev& P, const CrtView& cv, int64_t idx,
+                                                  uint32_t (&R)[ND]) {
+  const int64_t up = P.upitch;
+  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx]) >> 32;
+  const int D = P.D32, ng = P.crt_ngrp;
+  uint32_t w0[ND], w1[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {                   // independent loads first
+    const int g = d / 7, k = d - 7 * g;
+    w0[d] = (d < D && g < ng) ? __ldg(P.crt_q + ((int64_t)g * 9 + k) * up + idx) : 0u;
+    w1[d] = (d < D && k < 2 && g >= 1 && g - 1 < ng) ? __ldg(P.crt_q + ((int64_t)(g - 1) * 9 + k + 7) * up + idx) : 0u;
+  }
+  uint64_t carry = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    R[d] = 0u;
+    if (d < D) {
+      const uint64_t x = carry + alpha * __ldg(cv.negP + d) + w0[d] + w1[d];
+      R[d] = (uint32_t)x;
+      carry = x >> 32;
+    }
+  }
+}
+
 constexpr int kEpb1 = 128;
+
+// acc[d] += sum_l v_l M_l[d] for the first NM digits (the rest of M_l is zero)
+template <int ND, int NM>
+__device__ __forceinline__ void crt1_sum(uint64_t (&acc)[ND], const uint16_t* s_v, const uint32_t* s_M,
+                                         int L, int e) {
+  static_assert(NM % 4 == 0 && NM <= ND, "digit columns in groups of four");
+  for (int l = 0; l < L; ++l) {
+    const uint32_t v = s_v[l * kEpb1 + e];
+    const uint4* mrow = reinterpret_cast<const uint4*>(s_M + l * ND);
+#pragma unroll
+    for (int q = 0; q < NM / 4; ++q) {
+      const uint4 m4 = mrow[q];
+      acc[4 * q + 0] += (uint64_t)v * m4.x;
+      acc[4 * q + 1] += (uint64_t)v * m4.y;
+      acc[4 * q + 2] += (uint64_t)v * m4.z;
+      acc[4 * q + 3] += (uint64_t)v * m4.w;
+    }
+  }
+}
 
 template <int ND>
 __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restrict__ blk) {
@@ -456,7 +510,9 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   uint32_t* s_mu = s_M + L * ND;                              // [L]
   uint32_t* s_tab = s_mu + L;                                 // [3][ND]: negP, negH1, P
   uint32_t* s_mag = s_tab + 3 * ND;                           // [ND][kEpb1]
-  for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
+  const bool from_r = P.crt_mode == 2;     // S already summed in chunks on the tensor cores
+  if (!from_r)
+    for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
   for (int i = threadIdx.x; i < ND; i += kEpb1) {
     s_tab[i] = __ldg(cv.negP + i);
     s_tab[ND + i] = __ldg(cv.negH1 + i);
@@ -464,7 +520,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   }
   // v_l = u_l M_l^{-1} mod m_l: 16-byte loads of 8 reduced products; a block
   // covers 16 x 8 = 128 outputs of 8 moduli per pass, independent loads first
-  {
+  if (!from_r) {
     const int lane8 = threadIdx.x & 15;                       // which 8 outputs
     const int lrow = threadIdx.x >> 4;                        // modulus within the pass
     const bool full = e0 + kEpb1 <= MN;
@@ -510,6 +566,12 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   const int e = threadIdx.x;
   const int64_t idx = e0 + e;
   if (idx >= MN) return;
+  if (from_r) {
+    uint32_t R[ND];
+    crt_assemble_regs<ND>(P, cv, idx, R);
+    crt_finish<ND>(P, R, s_tab, s_mag, kEpb1, e, idx, T.status);
+    return;
+  }
 
   // quotient estimate alpha~ in {alpha - 1, alpha}
   uint64_t sig = 0;
@@ -520,18 +582,9 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   uint64_t acc[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) acc[d] = (uint64_t)alpha * s_tab[d];
-  for (int l = 0; l < L; ++l) {
-    const uint32_t v = s_v[l * kEpb1 + e];
-    const uint4* mrow = reinterpret_cast<const uint4*>(s_M + l * ND);
-#pragma unroll
-    for (int q = 0; q < ND / 4; ++q) {
-      const uint4 m4 = mrow[q];
-      acc[4 * q + 0] += (uint64_t)v * m4.x;
-      acc[4 * q + 1] += (uint64_t)v * m4.y;
-      acc[4 * q + 2] += (uint64_t)v * m4.z;
-      acc[4 * q + 3] += (uint64_t)v * m4.w;
-    }
-  }
+  // M_l < P < 2^(32 (D - 2)): digits D - 2 and up of every M_l are zero
+  if (D - 2 <= ND - 4) crt1_sum<ND, ND - 4>(acc, s_v, s_M, L, e);
+  else crt1_sum<ND, ND>(acc, s_v, s_M, L, e);
   uint32_t R[ND];
   {
     uint64_t c = 0;
@@ -801,6 +854,429 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
   }
 }
 
+// ---------------------------------------------------------------------------
+// Finish of long accumulators (crt_mode 2, more than 40 digits): one thread
+// per output, R assembled from the tensor-core chunk sums into shared memory
+// as a [D][128] digit column per thread, then the same steps as crt_finish with
+// digit-serial carries: subtract P once if R >= P (R + (2^(32 D) - P) carries
+// out of digit D - 1 exactly when R >= P), the sign test against floor(P/2)
+// + 1, |c_hat| = P - x0 for negative results, and the rounding.
+// Block list entry: {problem, block of 128 outputs, 0, 0}.
+// ---------------------------------------------------------------------------
+constexpr int kFinThreads = 128;
+
+__global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const int4* __restrict__ blk) {
+  extern __shared__ __align__(16) uint32_t sf[];
+  const int4 b = blk[blockIdx.x];
+  const ProbDev& P = T.probs[b.x];
+  const int D = P.D32, ng = P.crt_ngrp;
+  const CrtView cv = crt_view(T.crt_pool, P);
+  uint32_t* s_P = sf;                   // [D]
+  uint32_t* s_negP = s_P + D;           // [D]
+  uint32_t* s_negH1 = s_negP + D;       // [D]
+  uint32_t* s_R = s_negH1 + D;          // [D][128]
+  uint32_t* s_W = s_R + D * kFinThreads;   // [2 ng][128]: words 7, 8 of every group
+  for (int i = threadIdx.x; i < D; i += kFinThreads) {
+    s_P[i] = __ldg(cv.P + i);
+    s_negP[i] = __ldg(cv.negP + i);
+    s_negH1[i] = __ldg(cv.negH1 + i);
+  }
+  __syncthreads();
+  const int e = threadIdx.x;
+  const int64_t idx = (int64_t)b.y * kFinThreads + e;
+  if (idx >= (int64_t)P.M * P.N) return;
+  const int64_t up = P.upitch;
+  // the group words, independent coalesced loads: words 0..6 of group d / 7
+  // in digit order, and the overlap words 7, 8 of every group
+#pragma unroll 8
+  for (int d = 0; d < D; ++d) {
+    const int g = d / 7;
+    s_R[d * kFinThreads + e] = g < ng ? __ldg(P.crt_q + ((int64_t)g * 9 + (d - 7 * g)) * up + idx) : 0u;
+  }
+#pragma unroll 4
+  for (int g = 0; g < ng; ++g) {
+    s_W[(2 * g) * kFinThreads + e] = __ldg(P.crt_q + ((int64_t)g * 9 + 7) * up + idx);
+    s_W[(2 * g + 1) * kFinThreads + e] = __ldg(P.crt_q + ((int64_t)g * 9 + 8) * up + idx);
+  }
+  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx]) >> 32;
+  // pass 1, least significant digit first: R = (S + alpha~ (2^(32 D) - P)) mod
+  // 2^(32 D), and the carries out of R + (2^(32 D) - P) (R >= P), of
+  // R + (2^(32 D) - floor(P/2) - 1) and of (R - P) + the same (the sign of the
+  // signed representative either way)
+  uint64_t carry = 0;
+  uint32_t c1 = 0, c3 = 0, c4 = 0;
+  for (int d = 0; d < D; ++d) {
+    const int g = d / 7, k = d - 7 * g;
+    uint64_t x = carry + alpha * s_negP[d] + s_R[d * kFinThreads + e];
+    if (k < 2 && g >= 1 && g - 1 < ng) x += s_W[(2 * (g - 1) + k) * kFinThreads + e];
+    const uint32_t r = (uint32_t)x;
+    carry = x >> 32;
+    s_R[d * kFinThreads + e] = r;
+    const uint64_t t1 = (uint64_t)r + s_negP[d] + c1;       // R - P
+    c1 = (uint32_t)(t1 >> 32);
+    const uint64_t t3 = (uint64_t)r + s_negH1[d] + c3;
+    c3 = (uint32_t)(t3 >> 32);
+    const uint64_t t4 = (uint64_t)(uint32_t)t1 + s_negH1[d] + c4;
+    c4 = (uint32_t)(t4 >> 32);
+  }
+  const bool ge = c1 != 0;               // R >= P: x0 = R - P
+  const bool neg = ge ? c4 != 0 : c3 != 0;
+  // pass 2: |c_hat| = x0, or P - x0 for negative results; x0 < P is checked
+  uint32_t cs = 0, br = 0, cc = 0;
+  int top = -1;
+  for (int d = 0; d < D; ++d) {
+    const uint32_t r = s_R[d * kFinThreads + e];
+    const uint64_t t1 = (uint64_t)r + s_negP[d] + cs;
+    cs = (uint32_t)(t1 >> 32);
+    const uint32_t x0 = ge ? (uint32_t)t1 : r;
+    const uint64_t tc = (uint64_t)x0 + s_negP[d] + cc;     // carry out iff x0 >= P
+    cc = (uint32_t)(tc >> 32);
+    uint32_t mag = x0;
+    if (neg) {
+      const uint64_t tn = (uint64_t)s_P[d] - x0 - br;
+      mag = (uint32_t)tn;
+      br = (uint32_t)(tn >> 63);
+    }
+    s_R[d * kFinThreads + e] = mag;
+    if (mag) top = d;
+  }
+  if (cc) atomicOr(T.status, kStatusCrtRange);
+  if (P.dbg_chat != nullptr) {
+    uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
+    dst[0] = neg;
+    for (int d = 0; d < D; ++d) dst[1 + d] = s_R[d * kFinThreads + e];
+  }
+  crt_round_write(P, s_R, kFinThreads, e, D, top, neg, idx);
+}
+
+// ---------------------------------------------------------------------------
+// CRT sums of any length on the tensor cores (crt_mode 2).  As in k_crt_tc,
+// S = sum_l v_l M_l = sum_j 128^j Y_j with Y = V B (K = 2L: the 7-bit halves
+// of v_l; columns j: the 7-bit pieces of M_l), and every fp32 sum in TMEM is
+// an exact integer below 2L 127^2 < 2^24 for L <= 520.  The plane GEMM
+// already stored v_l = u_l M_l^{-1} mod m_l in place of u_l.
+//
+// Per tile of 128 consecutive outputs, V lives in tensor memory: TMEM lane r
+// holds output r's row, column l the bf16 pair (v0_l, v1_l).  The columns of
+// Y run in chunks of cw (a multiple of 32, kpad / 2 + 2 cw <= 512) through
+// two TMEM accumulator slots after V; the B blocks (64 k x cw columns) stream
+// through a shared-memory ring.  32 consecutive pieces span exactly 7 words,
+// so group g of 32 columns is the integer
+//   Q_g = sum_{q < 32} Y_{32 g + q} 2^(7 q),   S = sum_g Q_g 2^(224 g),
+// with piece q in word 7 q / 32 at shift 7 q mod 32 (both constants); each
+// Q_g is written on its own as 9 words (7 carried word sums and the carry),
+// and the finish adds the groups and alpha~ (2^(32 D) - P).
+//   warp 0      TMA producer of the B blocks, in (chunk, K block) order
+//   warp 1      MMA issuer: chunk c into slot c & 1 (counted over the CTA's
+//               tiles); commits per ring stage and per chunk
+//   warp 2      TMA producer of the tile's v values, 32 moduli x 128 outputs
+//               per copy, into a four-slot ring
+//   warps 3-10  two threads per output (its TMEM lane), halves h = 0, 1:
+//               half h writes the V columns of the copies of its parity (one
+//               tcgen05.st of 32 columns each) and its part of the quotient
+//               sum sum_l v_l floor(2^32 / m_l); then, for every chunk, the
+//               groups of 32 columns of its parity.
+// A warp rewrites its V columns only after the commit that follows the
+// previous tile's last MMA, and the next tile's MMAs wait for every warp's V
+// columns (tcgen05.st waited and fenced), so V is never read and written at
+// once; an accumulator slot is reused only after both halves have read it.
+// Tile list entry: {problem, tile, 0, 0}.
+// ---------------------------------------------------------------------------
+constexpr int kCmWorkers = 256;
+constexpr int kCmThreads = 96 + kCmWorkers;
+constexpr int kCmMaxStages = 24;
+constexpr int kCmUMods = 32;                         // moduli per v copy
+constexpr int kCmUSlots = 4;
+constexpr uint32_t kCmUBytes = kCmUMods * 128 * 2;   // [32][128] uint16
+constexpr int kCmMinSmem = 116 * 1024;               // one CTA per SM: it holds all 512 TMEM columns
+
+struct CmLayout {
+  uint32_t ring_off, u_off, mu_off, bar_off, total;
+  __host__ __device__ CmLayout(uint32_t stage_bytes, int stages, int lmax) {
+    ring_off = 0;
+    u_off = (uint32_t)stages * stage_bytes;
+    mu_off = u_off + kCmUSlots * kCmUBytes;                 // floor(2^32 / m_l) [lmax]
+    bar_off = mu_off + (((uint32_t)lmax * 4 + 15u) & ~15u);
+    // barriers: full, empty [kCmMaxStages], u_full, u_free [kCmUSlots], acc_full, acc_free [2],
+    // v_full, v_free, drain; then the abort flag and the TMEM slot
+    total = 1024 + bar_off + (2 * kCmMaxStages + 2 * kCmUSlots + 7) * 8 + 16;
+    if (total < (uint32_t)kCmMinSmem) total = kCmMinSmem;
+  }
+};
+
+// exact integer value (< 2^24) of an fp32 holding one
+__device__ __forceinline__ uint32_t f2u_exact24(uint32_t bits) {
+  const float f = __uint_as_float(bits);
+  return f >= 8388608.0f ? bits - 0x4A800000u : __float_as_uint(f + 8388608.0f) - 0x4B000000u;
+}
+
+// bf16 bits of an integer 0 <= x < 256: 2^23 + x has x in its low mantissa bits
+__device__ __forceinline__ uint32_t bf16_small(uint32_t x) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | x) - 8388608.0f) >> 16;
+}
+
+// Add 32 pieces y[q] 2^(7 q) of one group into the 7 word accumulators.
+template <int NQ>
+__device__ __forceinline__ void crt_group(const uint32_t* y, uint64_t (&acc)[7]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[(7 * q) >> 5] += (uint64_t)f2u_exact24(y[q]) << ((7 * q) & 31);
+}
+
+__global__ void __launch_bounds__(kCmThreads, 1)
+    k_crt_mm(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, uint32_t stage_bytes,
+             int stages) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const CmLayout lay(stage_bytes, stages, T.lmax);
+  const uint32_t sRing = base + lay.ring_off;                 // B ring [stages][cw cols][128 B]
+  uint32_t* s_mu = reinterpret_cast<uint32_t*>(sm + lay.mu_off);
+  const uint32_t sU = base + lay.u_off;                       // v ring [kCmUSlots][32][128] uint16
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);
+  uint64_t* full = bars;                                      // [kCmMaxStages]
+  uint64_t* empty = bars + kCmMaxStages;                      // [kCmMaxStages]
+  uint64_t* u_full = bars + 2 * kCmMaxStages;                 // [kCmUSlots]
+  uint64_t* u_free = u_full + kCmUSlots;                      // [kCmUSlots] (128 arrivals: one half)
+  uint64_t* acc_full = u_free + kCmUSlots;                    // [2] chunk in slot done
+  uint64_t* acc_free = acc_full + 2;                          // [2] slot read out (256 arrivals)
+  uint64_t* v_full = acc_free + 2;                            // V columns written (256 arrivals)
+  uint64_t* v_free = v_full + 1;                              // MMAs of the tile done (V may be rewritten)
+  uint64_t* drain = v_full + 2;                               // abort drain of the MMA pipe
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(v_full + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(v_full + 3) + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kCmMaxStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < kCmUSlots; ++i) {
+      mbar_init(u_full + i, 1);
+      mbar_init(u_free + i, 128);
+    }
+    for (int i = 0; i < 2; ++i) mbar_init(acc_full + i, 1);
+    mbar_init(v_full, kCmWorkers);
+    mbar_init(v_free, 1);
+    for (int i = 0; i < 2; ++i) mbar_init(acc_free + i, kCmWorkers);   // both halves read every chunk
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int l = threadIdx.x; l < T.lmax; l += kCmThreads) s_mu[l] = __ldg(&T.mods[l].mu);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ B producer
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      int issued_phase[kCmMaxStages];
+      for (int i = 0; i < kCmMaxStages; ++i) issued_phase[i] = -1;
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+        const int4 tl = tiles[i];
+        const ProbDev& P = T.probs[tl.x];
+        const CUtensorMap* mt = T.tmaps + 2 * T.count + tl.x;
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw;
+        for (int c = 0; ok && c < P.crt_nchunk; ++c) {
+          for (int q = 0; q < nkb; ++q) {
+            if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
+            mbar_expect_tx(full + st, (uint32_t)cw * 128u);
+            tma_load_2d(sRing + st * stage_bytes, mt, smem_u32(full + st), q * 64, c * cw);
+            issued_phase[st] = (int)ph;
+            if (++st == stages) { st = 0; ph ^= 1u; }
+          }
+        }
+      }
+      if (!ok) {
+        // let copies already in flight land before the CTA exits
+        for (int i = 0; i < stages; ++i)
+          if (issued_phase[i] >= 0)
+            for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(full + i, (uint32_t)issued_phase[i]); ++t) {}
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      int ck = 0, tcount = 0;
+      bool ok = true, any = false;
+      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+        const int4 tl = tiles[i];
+        const ProbDev& P = T.probs[tl.x];
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw;
+        const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
+        if (!mbar_wait(v_full, (uint32_t)(tcount & 1), abort_flag, T.status)) { ok = false; break; }
+        tc_fence_after();
+        for (int c = 0; ok && c < P.crt_nchunk; ++c, ++ck) {
+          const int s = ck & 1, use = ck >> 1;
+          if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int ncol = min(cw, P.crt_npad - c * cw);       // a multiple of 16
+          const uint32_t idesc = idesc_bf16(128, ncol);
+          const uint32_t d = tmem + vcols + (uint32_t)(s * cw);
+          for (int q = 0; q < nkb; ++q) {
+            if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t db = desc_sw128(sRing + st * stage_bytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              umma_bf16_ta(d, tmem + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
+            umma_commit(empty + st);
+            any = true;
+            if (++st == stages) { st = 0; ph ^= 1u; }
+          }
+          if (ok) umma_commit(acc_full + s);
+        }
+        if (!ok) break;
+        umma_commit(v_free);
+        ++tcount;
+      }
+      if (!ok && any) {
+        // drain issued MMAs before TMEM is released
+        umma_commit(drain);
+        for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(drain, 0u); ++t) {}
+      }
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ v producer
+    if (lane == 0) {
+      int uc = 0;
+      int issued_phase[kCmUSlots];
+      for (int i = 0; i < kCmUSlots; ++i) issued_phase[i] = -1;
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+        const int4 tl = tiles[i];
+        const ProbDev& P = T.probs[tl.x];
+        const CUtensorMap* mu_ = T.tmaps + 3 * T.count + tl.x;
+        for (int l0 = 0; l0 < P.L; l0 += kCmUMods, ++uc) {
+          const int s = uc % kCmUSlots, use = uc / kCmUSlots;
+          if (use > 0 && !mbar_wait(u_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(u_full + s, kCmUBytes);
+          tma_load_2d(sU + s * kCmUBytes, mu_, smem_u32(u_full + s), tl.y * 128, l0);
+          issued_phase[s] = use & 1;
+        }
+      }
+      if (!ok)
+        for (int s = 0; s < kCmUSlots; ++s)
+          if (issued_phase[s] >= 0)
+            for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(u_full + s, (uint32_t)issued_phase[s]); ++t) {}
+    }
+  } else {
+    // ------------------------------------------------------------ V columns + chunk epilogues
+    const int wk = warp - 3;
+    const int half = wk >> 2;
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint16_t* s_u = reinterpret_cast<const uint16_t*>(sm + lay.u_off);
+    int ck = 0, uc = 0, tcount = 0;
+    bool ok = true;
+    for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
+      const int4 tl = tiles[i];
+      const ProbDev& P = T.probs[tl.x];
+      const int L = P.L, cw = P.crt_cw;
+      // V may be rewritten once every MMA of the previous tile is done (a
+      // half may have had no chunk of that tile to wait for)
+      if (tcount > 0 && ok) ok = mbar_wait(v_free, (uint32_t)((tcount - 1) & 1), abort_flag, T.status);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
+      const int64_t idx = (int64_t)tl.y * 128 + row;
+      const bool valid = idx < (int64_t)P.M * P.N;
+      const int64_t up = P.upitch;
+      uint64_t sig = 0;
+      for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
+        if ((uc & 1) != half) continue;             // the other half's copy
+        const int s = uc % kCmUSlots, use = uc / kCmUSlots;
+        if (ok) ok = mbar_wait(u_full + s, (uint32_t)(use & 1), abort_flag, T.status);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        const uint16_t* su = s_u + s * (kCmUMods * 128);
+        uint32_t pr[kCmUMods];
+#pragma unroll
+        for (int q = 0; q < kCmUMods; ++q) {
+          const int l = l0 + q;
+          const uint32_t v = l < L ? (uint32_t)su[q * 128 + row] : 0u;
+          sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
+          pr[q] = bf16_small(v & 127u) | (bf16_small(v >> 7) << 16);
+        }
+        mbar_arrive(u_free + s);
+        tmem_st32(tlane + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
+      }
+      if (!ok) break;
+      if (valid) P.crt_sig[half * up + idx] = sig;
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(v_full);
+      // chunk epilogues: half h takes the 32-column groups g = h, h + 2, ...
+      for (int c = 0; c < P.crt_nchunk; ++c, ++ck) {
+        const int s = ck & 1, use = ck >> 1;
+        if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t trow = tlane + vcols + (uint32_t)(s * cw);
+        const int ncol = min(cw, P.crt_npad - c * cw);       // columns written by the MMAs
+        for (int g = 32 * half; g < cw; g += 64) {
+          uint64_t acc[7] = {0, 0, 0, 0, 0, 0, 0};
+          if (g + 32 <= ncol) {
+            uint32_t y[32];
+            tmem_ld32(trow + (uint32_t)g, y);
+            crt_group<32>(y, acc);
+          } else if (g < ncol) {                      // 16 columns left
+            uint32_t y[16];
+            tmem_ld16(trow + (uint32_t)g, y);
+            crt_group<16>(y, acc);
+          }
+          // group sum as 9 words: 7 word sums with carries, then the carry
+          uint32_t* qcol = P.crt_q + (int64_t)((c * cw + g) >> 5) * 9 * up + (valid ? idx : 0);
+          uint64_t carry = 0;
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            const uint64_t x = acc[k] + carry;
+            if (valid) qcol[(int64_t)k * up] = (uint32_t)x;
+            carry = x >> 32;
+          }
+          if (valid) {
+            qcol[(int64_t)7 * up] = (uint32_t)carry;
+            qcol[(int64_t)8 * up] = (uint32_t)(carry >> 32);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(acc_free + s);
+      }
+      if (!ok) break;
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
 // Classes 0..8: one lane per output with ND = 8, 12, ..., 40 digits;
 // classes 9..11: lane groups (GL lanes x DPL digits) for larger accumulators.
 struct CrtClass { int gl, dpl; };
@@ -869,8 +1345,55 @@ cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int
   return cudaGetLastError();
 }
 
+// Chunk width of the tensor-core CRT sums: columns of Y per TMEM slot, a
+// multiple of 32 with V (kpad / 2 columns) and two slots within 512 columns.
+int crt_mm_chunk(int kpad, int npad) {
+  int cw = (512 - kpad / 2) / 2;
+  cw = cw > 256 ? 256 : cw;
+  cw &= ~31;
+  const int need = (npad + 31) & ~31;
+  return cw < need ? cw : need;
+}
+
+int crt_mm_smem_bytes(int cw_max, int lmax, int* stages) {
+  // the deepest B ring (2 to kCmMaxStages stages of cw_max columns) that fits
+  const uint32_t sb = (uint32_t)cw_max * 128u;
+  for (int st = kCmMaxStages; st >= 2; --st) {
+    const int bytes = (int)CmLayout(sb, st, lmax).total;
+    if (bytes <= 227 * 1024) {
+      if (stages) *stages = st;
+      return bytes;
+    }
+  }
+  if (stages) *stages = 0;
+  return -1;
+}
+
+cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int grid,
+                          cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  int stages = 0;
+  const int smem = crt_mm_smem_bytes(cw_max, t.lmax, &stages);
+  if (smem < 0) return cudaErrorInvalidValue;
+  const int g = ntiles < grid ? ntiles : grid;
+  k_crt_mm<<<g, kCmThreads, smem, s>>>(t, reinterpret_cast<const int4*>(tiles), ntiles, (uint32_t)cw_max * 128u,
+                                       stages);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
+                                   cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  const int smem = 3 * dmax * 4 + dmax * kFinThreads * 4 + 2 * gmax * kFinThreads * 4;
+  k_crt_fin_long<<<nblk, kFinThreads, smem, s>>>(t, reinterpret_cast<const int4*>(blk));
+  return cudaGetLastError();
+}
+
 cudaError_t init_crt_attributes() {
-  cudaError_t e = crt1_attr<8>();
+  cudaError_t e = cudaFuncSetAttribute(k_crt_mm, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_crt_fin_long, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess) e = crt1_attr<8>();
   if (e == cudaSuccess) e = crt1_attr<12>();
   if (e == cudaSuccess) e = crt1_attr<16>();
   if (e == cudaSuccess) e = crt1_attr<20>();

@@ -285,10 +285,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           }
           tmem_st32(tbase + (uint32_t)(c * 32), v);
         } else {
+          // final coefficient; for the tensor-core CRT sums also times
+          // M_l^{-1} mod m_l, so that the stored value is v_l (Sec. 4.4)
+          uint32_t fin = mc.kfin;
+          if (P.crt_mode == 2) fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
-            if (mc.kfin != 1u) r = barrett32(r * mc.kfin, mc.m, mc.mu);
+            if (fin != 1u) r = barrett32(r * fin, mc.m, mc.mu);
             v[i] = r;
           }
           const int col0 = col_base + c * 32;
@@ -384,6 +388,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevTables T, const int4* __re
     }
     v %= m;
     if (v < 0) v += m;
+    if (P.crt_mode == 2) v = v * __ldg(crt_view(T.crt_pool, P).Minv + u.ell) % m;   // v_l for the CRT sums
     P.u[(int64_t)u.ell * P.upitch + (int64_t)row * P.N + col] = (uint16_t)v;
   }
 }

@@ -68,7 +68,8 @@ struct ProbDev {
   const int32_t* ext_scale;                                  // per-line extra exponent (backward)
   int32_t ext_scale_axis, pad2;
   int32_t DS;            // digit stride of the CRT tables (digits of the kernel class)
-  int32_t crt_mode;      // 0: CUDA-core CRT; 1: column sums on the tensor cores
+  int32_t crt_mode;      // 0: CUDA-core CRT; 1: column sums on the tensor cores (one kernel);
+                         // 2: column sums on the tensor cores written as digits R, then the finish
   uint32_t* dbg_chat;    // optional: [M*N][D32+1] sign word + |c_hat| digits
   int32_t crt_kpad;      // tensor-core CRT: K = 2L padded to a multiple of 64
   int32_t crt_npad;      // tensor-core CRT: 7-bit pieces of S padded to a multiple of 16
@@ -78,7 +79,12 @@ struct ProbDev {
   int32_t res_mode;      // 0: residues on the CUDA cores; 1: byte GEMM on the tensor cores
   int32_t res_kpad;      // tensor-core residues: bytes of a (t+1)-bit integer, padded to 64
   int32_t res_npad;      // tensor-core residues: table rows L1 + 2 (L - L1), padded to 16
-  int32_t pad5;
+  int32_t crt_nchunk;    // crt_mode 2: chunks of crt_cw columns of Y
+  int32_t crt_cw;        // crt_mode 2: columns of Y per chunk (a multiple of 32)
+  uint32_t* crt_q;       // crt_mode 2: group sums Q_g as [ngrp][9][upitch] words
+  uint64_t* crt_sig;     // crt_mode 2: two partial quotient sums [2][upitch]
+  int32_t crt_ngrp;      // crt_mode 2: groups of 32 columns, nchunk cw / 32
+  int32_t pad6;
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -148,6 +154,15 @@ cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int
 cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int ntiles, int kpad_max,
                           int npad_max, int lmax, int sms, cudaStream_t s);
 int crt_tc_smem_bytes(int cls, int kpad_max, int npad_max, int lmax, int nbuf);
+// Tensor-core CRT sums of any length (crt_mode 2): tiles of 128 outputs
+// {problem, tile}; R digits to the workspace.  Then the finish of long
+// accumulators (> 40 digits), blocks of 128 outputs {problem, block}.
+cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int grid,
+                          cudaStream_t s);
+int crt_mm_chunk(int kpad, int npad);
+int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
+cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
+                                   cudaStream_t s);
 // Tensor-core residues: persistent tiles of 4 lines x 32 k.
 cudaError_t launch_residues_tc(const DevTables& t, const int32_t* tiles, int ntiles, int kpad_max, int npad_max,
                                int lmax, int sms, cudaStream_t s);

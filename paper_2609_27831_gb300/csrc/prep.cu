@@ -170,6 +170,86 @@ __device__ __forceinline__ void element_words(const uint32_t* __restrict__ limbs
   }
 }
 
+// Residues of two elements over all L moduli from their first NW words, and
+// the plane writes.  The table row of modulus l holds the packed low bytes of
+// 2^(8 b) mod m_l in words [0, W32) and the high bytes in words [W32, 2 W32).
+template <int NW, int W32>
+__device__ __forceinline__ void residue_planes(const uint32_t (&w0)[W32], const uint32_t (&w1)[W32], bool n0,
+                                               bool n1, const uint32_t* s_t8, const uint4* s_mc, int L, int L1,
+                                               uint16_t* dst, int64_t plane_stride, bool two) {
+  constexpr int RS = 2 * W32;
+  auto put = [&](int x0, int x1) {                     // writes plane at dst, then moves to the next
+    if (two) *reinterpret_cast<uint32_t*>(dst) = bf16_bits(x0) | (bf16_bits(x1) << 16);
+    else *dst = (uint16_t)bf16_bits(x0);
+    dst += plane_stride;
+  };
+  for (int l = 0; l < L; ++l) {
+    const uint4 mcv = s_mc[l];
+    const uint32_t m = mcv.x, mu = mcv.y;
+    const uint32_t* tw = s_t8 + l * RS;
+    const uint2* tl = reinterpret_cast<const uint2*>(tw);
+    uint32_t r0, r1;
+    if (l < L1) {
+      uint32_t a0 = 0u, a1 = 0u;   // <= 4 W32 bytes * 255 * 255 < 2^32
+#pragma unroll
+      for (int q = 0; q < NW / 2; ++q) {
+        const uint2 t2 = tl[q];
+        a0 = __dp4a(w0[2 * q], t2.x, a0);
+        a0 = __dp4a(w0[2 * q + 1], t2.y, a0);
+        a1 = __dp4a(w1[2 * q], t2.x, a1);
+        a1 = __dp4a(w1[2 * q + 1], t2.y, a1);
+      }
+      if (NW & 1) {
+        const uint32_t tx = tw[NW - 1];
+        a0 = __dp4a(w0[NW - 1], tx, a0);
+        a1 = __dp4a(w1[NW - 1], tx, a1);
+      }
+      r0 = barrett32(a0, m, mu);
+      r1 = barrett32(a1, m, mu);
+    } else {
+      // low and high table bytes: x = s_lo + 256 s_hi < 2^32
+      uint32_t l0 = 0u, l1 = 0u, h0 = 0u, h1 = 0u;
+      const uint2* th = tl + W32 / 2;
+#pragma unroll
+      for (int q = 0; q < NW / 2; ++q) {
+        const uint2 t2 = tl[q];
+        const uint2 u2 = th[q];
+        l0 = __dp4a(w0[2 * q], t2.x, l0);
+        l0 = __dp4a(w0[2 * q + 1], t2.y, l0);
+        l1 = __dp4a(w1[2 * q], t2.x, l1);
+        l1 = __dp4a(w1[2 * q + 1], t2.y, l1);
+        h0 = __dp4a(w0[2 * q], u2.x, h0);
+        h0 = __dp4a(w0[2 * q + 1], u2.y, h0);
+        h1 = __dp4a(w1[2 * q], u2.x, h1);
+        h1 = __dp4a(w1[2 * q + 1], u2.y, h1);
+      }
+      if (NW & 1) {
+        const uint32_t tx = tw[NW - 1], ux = tw[W32 + NW - 1];
+        l0 = __dp4a(w0[NW - 1], tx, l0);
+        l1 = __dp4a(w1[NW - 1], tx, l1);
+        h0 = __dp4a(w0[NW - 1], ux, h0);
+        h1 = __dp4a(w1[NW - 1], ux, h1);
+      }
+      r0 = barrett32(l0 + (h0 << 8), m, mu);
+      r1 = barrett32(l1 + (h1 << 8), m, mu);
+    }
+    const int x0 = centered(r0, m, n0);
+    const int x1 = centered(r1, m, n1);
+    if (l < L1) {
+      put(x0, x1);                                   // plane l
+    } else {
+      // balanced base-128 split: r = r0 + 128 r1 with r0 = cen(r mod 128);
+      // planes L1 + 3 (l - L1) + {0, 1, 2} = r0, r1, r0 + r1
+      const int y0 = x0 & 127, y1 = x1 & 127;
+      const int lo0 = y0 > 64 ? y0 - 128 : y0, lo1 = y1 > 64 ? y1 - 128 : y1;
+      const int hi0 = (x0 - lo0) >> 7, hi1 = (x1 - lo1) >> 7;
+      put(lo0, lo1);
+      put(hi0, hi1);
+      put(lo0 + hi0, lo1 + hi1);
+    }
+  }
+}
+
 // Two horizontally adjacent elements per thread (k and k + 1).  The residue
 // of |a_hat| mod m is sum_b beta_b (2^(8 b) mod m) over its bytes beta_b
 // (Sec. 5.3's digit table, at byte granularity): one dp4a multiplies four
@@ -235,63 +315,11 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
   uint16_t* planes = side ? P.pb : P.pa;
   const int64_t plane_stride = (int64_t)R * P.Kp;
   uint16_t* dst = planes + (int64_t)r * P.Kp + k;      // k even, Kp even: 4-byte aligned pairs
-  auto put = [&](int x0, int x1) {                     // writes plane at dst, then moves to the next
-    if (two) *reinterpret_cast<uint32_t*>(dst) = bf16_bits(x0) | (bf16_bits(x1) << 16);
-    else *dst = (uint16_t)bf16_bits(x0);
-    dst += plane_stride;
-  };
-  for (int l = 0; l < L; ++l) {
-    const uint4 mcv = s_mc[l];
-    const uint32_t m = mcv.x, mu = mcv.y;
-    const uint2* tl = reinterpret_cast<const uint2*>(s_t8 + l * RS);
-    uint32_t r0, r1;
-    if (l < L1) {
-      uint32_t a0 = 0u, a1 = 0u;   // <= 4 W32 bytes * 255 * 255 < 2^32
-#pragma unroll
-      for (int q = 0; q < W32 / 2; ++q) {
-        const uint2 t2 = tl[q];
-        a0 = __dp4a(w0[2 * q], t2.x, a0);
-        a0 = __dp4a(w0[2 * q + 1], t2.y, a0);
-        a1 = __dp4a(w1[2 * q], t2.x, a1);
-        a1 = __dp4a(w1[2 * q + 1], t2.y, a1);
-      }
-      r0 = barrett32(a0, m, mu);
-      r1 = barrett32(a1, m, mu);
-    } else {
-      // low and high table bytes: x = s_lo + 256 s_hi < 2^32
-      uint32_t l0 = 0u, l1 = 0u, h0 = 0u, h1 = 0u;
-      const uint2* th = tl + W32 / 2;
-#pragma unroll
-      for (int q = 0; q < W32 / 2; ++q) {
-        const uint2 t2 = tl[q];
-        const uint2 u2 = th[q];
-        l0 = __dp4a(w0[2 * q], t2.x, l0);
-        l0 = __dp4a(w0[2 * q + 1], t2.y, l0);
-        l1 = __dp4a(w1[2 * q], t2.x, l1);
-        l1 = __dp4a(w1[2 * q + 1], t2.y, l1);
-        h0 = __dp4a(w0[2 * q], u2.x, h0);
-        h0 = __dp4a(w0[2 * q + 1], u2.y, h0);
-        h1 = __dp4a(w1[2 * q], u2.x, h1);
-        h1 = __dp4a(w1[2 * q + 1], u2.y, h1);
-      }
-      r0 = barrett32(l0 + (h0 << 8), m, mu);
-      r1 = barrett32(l1 + (h1 << 8), m, mu);
-    }
-    const int x0 = centered(r0, m, n0);
-    const int x1 = centered(r1, m, n1);
-    if (l < L1) {
-      put(x0, x1);                                   // plane l
-    } else {
-      // balanced base-128 split: r = r0 + 128 r1 with r0 = cen(r mod 128);
-      // planes L1 + 3 (l - L1) + {0, 1, 2} = r0, r1, r0 + r1
-      const int y0 = x0 & 127, y1 = x1 & 127;
-      const int lo0 = y0 > 64 ? y0 - 128 : y0, lo1 = y1 > 64 ? y1 - 128 : y1;
-      const int hi0 = (x0 - lo0) >> 7, hi1 = (x1 - lo1) >> 7;
-      put(lo0, lo1);
-      put(hi0, hi1);
-      put(lo0 + hi0, lo1 + hi1);
-    }
-  }
+  // |a_hat| <= 2^t has ceil(W16 / 2) nonzero words; the class may hold one more
+  if ((P.W16 + 1) / 2 <= W32 - 1)
+    residue_planes<W32 - 1, W32>(w0, w1, n0, n1, s_t8, s_mc, L, L1, dst, plane_stride, two);
+  else
+    residue_planes<W32, W32>(w0, w1, n0, n1, s_t8, s_mc, L, L1, dst, plane_stride, two);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,8 @@ WORKLOADS = {
     "gemm_1024_p256": (1024, 1024, 1024, 256, -32, 32, 1001),
     "gemm_2048_p512": (2048, 2048, 2048, 512, -8, 8, 1001),
     "gemm_4096_p53": (4096, 4096, 4096, 53, -8, 8, 1001),
+    "gemm_1024_p1024": (1024, 1024, 1024, 1024, -64, 64, 1001),
+    "gemm_1024_p2048": (1024, 1024, 1024, 2048, -64, 64, 1001),
 }
 
 
@@ -27,6 +29,8 @@ def main():
     ap.add_argument("--schedule", type=int, default=0)
     ap.add_argument("--res-engine", type=int, default=0)
     ap.add_argument("--crt-engine", type=int, default=0)
+    ap.add_argument("--time", action="store_true",
+                    help="also print the median per-stage milliseconds over --reps timed products")
     args = ap.parse_args()
     import torch
 
@@ -39,13 +43,23 @@ def main():
     dA, dB = ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B)
     C = ozk.MPMatrix.empty(M, N, p)
     plan = ozk.Plan((M, N, K, p), schedule=args.schedule, res_engine=args.res_engine,
-                    crt_engine=args.crt_engine)
+                    crt_engine=args.crt_engine, timing=1 if args.time else 0)
     ws = plan.workspace()
     for _ in range(args.reps):
         plan.execute(dA, dB, C, ws)
     plan.check()
     torch.cuda.synchronize()
     print("ok", args.workload, plan.info)
+    if args.time:
+        import statistics
+        stages = []
+        for _ in range(args.reps):
+            plan.execute(dA, dB, C, ws)
+            stages.append(plan.timings())
+        plan.check()
+        med = {k: round(statistics.median(t[k] for t in stages), 4) for k in stages[0]}
+        print("stage_ms", args.workload, med,
+              "rate_2MNK_per_s %.4g" % (2.0 * M * N * K / (med["total"] / 1e3)))
 
 
 if __name__ == "__main__":

@@ -83,7 +83,17 @@ def assert_full_parity(ozk, A, B, p, truth=True, **kw):
     assert e_ok.all()
     assert np.array_equal(bf16_to_int(got["pa"]), ref["planes_a"])
     assert np.array_equal(bf16_to_int(got["pb"]), ref["planes_b"])
-    assert np.array_equal(got["u"].astype(np.int64), ref["u"])
+    if got["plan"].info["crt_mode"] == 2:
+        # the CRT-sum engine stores v_l = u_l M_l^{-1} mod m_l, M_l = P / m_l
+        mods = ref["par"].moduli
+        P = 1
+        for m in mods:
+            P *= m
+        inv = np.array([pow((P // m) % m, -1, m) for m in mods], dtype=np.int64)
+        want = (ref["u"] * inv[:, None, None]) % np.array(mods, dtype=np.int64)[:, None, None]
+        assert np.array_equal(got["u"].astype(np.int64), want)
+    else:
+        assert np.array_equal(got["u"].astype(np.int64), ref["u"])
     assert all(got["chat"][i, j] == ref["chat"][i, j] for i in range(M) for j in range(N))
     for key in ("limbs", "exp", "sign"):
         assert np.array_equal(got["C"][key], ref["C"][key]), key
@@ -192,25 +202,95 @@ def test_zero_lines_and_tiny_shapes(ozk):
 
 def test_p2048_small(ozk):
     """p = 2048 (the largest precision): 32-limb inputs, 132-digit residue
-    class, two-limb moduli, 32-lane CRT groups; every stage bit-exact."""
+    class, two-limb moduli; the CRT both as tensor-core sums (the default at
+    this length) and on 32-lane CUDA-core groups; every stage bit-exact."""
     rng = np.random.Generator(np.random.PCG64(2030))
     A = synth.mp_matrix(rng, 20, 24, 2048, -64, 64)
     B = synth.mp_matrix(rng, 24, 18, 2048, -64, 64)
-    assert_full_parity(ozk, A, B, 2048, truth=False)
+    got, _ = assert_full_parity(ozk, A, B, 2048, truth=False)
+    assert got["plan"].info["crt_mode"] == 2
+    got3, _ = assert_full_parity(ozk, A, B, 2048, truth=False, crt_engine=3)
+    assert got3["plan"].info["crt_mode"] == 0
 
 
 @pytest.mark.parametrize("p", [300, 700])
 def test_crt_engines_bit_exact(ozk, p):
-    """The CUDA-core CRT (default) and the tensor-core CRT give the same CRT
-    integers and outputs, and both match the oracle."""
+    """The CRT engines (automatic, CUDA cores only, tensor-core column sums in
+    one kernel) give the same CRT integers and outputs, and all match the
+    oracle."""
     rng = np.random.Generator(np.random.PCG64(2010 + p))
     A = synth.mp_matrix(rng, 140, 60, p, -30, 30)
     B = synth.mp_matrix(rng, 60, 20, p, -30, 30)
-    got_tc, ref = assert_full_parity(ozk, A, B, p, truth=False)
-    got_cc = run_gpu(ozk, A, B, p, crt_engine=1)
-    assert all(got_cc["chat"][i, j] == ref["chat"][i, j] for i in range(140) for j in range(20))
+    got_auto, ref = assert_full_parity(ozk, A, B, p, truth=False)
+    for eng in (1, 3):
+        got = run_gpu(ozk, A, B, p, crt_engine=eng)
+        assert all(got["chat"][i, j] == ref["chat"][i, j] for i in range(140) for j in range(20))
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(got["C"][key], got_auto["C"][key])
+
+
+@pytest.mark.parametrize("shape", [(140, 20, 60, 300), (70, 45, 50, 700), (40, 36, 30, 1024),
+                                   (20, 18, 24, 2048), (9, 15, 7, 130)])
+def test_crt_sum_engine_stages(ozk, shape):
+    """CRT sums on the tensor cores (crt_engine 2): one-lane finish (<= 40
+    digits) and the long finish (> 40 digits), one to five 128-column chunks,
+    ragged last tiles; every stage bit-exact against the oracle."""
+    M, N, K, p = shape
+    rng = np.random.Generator(np.random.PCG64(2040 + p))
+    A = synth.mp_matrix(rng, M, K, p, -30, 30)
+    B = synth.mp_matrix(rng, K, N, p, -30, 30)
+    assert_full_parity(ozk, A, B, p, truth=False, crt_engine=2)
+
+
+def test_crt_sum_engine_many_tiles(ozk):
+    """More 128-output tiles than CTAs (V rebuilt, TMEM slots and rings
+    cycling): identical to the CUDA-core CRT, and sampled entries against the
+    oracle."""
+    M, N, K, p = 256, 160, 16, 1024
+    rng = np.random.Generator(np.random.PCG64(2045))
+    A = synth.mp_matrix(rng, M, K, p, -20, 20)
+    B = synth.mp_matrix(rng, K, N, p, -20, 20)
+    g2 = run_gpu(ozk, A, B, p, debug=False, crt_engine=2)
+    g0 = run_gpu(ozk, A, B, p, debug=False)
     for key in ("limbs", "exp", "sign"):
-        assert np.array_equal(got_cc["C"][key], got_tc["C"][key])
+        assert np.array_equal(g2["C"][key], g0["C"][key])
+    rnd = random.Random(11)
+    pairs = [(0, 0), (M - 1, N - 1)] + [(rnd.randrange(M), rnd.randrange(N)) for _ in range(6)]
+    for (i, j), r in zip(pairs, o.ozaki2_entries(A, B, p, pairs)):
+        assert o.matrix_entry(g2["C"], i, j) == (r["limbs"], r["exp"], r["sign"])
+
+
+def test_crt_sum_engine_one_chunk_many_tiles(ozk):
+    """One 128-column chunk per tile (p = 256) and many tiles per CTA: the half
+    without a chunk in a tile must still wait for that tile's MMAs before it
+    rewrites V.  Identical to the CUDA-core CRT."""
+    M, N, K, p = 512, 448, 8, 256
+    rng = np.random.Generator(np.random.PCG64(2047))
+    A = synth.mp_matrix(rng, M, K, p, -20, 20)
+    B = synth.mp_matrix(rng, K, N, p, -20, 20)
+    g2 = run_gpu(ozk, A, B, p, debug=False, crt_engine=2)
+    g0 = run_gpu(ozk, A, B, p, debug=False)
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(g2["C"][key], g0["C"][key])
+
+
+def test_crt_sum_engine_batched(ozk):
+    """A batch whose problems have different modulus counts and digit lengths
+    (tables switch between tiles of one CTA) through the tensor-core sums."""
+    rng = np.random.Generator(np.random.PCG64(2046))
+    shapes = [(70, 40, 30, 256), (33, 60, 17, 1024), (40, 30, 50, 512), (5, 5, 5, 53)]
+    mats = [(synth.mp_matrix(rng, M, K, p, -8, 8), synth.mp_matrix(rng, K, N, p, -8, 8))
+            for (M, N, K, p) in shapes]
+    plan = ozk.Plan(shapes, crt_engine=2)
+    ws = plan.workspace()
+    trip = [(ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), ozk.MPMatrix.empty(M, N, p))
+            for (M, N, K, p), (A, B) in zip(shapes, mats)]
+    plan.execute_batched(trip, ws)
+    plan.check()
+    for (M, N, K, p), (A, B), (_, _, Cd) in zip(shapes, mats, trip):
+        ref = o.ozaki2_full(A, B, p)["C"]
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(Cd.to_host()[key], ref[key])
 
 
 @pytest.mark.parametrize("shape", [(130, 70, 45, 256), (33, 9, 100, 53), (64, 129, 17, 500), (5, 3, 1, 2)])

@@ -97,7 +97,8 @@ def test_argument_errors(ozk, args, status):
 
 def test_bad_options(ozk):
     h = C.c_void_p()
-    for kw in ({"k_chunk": 100}, {"k_chunk": 2048}, {"engine": 7}, {"schedule": 9}):
+    for kw in ({"k_chunk": 100}, {"k_chunk": 2048}, {"engine": 7}, {"schedule": 9}, {"crt_engine": 4},
+               {"crt_engine": -1}, {"res_engine": 2}):
         st = ozk.lib().ozaki2_plan_create(64, 64, 64, 53, C.byref(ozk.opts(**kw)), C.byref(h))
         assert st == 1, kw
 
@@ -110,3 +111,37 @@ def test_null_pointer_errors(ozk):
     assert lib.ozaki2_check(None, None) == 1
     assert lib.ozaki2_cache_destroy(None) == 1
     assert lib.ozaki2_dgemm_bwd(None, None, 0, None, 0, None, 0, None) == 1
+
+
+def test_crt_sum_engine_workspace(ozk):
+    """crt_engine 2 adds the group sums ([groups of 32 columns][9][M N rounded
+    to 8] uint32) and the two partial quotient sums ([2][M N rounded to 8]
+    uint64) to the workspace where it applies, and nothing where it does not."""
+    shape = (256, 256, 64, 1024)
+    base = ozk.Plan(shape, crt_engine=3).info
+    plan = ozk.Plan(shape, crt_engine=2)
+    P = 1
+    for m in plan.moduli():
+        P *= m
+    L = plan.info["L"]
+    kpad = -(-2 * L // 64) * 64
+    npad = -(-(-(-P.bit_length() // 7) + 1) // 16) * 16
+    cw = min(256, ((512 - kpad // 2) // 2) // 32 * 32, -(-npad // 32) * 32)
+    ngrp, up = -(-npad // cw) * cw // 32, 256 * 256
+    a256 = lambda x: -(-x // 256) * 256
+    assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(16 * up)
+    small = (4, 4, 4, 53)                        # M N < 128: the CUDA-core CRT
+    assert ozk.Plan(small, crt_engine=2).info["workspace_bytes"] == ozk.Plan(small, crt_engine=3).info["workspace_bytes"]
+
+
+def test_crt_engine_choice(ozk):
+    """The automatic CRT choice: tensor-core sums only where the accumulator
+    needs more than 40 digits; engine 3 keeps the CUDA cores; engine 2 asks for
+    the sums wherever the shape qualifies (L >= 32, M N >= 128)."""
+    lo, hi = (64, 64, 64, 256), (64, 64, 64, 1024)
+    assert ozk.Plan(lo).info["crt_digits"] <= 40 and ozk.Plan(lo).info["crt_mode"] == 0
+    assert ozk.Plan(hi).info["crt_digits"] > 40 and ozk.Plan(hi).info["crt_mode"] == 2
+    assert ozk.Plan(hi, crt_engine=3).info["crt_mode"] == 0
+    assert ozk.Plan(lo, crt_engine=2).info["crt_mode"] == 2
+    assert ozk.Plan((8, 8, 64, 1024)).info["crt_mode"] == 0          # M N < 128
+    assert ozk.Plan((64, 64, 64, 53), crt_engine=2).info["crt_mode"] == 0   # L < 32
