@@ -189,7 +189,7 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # one ncu capture of the committed kernels on the same workload; the source
 # summaries are under profiles/.  A kernel changed since its capture has None.
 NCU_TRAFFIC = {
-    "gemm_1024_p256": {"residues": 445.094912e6, "gemm": 564.684032e6, "crt": 168.133376e6},
+    "gemm_1024_p256": {"residues": 443.812096e6, "gemm": 563.543552e6, "crt": 168.199424e6},
 }
 
 
@@ -361,7 +361,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "bf16-int (exact integer planes on tcgen05 kind::f16)",
         "data": "synthetic", "impl": "ours",
         "config": {"workload": WORK["workload"], "M": M, "N": N, "K": K, "p": p,
-                   "exp_range": WORK["exp_range"], "t": info["t"], "moduli": L, "gemms": G,
+                   "exp_range": WORK["exp_range"], "t": info["t"], "moduli": info["L"], "gemms": info["G"],
                    "parallelism": f"replicas{world}", "l2": "flushed (512 MiB write between steps)"},
         "e2e": {"value": replica_value(world, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -505,11 +505,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rounds", type=int, default=2)
+    ap.add_argument("--cpu-rounds", type=int, default=6)
     ap.add_argument("--workload", default="gemm_1024_p256",
                     choices=["gemm_1024_p256", "batched64", "dgemm4096_autograd", "gemm_4096_p2048",
                              "gemm_8192_p53", "gemm_4096_p53", "gemm_2048_p512"])

@@ -106,7 +106,9 @@ typedef struct {
                      3: the CRT on the CUDA cores only */
   int res_engine; /* 0: residues on the CUDA cores (default); 1: residues as an exact bf16 GEMM of
                      the bytes of a_hat with a table of centered 2^(8b) mod m on the tensor cores
-                     where the table has <= 256 rows and <= 256 bytes (CUDA cores otherwise) */
+                     where the table has <= 256 rows and <= 256 bytes (CUDA cores otherwise);
+                     2: the same GEMM, warp-specialised (bytes in tensor memory, table streamed),
+                     for integers of up to 512 bytes */
 } ozaki2_opts;
 
 /* Facts about a plan (all computed on the host at plan creation). */

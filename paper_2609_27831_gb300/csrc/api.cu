@@ -163,13 +163,14 @@ struct ProbHost {
   int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp;
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [2][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
+  int res_cw, res_nchunk, res_tcols;           // res_mode 2: chunk width, chunks, TMEM columns
 };
 
 // Tensor-core residue table [npad][kpad] (bf16 bits): row l (one-limb) =
 // cen(2^(8 b) mod m_l); rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
 // base-128 halves of cen(2^(8 b) mod m_l).
 struct ResTable {
-  int L, kpad, npad;
+  int L, kpad, npad, rows;   // rows: allocated (npad, or whole chunks of the warp-specialised kernel)
   std::vector<uint16_t> bits;
 };
 
@@ -209,6 +210,7 @@ struct DevState {
   int tct_npad[9] = {0};
   ListRef cmt;                  // tensor-core CRT sum tiles (smem = largest chunk width)
   ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = groups max)
+  ListRef rmt;                  // warp-specialised tensor-core residue tiles (smem = cw max, lmax = TMEM columns)
   ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
   int rtt_npad = 0;
   std::vector<void*> res_tab;   // per problem: device address of its residue table
@@ -393,16 +395,26 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int npad = (int)align_up((size_t)(h.L1 + 2 * (L - h.L1)), 16);
     h.res_mode = (o.res_engine == 1 && kpad <= 256 && npad <= 256 &&
                   residue_tc_smem_bytes(kpad, npad, L) <= 227 * 1024) ? 1 : 0;
+    // warp-specialised form: the bytes (kpad / 2 TMEM columns) and two slots
+    // of at least 32 columns; sums exact for <= 512 bytes
+    if (o.res_engine == 2 && kpad <= 512 && kpad / 2 + 64 <= 512) h.res_mode = 2;
     h.res_kpad = kpad;
     h.res_npad = npad;
+    h.res_cw = h.res_nchunk = 0;
+    h.res_tcols = 0;
+    if (h.res_mode == 2) {
+      residue_mm_geometry(kpad, npad, &h.res_cw, &h.res_tcols);
+      h.res_nchunk = (npad + h.res_cw - 1) / h.res_cw;
+    }
+    const int rows = h.res_mode == 2 ? h.res_cw * h.res_nchunk : npad;
     h.res_key = -1;
     if (h.res_mode) {
       for (size_t i = 0; i < pl->rtabs.size(); ++i)
-        if (pl->rtabs[i].L == L && pl->rtabs[i].kpad == kpad) h.res_key = (int)i;
+        if (pl->rtabs[i].L == L && pl->rtabs[i].kpad == kpad && pl->rtabs[i].rows == rows) h.res_key = (int)i;
       if (h.res_key < 0) {
         ResTable rt;
-        rt.L = L; rt.kpad = kpad; rt.npad = npad;
-        rt.bits.assign((size_t)npad * kpad, 0);
+        rt.L = L; rt.kpad = kpad; rt.npad = npad; rt.rows = rows;
+        rt.bits.assign((size_t)rows * kpad, 0);
         auto bf = [](int x) -> uint16_t {   // exact for |x| <= 256
           float f = (float)x;
           uint32_t u;
@@ -471,7 +483,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
-      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine != 0 && o.res_engine != 1)) {
+      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 2)) {
     delete pl;
     return OZ2_EINVAL;
   }
@@ -521,6 +533,8 @@ struct TableImage {
   std::vector<size_t> o_tctab;
   size_t o_cmt = 0, o_finl = 0;     // tensor-core CRT sum tiles; finish blocks of long accumulators
   int n_cmt = 0, cmt_cw = 0, n_finl = 0, finl_dmax = 0, finl_gmax = 0;
+  size_t o_rmt = 0;                 // warp-specialised tensor-core residue tile list
+  int n_rmt = 0, rmt_cw = 0, rmt_tcols = 0;
   size_t o_rtt = 0;                 // tensor-core residue tile list
   int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
   std::vector<size_t> o_rtab;
@@ -644,7 +658,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
   std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
-  std::vector<int4> rtt, cmt, finl;
+  std::vector<int4> rtt, cmt, finl, rmt;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a)
@@ -653,6 +667,14 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     if (!h.skip_b)
       for (int64_t c = 0; c < h.N; c += 32)
         for (int kp = 0; kp < kparts; ++kp) scan_cols.push_back(make_int4(pi, 1 | (kp << 8), (int)c, kparts));
+    for (int side = 0; h.res_mode == 2 && side < 2; ++side) {
+      if (side == 0 ? h.skip_a : h.skip_b) continue;
+      const int64_t R = side ? h.N : h.M;
+      for (int64_t r = 0; r < R; r += 4)
+        for (int64_t k = 0; k < h.K; k += 32) rmt.push_back(make_int4(pi, side, (int)r, (int)k));
+      ti.rmt_cw = std::max(ti.rmt_cw, h.res_cw);
+      ti.rmt_tcols = std::max(ti.rmt_tcols, h.res_tcols);
+    }
     for (int side = 0; h.res_mode == 1 && side < 2; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
@@ -747,6 +769,13 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.n_finl = (int)finl.size();
   ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
   ti.n_rtt = (int)rtt.size();
+  for (const ProbHost& h : pl->probs)
+    if (h.res_mode == 2 && (ti.rmt_cw < h.res_cw || ti.rmt_tcols < h.res_tcols || h.res_cw % 32 != 0 ||
+                            h.res_kpad / 2 + 2 * h.res_cw > h.res_tcols))
+      return OZ2_EINTERNAL;
+  if (!rmt.empty() && residue_mm_smem_bytes(ti.rmt_cw, pl->lmax, ti.rmt_tcols, nullptr) < 0) return OZ2_EINTERNAL;
+  ti.o_rmt = ti.b.add(rmt.data(), rmt.size() * 16);
+  ti.n_rmt = (int)rmt.size();
   ti.o_rtab.assign(pl->rtabs.size(), 0);
   for (size_t i = 0; i < pl->rtabs.size(); ++i)
     ti.o_rtab[i] = ti.b.add(pl->rtabs[i].bits.data(), pl->rtabs[i].bits.size() * 2, 1024);
@@ -794,10 +823,11 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   d.cmt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt), ti.n_cmt, ti.cmt_cw, 0};
   d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
   d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
+  d.rmt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rmt), ti.n_rmt, ti.rmt_cw, ti.rmt_tcols};
   d.rtt_npad = ti.rtt_npad;
   d.res_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
-    if (pl->probs[i].res_mode == 1) d.res_tab[i] = base + ti.o_rtab[pl->probs[i].res_key];
+    if (pl->probs[i].res_mode != 0) d.res_tab[i] = base + ti.o_rtab[pl->probs[i].res_key];
   d.crt_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
     if (pl->probs[i].crt_mode != 0) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
@@ -904,10 +934,14 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.res_mode = h.res_mode;
     P.res_kpad = h.res_kpad;
     P.res_npad = h.res_npad;
-    if (h.res_mode == 1) {
-      const cuuint64_t dims[2] = {(cuuint64_t)h.res_kpad, (cuuint64_t)h.res_npad};
+    P.res_cw = h.res_cw;
+    P.res_nchunk = h.res_nchunk;
+    if (h.res_mode != 0) {
+      // mode 1: the whole table in K blocks; mode 2: K block x cw columns
+      const int rows = pl->rtabs[h.res_key].rows;
+      const cuuint64_t dims[2] = {(cuuint64_t)h.res_kpad, (cuuint64_t)rows};
       const cuuint64_t strides[1] = {(cuuint64_t)h.res_kpad * 2};
-      const cuuint32_t box[2] = {64u, (cuuint32_t)h.res_npad};
+      const cuuint32_t box[2] = {64u, (cuuint32_t)(h.res_mode == 1 ? h.res_npad : h.res_cw)};
       const cuuint32_t es[2] = {1u, 1u};
       if (get_encode()(&tm[4 * count + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.res_tab[i], dims, strides,
                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -988,6 +1022,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     if (d.res[c].n) OZ2_CU(launch_residues(tab, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
   if (d.rtt.n)
     OZ2_CU(launch_residues_tc(tab, d.rtt.ptr, d.rtt.n, d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
+  if (d.rmt.n) OZ2_CU(launch_residues_mm(tab, d.rmt.ptr, d.rmt.n, d.rmt.smem, d.rmt.lmax, d.sms, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
   if (pl->opts.engine == OZ2_ENGINE_SIMT) {
     DevTables t2 = tab;

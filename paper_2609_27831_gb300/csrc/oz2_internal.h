@@ -76,7 +76,8 @@ struct ProbDev {
   int32_t crt_np;        // tensor-core CRT: 7-bit pieces of S (columns of Y)
   int32_t pad4;
   int64_t upitch;        // row pitch of u [L][upitch]: M*N rounded up to a multiple of 8
-  int32_t res_mode;      // 0: residues on the CUDA cores; 1: byte GEMM on the tensor cores
+  int32_t res_mode;      // 0: residues on the CUDA cores; 1: byte GEMM on the tensor cores;
+                         // 2: the byte GEMM, warp-specialised (bytes in TMEM, table streamed)
   int32_t res_kpad;      // tensor-core residues: bytes of a (t+1)-bit integer, padded to 64
   int32_t res_npad;      // tensor-core residues: table rows L1 + 2 (L - L1), padded to 16
   int32_t crt_nchunk;    // crt_mode 2: chunks of crt_cw columns of Y
@@ -84,7 +85,9 @@ struct ProbDev {
   uint32_t* crt_q;       // crt_mode 2: group sums Q_g as [ngrp][9][upitch] words
   uint64_t* crt_sig;     // crt_mode 2: two partial quotient sums [2][upitch]
   int32_t crt_ngrp;      // crt_mode 2: groups of 32 columns, nchunk cw / 32
-  int32_t pad6;
+  int32_t res_cw;        // res_mode 2: columns of Y per chunk (a multiple of 32)
+  int32_t res_nchunk;    // res_mode 2: chunks
+  int32_t pad7;
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -167,6 +170,11 @@ cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int n
 cudaError_t launch_residues_tc(const DevTables& t, const int32_t* tiles, int ntiles, int kpad_max, int npad_max,
                                int lmax, int sms, cudaStream_t s);
 int residue_tc_smem_bytes(int kpad, int npad, int lmax);
+// Warp-specialised tensor-core residues (res_mode 2): the same tiles.
+cudaError_t launch_residues_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int tcols,
+                               int sms, cudaStream_t s);
+void residue_mm_geometry(int kpad, int npad, int* cw, int* tcols);
+int residue_mm_smem_bytes(int cw_max, int lmax, int tcols, int* stages);
 
 // Internal plan variants used by the binary64 mode.
 struct PlanExtra {

@@ -293,15 +293,36 @@ def test_crt_sum_engine_batched(ozk):
             assert np.array_equal(Cd.to_host()[key], ref[key])
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("shape", [(130, 70, 45, 256), (33, 9, 100, 53), (64, 129, 17, 500), (5, 3, 1, 2)])
-def test_residue_engines_bit_exact(ozk, shape):
-    """Residues on the tensor cores (byte GEMM, opt-in) give the oracle's planes
-    bit for bit on both sides, with ragged tiles, zero lines and two-limb moduli."""
+def test_residue_engines_bit_exact(ozk, shape, engine):
+    """Residues on the tensor cores (byte GEMM, opt-in; one kernel or
+    warp-specialised) give the oracle's planes bit for bit on both sides, with
+    ragged tiles, zero lines and two-limb moduli."""
     M, N, K, p = shape
     rng = np.random.Generator(np.random.PCG64(2020 + M))
     A = synth.zero_rows(synth.mp_matrix(rng, M, K, p, -40, 40), [1])
     B = synth.zero_cols(synth.mp_matrix(rng, K, N, p, -40, 40), [0])
-    assert_full_parity(ozk, A, B, p, truth=False, res_engine=1)
+    assert_full_parity(ozk, A, B, p, truth=False, res_engine=engine)
+
+
+@pytest.mark.parametrize("shape", [(20, 18, 70, 2048), (40, 36, 130, 1024), (300, 260, 600, 113)])
+def test_residue_mm_engine_chunks_and_tiles(ozk, shape):
+    """The warp-specialised tensor-core residues with several column chunks
+    (p = 1024, 2048), 512 TMEM columns, and more tiles than CTAs (p = 113):
+    planes bit for bit against the CUDA-core kernel and the oracle."""
+    M, N, K, p = shape
+    rng = np.random.Generator(np.random.PCG64(2050 + p))
+    A = synth.zero_rows(synth.mp_matrix(rng, M, K, p, -50, 50), [2])
+    B = synth.zero_cols(synth.mp_matrix(rng, K, N, p, -50, 50), [1])
+    if M * N * K <= 600_000:
+        assert_full_parity(ozk, A, B, p, truth=False, res_engine=2)
+    else:
+        g2 = run_gpu(ozk, A, B, p, debug=False, res_engine=2)
+        g0 = run_gpu(ozk, A, B, p, debug=False)
+        assert np.array_equal(g2["pa"], g0["pa"]) and np.array_equal(g2["pb"], g0["pb"])
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(g2["C"][key], g0["C"][key])
 
 
 def test_cancellation_to_zero(ozk):

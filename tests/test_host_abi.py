@@ -98,7 +98,7 @@ def test_argument_errors(ozk, args, status):
 def test_bad_options(ozk):
     h = C.c_void_p()
     for kw in ({"k_chunk": 100}, {"k_chunk": 2048}, {"engine": 7}, {"schedule": 9}, {"crt_engine": 4},
-               {"crt_engine": -1}, {"res_engine": 2}):
+               {"crt_engine": -1}, {"res_engine": 3}):
         st = ozk.lib().ozaki2_plan_create(64, 64, 64, 53, C.byref(ozk.opts(**kw)), C.byref(h))
         assert st == 1, kw
 
