@@ -15,6 +15,8 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "gemm_256_p53": (256, 256, 256, 53, -8, 8, 1000),
     "gemm_1024_p256": (1024, 1024, 1024, 256, -32, 32, 1001),
+    "gemm_1024_p53": (1024, 1024, 1024, 53, -8, 8, 1001),
+    "gemm_2048_p256": (2048, 2048, 2048, 256, -32, 32, 1001),
     "gemm_2048_p512": (2048, 2048, 2048, 512, -8, 8, 1001),
     "gemm_4096_p53": (4096, 4096, 4096, 53, -8, 8, 1001),
     "gemm_1024_p1024": (1024, 1024, 1024, 1024, -64, 64, 1001),
