@@ -688,7 +688,8 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       for (int64_t r = 0; r < R; r += 8)
-        for (int64_t k = 0; k < h.K; k += 64) res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
+        for (int64_t k = 0; k < h.K; k += 32 * residue_class_ept(h.res_cls))
+          res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
     if (h.res_mode == 0) ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
     if (h.crt_mode == 1) {

@@ -282,18 +282,6 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   }
 }
 
-template <int ND>
-__device__ __forceinline__ int compare_digits(const uint32_t (&R)[ND], const uint32_t* Y) {
-  // sign of R - Y over ND digits, decided at the most significant differing digit
-  int cmp = 0;
-#pragma unroll
-  for (int d = ND - 1; d >= 0; --d) {
-    const uint32_t y = Y[d];
-    cmp = cmp ? cmp : (R[d] > y ? 1 : (R[d] < y ? -1 : 0));
-  }
-  return cmp;
-}
-
 // Round |c_hat| (nd digits in column e of s_mag, highest nonzero digit `top`,
 // -1 for zero) times 2^(e_i + f_j - 2t) to p bits, round-half-even, and write
 // output idx (limbs, exponent and sign, or a binary64 value).
@@ -384,41 +372,41 @@ template <int ND>
 __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], const uint32_t* s_tab,
                                            uint32_t* s_mag, int ldm, int e, int64_t idx, int32_t* status) {
   const int D = P.D32;
+  const uint32_t* negP = s_tab;
+  const uint32_t* negH1 = s_tab + ND;
   const uint32_t* Pd = s_tab + 2 * ND;
-  // R in [0, 2P): subtract P once if R >= P
-  if (compare_digits<ND>(R, Pd) >= 0) {
-    uint32_t br = 0;
+  // pass 1, least significant digit first, three independent carry chains:
+  // R + (2^(32 D) - P) carries out iff R >= P (then x0 = R - P, else x0 = R);
+  // x + (2^(32 D) - floor(P/2) - 1) carries out iff x > floor(P/2), for x = R
+  // and for x = R - P: the sign of c_hat for either choice of x0
+  uint32_t c1 = 0, c3 = 0, c4 = 0;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint64_t x = (uint64_t)R[d] - Pd[d] - br;
-      R[d] = (uint32_t)x;
-      br = (uint32_t)(x >> 63);
-    }
-    if (compare_digits<ND>(R, Pd) >= 0) atomicOr(status, kStatusCrtRange);   // x0 < P must hold
-  }
-  // signed representative: x0 > floor(P/2) means c_hat = x0 - P < 0, |c_hat| = P - x0.
-  // floor(P/2) + 1 is stored as its complement 2^(32 D) - (floor(P/2) + 1) in s_tab + ND;
-  // x0 > floor(P/2) <=> x0 >= floor(P/2) + 1 <=> x0 + complement carries out of digit D-1
-  bool neg;
-  {
-    const uint32_t* negH1 = s_tab + ND;
-    uint64_t c = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint64_t x = (uint64_t)R[d] + (d < D ? negH1[d] : 0u) + c;
-      c = (d < D) ? (x >> 32) : c;
-    }
-    neg = c != 0;
-  }
-  if (neg) {
-    uint32_t br = 0;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const uint64_t x = (uint64_t)Pd[d] - R[d] - br;
-      R[d] = (uint32_t)x;
-      br = (uint32_t)(x >> 63);
+  for (int d = 0; d < ND; ++d) {
+    if (d < D) {
+      const uint64_t t1 = (uint64_t)R[d] + negP[d] + c1;
+      c1 = (uint32_t)(t1 >> 32);
+      c3 = (uint32_t)(((uint64_t)R[d] + negH1[d] + c3) >> 32);
+      c4 = (uint32_t)(((uint64_t)(uint32_t)t1 + negH1[d] + c4) >> 32);
     }
   }
+  const bool ge = c1 != 0;
+  const bool neg = ge ? c4 != 0 : c3 != 0;
+  // pass 2: x0, the check x0 < P (x0 + 2^(32 D) - P must not carry out), and
+  // |c_hat| = x0 or P - x0
+  uint32_t cs = 0, cc = 0, br = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    if (d < D) {
+      const uint64_t t1 = (uint64_t)R[d] + negP[d] + cs;
+      cs = (uint32_t)(t1 >> 32);
+      const uint32_t x0 = ge ? (uint32_t)t1 : R[d];
+      cc = (uint32_t)(((uint64_t)x0 + negP[d] + cc) >> 32);
+      const uint64_t tn = (uint64_t)Pd[d] - x0 - br;
+      br = (uint32_t)(tn >> 63);
+      R[d] = neg ? (uint32_t)tn : x0;
+    }
+  }
+  if (cc) atomicOr(status, kStatusCrtRange);
   if (P.dbg_chat != nullptr) {
     uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
     dst[0] = neg;

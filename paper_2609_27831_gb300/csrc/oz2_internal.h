@@ -197,6 +197,7 @@ int plan_run(ozaki2_plan pl, const ozaki2_problem* q, void* ws, size_t ws_bytes,
 // Residue kernel W16 classes and CRT lane-group classes (host picks per problem).
 int residue_class_for(int w16);        // -> class index, or -1
 int residue_class_w16(int cls);
+int residue_class_ept(int cls);       // elements per thread of that class (block: 32 EPT k x 8 lines)
 constexpr int kCrtClassCount = 12;
 int crt_class_for(int d32);            // -> class index, or -1
 int crt_class_elems_per_block(int cls);

@@ -170,99 +170,146 @@ __device__ __forceinline__ void element_words(const uint32_t* __restrict__ limbs
   }
 }
 
-// Residues of two elements over all L moduli from their first NW words, and
+// Elements per thread of the CUDA-core residue kernel: four while their
+// words fit in registers, else two.
+__host__ __device__ constexpr int residue_ept(int w32) { return w32 <= 10 ? 4 : 2; }
+
+// Centered residue of s |a_hat| mod m from a = sum of the byte products
+// (a == |a_hat| mod m, a < 2^23), in fp32: f = s a exactly; q = f / m rounded
+// to nearest (the 1.5 2^23 addend rounds; q may be off by one because 1/m is
+// rounded), r = f - q m exactly (an fma of integers below 2^24), and one
+// step in each direction brings r into (-m/2, m/2] (ties: +m/2).  The result
+// is an exact small integer; + 0 turns a -0 into +0.
+__device__ __forceinline__ float centered_f32(uint32_t a, bool neg, float mf, float rcp, float hm) {
+  float f = __uint_as_float(a | 0x4B000000u) - 8388608.0f;
+  if (neg) f = -f;
+  const float q = fmaf(f, rcp, 12582912.0f) - 12582912.0f;
+  float r = fmaf(-q, mf, f);
+  r = r > hm ? r - mf : r;
+  r = r <= -hm ? r + mf : r;
+  return r + 0.0f;
+}
+
+// Residues of EPT elements over all L moduli from their first NW words, and
 // the plane writes.  The table row of modulus l holds the packed low bytes of
 // 2^(8 b) mod m_l in words [0, W32) and the high bytes in words [W32, 2 W32).
-template <int NW, int W32>
-__device__ __forceinline__ void residue_planes(const uint32_t (&w0)[W32], const uint32_t (&w1)[W32], bool n0,
-                                               bool n1, const uint32_t* s_t8, const uint4* s_mc, int L, int L1,
-                                               uint16_t* dst, int64_t plane_stride, bool two) {
+// s_mc[l] = {m, floor(2^32 / m), 1/m (fp32 bits), m/2 (fp32 bits)}.  One-limb
+// sums stay below 4 NW 255^2 < 2^23 for NW <= 32, so their reduction is done
+// in fp32 there (Barrett beyond); two-limb moduli use Barrett reduction of
+// lo + 256 hi < 2^32.
+template <int NW, int W32, int EPT>
+__device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], const bool (&ng)[EPT],
+                                               const uint32_t* s_t8, const uint4* s_mc, int L, int L1,
+                                               uint16_t* dst, int64_t plane_stride, int nk) {
+  static_assert(EPT == 2 || EPT == 4, "two or four elements per thread");
   constexpr int RS = 2 * W32;
-  auto put = [&](int x0, int x1) {                     // writes plane at dst, then moves to the next
-    if (two) *reinterpret_cast<uint32_t*>(dst) = bf16_bits(x0) | (bf16_bits(x1) << 16);
-    else *dst = (uint16_t)bf16_bits(x0);
+  // one plane of the EPT elements: one vector store when all are in range
+  auto put = [&](const uint32_t (&bits)[EPT]) {           // bf16 bits in the low halves
+    if (nk == EPT) {
+      if (EPT == 4) {
+        *reinterpret_cast<uint2*>(dst) = make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16));
+      } else {
+        *reinterpret_cast<uint32_t*>(dst) = bits[0] | (bits[1] << 16);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e)
+        if (e < nk) dst[e] = (uint16_t)bits[e];
+    }
     dst += plane_stride;
   };
   for (int l = 0; l < L; ++l) {
     const uint4 mcv = s_mc[l];
-    const uint32_t m = mcv.x, mu = mcv.y;
     const uint32_t* tw = s_t8 + l * RS;
     const uint2* tl = reinterpret_cast<const uint2*>(tw);
-    uint32_t r0, r1;
     if (l < L1) {
-      uint32_t a0 = 0u, a1 = 0u;   // <= 4 W32 bytes * 255 * 255 < 2^32
+      uint32_t a[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) a[e] = 0u;
 #pragma unroll
       for (int q = 0; q < NW / 2; ++q) {
         const uint2 t2 = tl[q];
-        a0 = __dp4a(w0[2 * q], t2.x, a0);
-        a0 = __dp4a(w0[2 * q + 1], t2.y, a0);
-        a1 = __dp4a(w1[2 * q], t2.x, a1);
-        a1 = __dp4a(w1[2 * q + 1], t2.y, a1);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          a[e] = __dp4a(w[e][2 * q], t2.x, a[e]);
+          a[e] = __dp4a(w[e][2 * q + 1], t2.y, a[e]);
+        }
       }
       if (NW & 1) {
         const uint32_t tx = tw[NW - 1];
-        a0 = __dp4a(w0[NW - 1], tx, a0);
-        a1 = __dp4a(w1[NW - 1], tx, a1);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) a[e] = __dp4a(w[e][NW - 1], tx, a[e]);
       }
-      r0 = barrett32(a0, m, mu);
-      r1 = barrett32(a1, m, mu);
+      uint32_t bits[EPT];
+      if constexpr (NW <= 32) {                             // a < 4 NW 255^2 < 2^23: fp32 reduction
+        const float mf = (float)mcv.x, rcp = __uint_as_float(mcv.z), hm = __uint_as_float(mcv.w);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) bits[e] = __float_as_uint(centered_f32(a[e], ng[e], mf, rcp, hm)) >> 16;
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) bits[e] = bf16_bits(centered(barrett32(a[e], mcv.x, mcv.y), mcv.x, ng[e]));
+      }
+      put(bits);                                            // plane l
     } else {
       // low and high table bytes: x = s_lo + 256 s_hi < 2^32
-      uint32_t l0 = 0u, l1 = 0u, h0 = 0u, h1 = 0u;
+      uint32_t lo[EPT], hi[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) lo[e] = hi[e] = 0u;
       const uint2* th = tl + W32 / 2;
 #pragma unroll
       for (int q = 0; q < NW / 2; ++q) {
         const uint2 t2 = tl[q];
         const uint2 u2 = th[q];
-        l0 = __dp4a(w0[2 * q], t2.x, l0);
-        l0 = __dp4a(w0[2 * q + 1], t2.y, l0);
-        l1 = __dp4a(w1[2 * q], t2.x, l1);
-        l1 = __dp4a(w1[2 * q + 1], t2.y, l1);
-        h0 = __dp4a(w0[2 * q], u2.x, h0);
-        h0 = __dp4a(w0[2 * q + 1], u2.y, h0);
-        h1 = __dp4a(w1[2 * q], u2.x, h1);
-        h1 = __dp4a(w1[2 * q + 1], u2.y, h1);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          lo[e] = __dp4a(w[e][2 * q], t2.x, lo[e]);
+          lo[e] = __dp4a(w[e][2 * q + 1], t2.y, lo[e]);
+          hi[e] = __dp4a(w[e][2 * q], u2.x, hi[e]);
+          hi[e] = __dp4a(w[e][2 * q + 1], u2.y, hi[e]);
+        }
       }
       if (NW & 1) {
         const uint32_t tx = tw[NW - 1], ux = tw[W32 + NW - 1];
-        l0 = __dp4a(w0[NW - 1], tx, l0);
-        l1 = __dp4a(w1[NW - 1], tx, l1);
-        h0 = __dp4a(w0[NW - 1], ux, h0);
-        h1 = __dp4a(w1[NW - 1], ux, h1);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          lo[e] = __dp4a(w[e][NW - 1], tx, lo[e]);
+          hi[e] = __dp4a(w[e][NW - 1], ux, hi[e]);
+        }
       }
-      r0 = barrett32(l0 + (h0 << 8), m, mu);
-      r1 = barrett32(l1 + (h1 << 8), m, mu);
-    }
-    const int x0 = centered(r0, m, n0);
-    const int x1 = centered(r1, m, n1);
-    if (l < L1) {
-      put(x0, x1);                                   // plane l
-    } else {
       // balanced base-128 split: r = r0 + 128 r1 with r0 = cen(r mod 128);
       // planes L1 + 3 (l - L1) + {0, 1, 2} = r0, r1, r0 + r1
-      const int y0 = x0 & 127, y1 = x1 & 127;
-      const int lo0 = y0 > 64 ? y0 - 128 : y0, lo1 = y1 > 64 ? y1 - 128 : y1;
-      const int hi0 = (x0 - lo0) >> 7, hi1 = (x1 - lo1) >> 7;
-      put(lo0, lo1);
-      put(hi0, hi1);
-      put(lo0 + hi0, lo1 + hi1);
+      uint32_t b0[EPT], b1[EPT], b2[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int x = centered(barrett32(lo[e] + (hi[e] << 8), mcv.x, mcv.y), mcv.x, ng[e]);
+        const int y = x & 127;
+        const int r0 = y > 64 ? y - 128 : y;
+        const int r1 = (x - r0) >> 7;
+        b0[e] = bf16_bits(r0);
+        b1[e] = bf16_bits(r1);
+        b2[e] = bf16_bits(r0 + r1);
+      }
+      put(b0);
+      put(b1);
+      put(b2);
     }
   }
 }
 
-// Two horizontally adjacent elements per thread (k and k + 1).  The residue
-// of |a_hat| mod m is sum_b beta_b (2^(8 b) mod m) over its bytes beta_b
-// (Sec. 5.3's digit table, at byte granularity): one dp4a multiplies four
-// bytes of a word by four packed table bytes and accumulates in 32 bits.
+// EPT horizontally adjacent elements per thread (k .. k + EPT - 1).  The
+// residue of |a_hat| mod m is sum_b beta_b (2^(8 b) mod m) over its bytes
+// beta_b (Sec. 5.3's digit table, at byte granularity): one dp4a multiplies
+// four bytes of a word by four packed table bytes and accumulates in 32 bits.
 // Two-limb moduli use two byte tables (the low and high byte of
-// 2^(8 b) mod m < 2^14).  The table is read once for both elements, and each
-// plane gets one 32-bit store of two bf16 values.  Block: 32 x 8 threads =
-// 64 columns x 8 rows of elements.
+// 2^(8 b) mod m < 2^14).  The table is read once for all EPT elements, and
+// each plane gets one vector store.  Block: 32 x 8 threads = 32 EPT columns x
+// 8 rows of elements.
 template <int W16>
 __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __restrict__ blk) {
   constexpr int W32 = W16 / 2;
+  constexpr int EPT = residue_ept(W32);
   constexpr int RS = 2 * W32;                          // table row stride (words)
-  extern __shared__ __align__(16) uint32_t s_t8[];     // [L][RS] packed bytes, then [L] x {m, mu, 0, 0}
+  extern __shared__ __align__(16) uint32_t s_t8[];     // [L][RS] packed bytes, then [L] x {m, mu, 1/m, m/2}
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
   const int side = b.y;
@@ -275,51 +322,48 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
   }
   for (int l = threadIdx.y * 32 + threadIdx.x; l < L; l += 256) {
     const ModConst mc = T.mods[l];
-    s_mc[l] = make_uint4(mc.m, mc.mu, 0u, 0u);
+    s_mc[l] = make_uint4(mc.m, mc.mu, __float_as_uint(mc.rcp), __float_as_uint(0.5f * (float)mc.m));
   }
   __syncthreads();
   const int R = side ? P.N : P.M;
   const int r = b.z + threadIdx.y;
-  const int k = b.w + 2 * threadIdx.x;
+  const int k = b.w + EPT * threadIdx.x;
   if (r >= R || k >= P.K) return;
-  const bool two = k + 1 < P.K;
+  const int nk = min(EPT, P.K - k);
 
   const uint64_t* limbs = side ? P.b_limbs : P.a_limbs;
   const int64_t ps = side ? P.b_ps : P.a_ps;
   const int64_t stride_k = side ? P.b_ld : 1;
   const int64_t off0 = side ? ((int64_t)k * P.b_ld + r) : ((int64_t)r * P.a_ld + k);
-  const int64_t off1 = off0 + stride_k;
   const int32_t* exps = side ? P.b_exp : P.a_exp;
   const int8_t* signs = side ? P.b_sign : P.a_sign;
   const int nl = P.nl;
   const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
   const int e_line = side ? P.f[r] : P.e[r];
 
-  uint32_t w0[W32], w1[W32];
-  bool n0 = false, n1 = false;
-  if (__ldg(limbs + (int64_t)(nl - 1) * ps + off0) != 0ull) {
-    element_words<W32>(limbs32, ps, off0, nl, __ldg(exps + off0), e_line, P.t, w0);
-    n0 = __ldg(signs + off0) != 0;
-  } else {
+  uint32_t w[EPT][W32];
+  bool ng[EPT];
 #pragma unroll
-    for (int w = 0; w < W32; ++w) w0[w] = 0u;
-  }
-  if (two && __ldg(limbs + (int64_t)(nl - 1) * ps + off1) != 0ull) {
-    element_words<W32>(limbs32, ps, off1, nl, __ldg(exps + off1), e_line, P.t, w1);
-    n1 = __ldg(signs + off1) != 0;
-  } else {
+  for (int e = 0; e < EPT; ++e) {
+    const int64_t off = off0 + e * stride_k;
+    ng[e] = false;
+    if (e < nk && __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull) {
+      element_words<W32>(limbs32, ps, off, nl, __ldg(exps + off), e_line, P.t, w[e]);
+      ng[e] = __ldg(signs + off) != 0;
+    } else {
 #pragma unroll
-    for (int w = 0; w < W32; ++w) w1[w] = 0u;
+      for (int q = 0; q < W32; ++q) w[e][q] = 0u;
+    }
   }
 
   uint16_t* planes = side ? P.pb : P.pa;
   const int64_t plane_stride = (int64_t)R * P.Kp;
-  uint16_t* dst = planes + (int64_t)r * P.Kp + k;      // k even, Kp even: 4-byte aligned pairs
+  uint16_t* dst = planes + (int64_t)r * P.Kp + k;      // k a multiple of EPT, Kp of 8: aligned vectors
   // |a_hat| <= 2^t has ceil(W16 / 2) nonzero words; the class may hold one more
   if ((P.W16 + 1) / 2 <= W32 - 1)
-    residue_planes<W32 - 1, W32>(w0, w1, n0, n1, s_t8, s_mc, L, L1, dst, plane_stride, two);
+    residue_planes<W32 - 1, W32, EPT>(w, ng, s_t8, s_mc, L, L1, dst, plane_stride, nk);
   else
-    residue_planes<W32, W32>(w0, w1, n0, n1, s_t8, s_mc, L, L1, dst, plane_stride, two);
+    residue_planes<W32, W32, EPT>(w, ng, s_t8, s_mc, L, L1, dst, plane_stride, nk);
 }
 
 // ---------------------------------------------------------------------------
@@ -974,6 +1018,7 @@ int residue_class_for(int w16) {
   return -1;
 }
 int residue_class_w16(int cls) { return kResidueW16[cls]; }
+int residue_class_ept(int cls) { return residue_ept(kResidueW16[cls] / 2); }
 
 cudaError_t launch_scan(const DevTables& t, int /*count*/, const int32_t* blk_rows,
                         const int32_t* blk_cols, int nblk_rows, int nblk_cols, cudaStream_t s) {
