@@ -661,9 +661,14 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   std::vector<int4> rtt, cmt, finl, rmt;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
-    if (!h.skip_a)
-      for (int64_t r = 0; r < h.M; r += 8) scan_rows.push_back(make_int4(pi, 0, (int)r, 1));
-    const int kparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 256));
+    if (!h.skip_a) {
+      // rows of A: 8 rows per block, K split into parts of >= 256 (maxima combined by atomicMax)
+      const int rparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 256));
+      for (int64_t r = 0; r < h.M; r += 8)
+        for (int kp = 0; kp < rparts; ++kp) scan_rows.push_back(make_int4(pi, kp << 8, (int)r, rparts));
+    }
+    // columns of B: 32 columns per block, K split into parts of >= 64
+    const int kparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 64));
     if (!h.skip_b)
       for (int64_t c = 0; c < h.N; c += 32)
         for (int kp = 0; kp < kparts; ++kp) scan_cols.push_back(make_int4(pi, 1 | (kp << 8), (int)c, kparts));
@@ -739,6 +744,9 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.o_ordered = ti.b.add(ordered.data(), ordered.size() * sizeof(Unit));
   ti.o_ctag = ti.b.add(cta_g.data(), cta_g.size() * 4);
   ti.o_ctap = ti.b.add(cta_p.data(), cta_p.size() * 4);
+  // one launch scans rows and columns: the column blocks follow the row blocks
+  scan_rows.insert(scan_rows.end(), scan_cols.begin(), scan_cols.end());
+  scan_cols.clear();
   ti.o_srows = ti.b.add(scan_rows.data(), scan_rows.size() * 16);
   ti.o_scols = ti.b.add(scan_cols.data(), scan_cols.size() * 16);
   ti.o_simt = ti.b.add(simt.data(), simt.size() * 16);
