@@ -185,6 +185,11 @@ OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digit
    two-limb modulus the planes r0, r1, r0 + r1 (balanced base-128 split). */
 OZ2_API int ozaki2_plan_layout(ozaki2_plan plan, int prob, size_t off[5], int64_t* kp);
 
+/* Number of kernel launches of this library per execute of the plan (the
+   workspace memsets are not counted).  Known once the plan has run
+   (OZ2_EINVAL before the first execute). */
+OZ2_API int ozaki2_plan_launches(ozaki2_plan plan, int* n);
+
 /* Debugging aid: when dev_buf is not NULL, later executes also write the
    CRT integer c_hat of every output of problem `prob` to dev_buf (device,
    uint32 [M*N][crt_digits + 1]: word 0 = 1 for a negative c_hat, then

@@ -138,6 +138,12 @@ class Plan:
     def workspace(self, device="cuda") -> torch.Tensor:
         return torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
 
+    def launches(self) -> int:
+        """Kernel launches of the library per execute (after the first execute)."""
+        n = C.c_int()
+        check(lib().ozaki2_plan_launches(self._h, C.byref(n)), "ozaki2_plan_launches")
+        return n.value
+
     def set_debug_chat(self, prob: int, buf: torch.Tensor | None):
         check(lib().ozaki2_plan_set_debug_chat(self._h, prob, None if buf is None else buf.data_ptr()),
               "ozaki2_plan_set_debug_chat")

@@ -62,6 +62,7 @@ _SIGS = {
                                           C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ozaki2_plan_layout": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_size_t),
                                       C.POINTER(C.c_int64)]),
+    "ozaki2_plan_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "ozaki2_plan_set_debug_chat": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "ozaki2_execute": (C.c_int, [C.c_void_p, C.POINTER(Mat), C.POINTER(Mat), C.POINTER(Mat),
                                   C.c_void_p, C.c_size_t, C.c_void_p]),

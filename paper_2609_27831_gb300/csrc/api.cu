@@ -1246,6 +1246,26 @@ int ozaki2_plan_layout(ozaki2_plan pl, int prob, size_t off[5], int64_t* kp) {
   return OZ2_OK;
 }
 
+int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
+  if (!pl || !n) return OZ2_EINVAL;
+  const DevState& d = pl->dev;
+  if (!d.mem) return OZ2_EINVAL;                 // counted once the plan has run
+  int c = 0;
+  c += (d.scan_rows.n || d.scan_cols.n) ? 1 : 0;
+  for (int i = 0; i < 6; ++i) c += d.res[i].n ? 1 : 0;
+  c += d.rtt.n ? 1 : 0;
+  c += d.rmt.n ? 1 : 0;
+  if (pl->opts.engine == OZ2_ENGINE_SIMT) c += 1;
+  else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += 1;
+  else c += (int)d.plain.size();
+  c += d.cmt.n ? 1 : 0;
+  c += d.finl.n ? 1 : 0;
+  for (int i = 0; i < kCrtClassCount; ++i) c += d.crt[i].n ? 1 : 0;
+  for (int i = 0; i < 9; ++i) c += d.tct[i].n ? 1 : 0;
+  *n = c;
+  return OZ2_OK;
+}
+
 int ozaki2_plan_set_debug_chat(ozaki2_plan pl, int prob, uint32_t* dev_buf) {
   if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
   if (pl->dbg_chat.empty()) pl->dbg_chat.assign(pl->probs.size(), nullptr);

@@ -400,6 +400,18 @@ def test_batched_and_graph(ozk):
         assert np.array_equal(Cd.to_host()["limbs"], ref["limbs"])
 
 
+def test_launch_count(ozk):
+    """The library reports its kernel launches per execute: scan, residues,
+    plane GEMM and CRT for a short accumulator; the CRT sums and the long
+    finish replace the one-lane CRT above 40 digits."""
+    rng = np.random.Generator(np.random.PCG64(2060))
+    for p, n in ((256, 4), (2048, 5)):
+        A = synth.mp_matrix(rng, 40, 30, p, -5, 5)
+        B = synth.mp_matrix(rng, 30, 50, p, -5, 5)
+        got = run_gpu(ozk, A, B, p, debug=False)
+        assert got["plan"].launches() == n
+
+
 def test_convenience_gemm_call(ozk):
     rng = np.random.Generator(np.random.PCG64(2008))
     A = synth.mp_matrix(rng, 40, 50, 160, -4, 4)
