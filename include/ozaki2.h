@@ -104,11 +104,12 @@ typedef struct {
                      32 <= L <= 448 and M N >= 128 (CUDA cores otherwise); the reduced-product
                      region then holds v_l = (c mod m_l) M_l^{-1} mod m_l, M_l = P / m_l;
                      3: the CRT on the CUDA cores only */
-  int res_engine; /* 0: residues on the CUDA cores (default); 1: residues as an exact bf16 GEMM of
-                     the bytes of a_hat with a table of centered 2^(8b) mod m on the tensor cores
-                     where the table has <= 256 rows and <= 256 bytes (CUDA cores otherwise);
-                     2: the same GEMM, warp-specialised (bytes in tensor memory, table streamed),
-                     for integers of up to 512 bytes */
+  int res_engine; /* 0: automatic (default): engine 2 for integers of more than 192 bytes
+                     (p above about 1500), CUDA cores otherwise; 1: residues as an exact bf16
+                     GEMM of the bytes of a_hat with a table of centered 2^(8b) mod m on the
+                     tensor cores where the table has <= 256 rows and <= 256 bytes (CUDA cores
+                     otherwise); 2: the same GEMM, warp-specialised (bytes in tensor memory, table
+                     streamed), for integers of up to 448 bytes; 3: CUDA cores only */
 } ozaki2_opts;
 
 /* Facts about a plan (all computed on the host at plan creation). */
@@ -124,6 +125,7 @@ typedef struct {
   size_t workspace_bytes;
   int crt_mode;     /* CRT path of problem 0: 0 CUDA cores, 1 tensor-core column sums in one
                        kernel, 2 tensor-core sums of any length plus the finish (see crt_engine) */
+  int res_mode;     /* residue path of problem 0: 0 CUDA cores, 1 or 2 tensor cores (res_engine) */
 } ozaki2_info;
 
 typedef struct {

@@ -31,7 +31,8 @@ class Opts(C.Structure):
 class Info(C.Structure):
     _fields_ = [("count", C.c_int), ("t", C.c_int), ("L", C.c_int), ("L1", C.c_int),
                 ("G", C.c_int), ("crt_digits", C.c_int), ("units", C.c_int),
-                ("jobs", C.c_int), ("workspace_bytes", C.c_size_t), ("crt_mode", C.c_int)]
+                ("jobs", C.c_int), ("workspace_bytes", C.c_size_t), ("crt_mode", C.c_int),
+                ("res_mode", C.c_int)]
 
 
 class Problem(C.Structure):

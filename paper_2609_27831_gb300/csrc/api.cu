@@ -395,9 +395,12 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int npad = (int)align_up((size_t)(h.L1 + 2 * (L - h.L1)), 16);
     h.res_mode = (o.res_engine == 1 && kpad <= 256 && npad <= 256 &&
                   residue_tc_smem_bytes(kpad, npad, L) <= 227 * 1024) ? 1 : 0;
-    // warp-specialised form: the bytes (kpad / 2 TMEM columns) and two slots
-    // of at least 32 columns; sums exact for <= 512 bytes
-    if (o.res_engine == 2 && kpad <= 512 && kpad / 2 + 64 <= 512) h.res_mode = 2;
+    // warp-specialised form: two byte buffers (kpad / 2 TMEM columns each) and
+    // two slots of at least 32 columns; sums exact for <= 512 bytes.  The
+    // automatic choice takes it for integers of more than 192 bytes, where it
+    // beats the dp4a kernel (two-limb moduli dominate and the tiles are long)
+    const bool want_rmm = o.res_engine == 2 || (o.res_engine == 0 && kpad >= 256);
+    if (want_rmm && kpad + 64 <= 512) h.res_mode = 2;
     h.res_kpad = kpad;
     h.res_npad = npad;
     h.res_cw = h.res_nchunk = 0;
@@ -483,7 +486,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
-      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 2)) {
+      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 3)) {
     delete pl;
     return OZ2_EINVAL;
   }
@@ -780,7 +783,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.n_rtt = (int)rtt.size();
   for (const ProbHost& h : pl->probs)
     if (h.res_mode == 2 && (ti.rmt_cw < h.res_cw || ti.rmt_tcols < h.res_tcols || h.res_cw % 32 != 0 ||
-                            h.res_kpad / 2 + 2 * h.res_cw > h.res_tcols))
+                            h.res_kpad + 2 * h.res_cw > h.res_tcols))
       return OZ2_EINTERNAL;
   if (!rmt.empty() && residue_mm_smem_bytes(ti.rmt_cw, pl->lmax, ti.rmt_tcols, nullptr) < 0) return OZ2_EINTERNAL;
   ti.o_rmt = ti.b.add(rmt.data(), rmt.size() * 16);
@@ -1207,6 +1210,7 @@ int ozaki2_plan_info(ozaki2_plan pl, ozaki2_info* out) {
   out->jobs = (int)std::min<int64_t>(INT_MAX, pl->total_jobs);
   out->workspace_bytes = pl->ws_bytes;
   out->crt_mode = h.crt_mode;
+  out->res_mode = h.res_mode;
   return OZ2_OK;
 }
 

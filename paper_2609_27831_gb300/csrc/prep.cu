@@ -641,36 +641,39 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 // exact in fp32: |beta T| <= 255 * 127 < 2^15 and at most 512 bytes keep
 // every sum below 2^24.  Per tile of 4 lines x 32 consecutive k (128
 // elements; TMEM lane e is line e / 32, k e % 32: 32-byte runs on both sides
-// for the limb reads and the plane writes) the bytes live in tensor memory
-// as the A operand (two bf16 bytes per 32-bit column), the table streams
-// through a shared-memory ring as B in blocks of 64 bytes x cw columns, and
-// Y runs in chunks of cw columns through two TMEM accumulator slots.
-//   warp 0     TMA producer of the table blocks
-//   warp 1     MMA issuer: chunk c into slot c & 1; commits per ring stage,
-//              per chunk and per tile
-//   warps 2-9  two threads per element (halves h = 0, 1): half 0 integerizes
-//              the element and writes its bytes into TMEM once the previous
-//              tile's MMAs are done; then for every chunk each half takes the
-//              32-column groups of its parity (a two-limb pair never straddles
-//              a group: L1 is even): reduce mod m_l, apply the sign, center,
-//              split two-limb residues, store the bf16 planes.
+// for the limb reads and the plane writes) the bytes live in tensor memory as
+// the A operand (two bf16 bytes per 32-bit column, two buffers), the table
+// streams through a shared-memory ring as B in blocks of 64 bytes x cw
+// columns, and Y runs in chunks of cw columns through two accumulator slots:
+//   [A0: kpad/2][A1: kpad/2][slot 0: cw][slot 1: cw]  <= 512 TMEM columns.
+//   warp 0      TMA producer of the table blocks
+//   warp 1      MMA issuer: tile t reads A buffer t & 1; chunk c into slot
+//               c & 1; commits per ring stage, per chunk and per tile
+//   warps 2-5   one per TMEM lane quadrant: integerize the tile's elements and
+//               write their bytes into A buffer t & 1 once the MMAs of tile
+//               t - 2 are done, so that they run ahead of the epilogue
+//   warps 6-21  four per lane quadrant (sub-groups s = 0..3): for every chunk,
+//               the 32-column groups g = s, s + 4, ...; a group is all
+//               one-limb, all two-limb pairs (L1 is even) or the one mixed
+//               group: reduce mod m_l (round-to-nearest quotient in fp32, the
+//               sign applied first), split two-limb residues, store the bf16
+//               planes through incremental plane pointers.
 // Tile list entry: {problem, side, first line, first k}.
 // ---------------------------------------------------------------------------
-constexpr int kRmWorkers = 256;
-constexpr int kRmThreads = 64 + kRmWorkers;
+constexpr int kRmBuilders = 128;
+constexpr int kRmEpi = 512;
+constexpr int kRmThreads = 64 + kRmBuilders + kRmEpi;
 constexpr int kRmMaxStages = 16;
 
 struct RmLayout {
   uint32_t mc_off, bar_off, total;
-  __host__ __device__ RmLayout(uint32_t stage_bytes, int stages, int lmax, int tcols) {
-    mc_off = (uint32_t)stages * stage_bytes;                 // {m, 1/m} as floats [lmax]
-    bar_off = mc_off + (((uint32_t)lmax * 8 + 15u) & ~15u);
-    // barriers: full, empty [kRmMaxStages], acc_full, acc_free [2], a_full, v_free, drain;
+  __host__ __device__ RmLayout(uint32_t stage_bytes, int stages, int lmax) {
+    mc_off = (uint32_t)stages * stage_bytes;                 // {m, 1/m, m/2, 0} as floats [lmax]
+    bar_off = mc_off + (uint32_t)lmax * 16;
+    // barriers: full, empty [kRmMaxStages], acc_full, acc_free, a_full, a_free [2], drain;
     // then the abort flag and the TMEM slot
-    total = 1024 + bar_off + (2 * kRmMaxStages + 7) * 8 + 16;
-    // at most 512 / tcols CTAs per SM, so that their TMEM allocations always fit
-    const uint32_t floor_ = tcols > 256 ? 116u * 1024u : 78u * 1024u;
-    if (total < floor_) total = floor_;
+    total = 1024 + bar_off + (2 * kRmMaxStages + 9) * 8 + 16;
+    if (total < 116u * 1024u) total = 116u * 1024u;          // one CTA per SM: all 512 TMEM columns
   }
 };
 
@@ -679,31 +682,59 @@ __device__ __forceinline__ uint32_t bf16_byte(uint32_t x) {
   return __float_as_uint(__uint_as_float(0x4B000000u | x) - 8388608.0f) >> 16;
 }
 
+// Centered residue of an exact fp32 integer y (|y| < 2^24): y - q m with q the
+// round-to-nearest of y / m (the 1.5 2^23 addend rounds; q may be off by one
+// because 1/m is rounded), then one step each way into (-m/2, m/2]; exact.
+__device__ __forceinline__ float cmod_f32(float y, float mf, float rcp, float hm) {
+  const float q = fmaf(y, rcp, 12582912.0f) - 12582912.0f;
+  float r = fmaf(-q, mf, y);
+  r = r > hm ? r - mf : r;
+  r = r <= -hm ? r + mf : r;
+  return r;
+}
+
+// A value congruent to y0 + 128 y1 (mod m) for the two byte sums of a
+// two-limb modulus (table halves |T0| <= 64, |T1| <= 63, at most 448 bytes):
+// y1 is reduced with a round-to-nearest quotient only (|r1| < 1.5 m), so that
+// |y0 + 128 r1| <= 448 255 64 + 192 16191 < 2^24 is an exact fp32 integer
+// (and cmod_f32's quotient stays exact: |y / m| < 2^22).
+__device__ __forceinline__ float pair_f32(uint32_t y0bits, uint32_t y1bits, float mf, float rcp) {
+  const float y1 = __uint_as_float(y1bits);
+  const float q = fmaf(y1, rcp, 12582912.0f) - 12582912.0f;
+  const float r1 = fmaf(-q, mf, y1);
+  return fmaf(128.f, r1, __uint_as_float(y0bits));
+}
+
 __global__ void __launch_bounds__(kRmThreads, 1)
     k_residue_mm(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles,
-                 uint32_t stage_bytes, int stages, int tcols) {
+                 uint32_t stage_bytes, int stages) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sm = smem_raw + (base - raw);
-  const RmLayout lay(stage_bytes, stages, T.lmax, tcols);
+  const RmLayout lay(stage_bytes, stages, T.lmax);
   const uint32_t sRing = base;                                // table ring [stages][cw rows][128 B]
-  float2* s_mc = reinterpret_cast<float2*>(sm + lay.mc_off);  // [lmax] {m, 1/m}
+  const float4* s_mc = reinterpret_cast<const float4*>(sm + lay.mc_off);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);
   uint64_t* full = bars;                                      // [kRmMaxStages]
   uint64_t* empty = bars + kRmMaxStages;                      // [kRmMaxStages]
   uint64_t* acc_full = bars + 2 * kRmMaxStages;               // [2]
-  uint64_t* acc_free = acc_full + 2;                          // [2] (256 arrivals)
-  uint64_t* a_full = acc_full + 4;                            // bytes written (128 arrivals)
-  uint64_t* v_free = acc_full + 5;                            // MMAs of the tile done
-  uint64_t* drain = acc_full + 6;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_full + 7);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 7) + 1;
+  uint64_t* acc_free = acc_full + 2;                          // [2] (kRmEpi arrivals)
+  uint64_t* a_full = acc_full + 4;                            // [2] (kRmBuilders arrivals)
+  uint64_t* a_free = acc_full + 6;                            // [2] MMAs of the buffer's tile done
+  uint64_t* drain = acc_full + 8;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_full + 9);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 9) + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int l = threadIdx.x; l < T.lmax; l += kRmThreads)
-    s_mc[l] = make_float2((float)__ldg(&T.mods[l].m), __ldg(&T.mods[l].rcp));
+  {
+    float4* w_mc = reinterpret_cast<float4*>(sm + lay.mc_off);
+    for (int l = threadIdx.x; l < T.lmax; l += kRmThreads) {
+      const float mf = (float)__ldg(&T.mods[l].m);
+      w_mc[l] = make_float4(mf, __ldg(&T.mods[l].rcp), 0.5f * mf, 0.f);
+    }
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < kRmMaxStages; ++i) {
       mbar_init(full + i, 1);
@@ -711,17 +742,16 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(acc_full + i, 1);
-      mbar_init(acc_free + i, kRmWorkers);
+      mbar_init(acc_free + i, kRmEpi);
+      mbar_init(a_full + i, kRmBuilders);
+      mbar_init(a_free + i, 1);
     }
-    mbar_init(a_full, 128);
-    mbar_init(v_free, 1);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(tcols)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -766,13 +796,15 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       uint32_t ph = 0;
       int ck = 0, tcount = 0;
       bool ok = true, any = false;
-      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x, ++tcount) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const int nkb = P.res_kpad / 64, cw = P.res_cw;
         const uint32_t acols = (uint32_t)P.res_kpad / 2;
-        if (!mbar_wait(a_full, (uint32_t)(tcount & 1), abort_flag, T.status)) { ok = false; break; }
+        const int ab = tcount & 1;
+        if (!mbar_wait(a_full + ab, (uint32_t)((tcount >> 1) & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
+        const uint32_t abase = tmem + (uint32_t)ab * acols;
         for (int c = 0; ok && c < P.res_nchunk; ++c, ++ck) {
           const int s = ck & 1, use = ck >> 1;
           if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
@@ -782,14 +814,14 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           tc_fence_after();
           const int ncol = min(cw, P.res_npad - c * cw);       // a multiple of 16
           const uint32_t idesc = idesc_bf16(128, ncol);
-          const uint32_t d = tmem + acols + (uint32_t)(s * cw);
+          const uint32_t d = tmem + 2 * acols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
             tc_fence_after();
             const uint64_t db = desc_sw128(sRing + st * stage_bytes);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              umma_bf16_ta(d, tmem + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
+              umma_bf16_ta(d, abase + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
             umma_commit(empty + st);
             any = true;
             if (++st == stages) { st = 0; ph ^= 1u; }
@@ -797,101 +829,115 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           if (ok) umma_commit(acc_full + s);
         }
         if (!ok) break;
-        umma_commit(v_free);
-        ++tcount;
+        umma_commit(a_free + ab);
       }
       if (!ok && any) {
         umma_commit(drain);
         for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(drain, 0u); ++t) {}
       }
     }
-  } else {
-    // ------------------------------------------------------------ bytes + epilogues
-    const int wk = warp - 2;
-    const int half = wk >> 2;
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ byte builders
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;                 // TMEM lane = element of the tile
+    const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
-    int ck = 0, tcount = 0;
     bool ok = true;
+    int tcount = 0;
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
+      const int4 tl = tiles[i];
+      const ProbDev& P = T.probs[tl.x];
+      const int ab = tcount & 1;
+      if (tcount >= 2 && ok) ok = mbar_wait(a_free + ab, (uint32_t)(((tcount >> 1) - 1) & 1), abort_flag, T.status);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const int side = tl.y;
+      const int R = side ? P.N : P.M;
+      const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
+      const uint32_t acols = (uint32_t)P.res_kpad / 2;
+      const int nl = P.nl;
+      const uint64_t* limbs = side ? P.b_limbs : P.a_limbs;
+      const int64_t ps = side ? P.b_ps : P.a_ps;
+      const int64_t off = side ? ((int64_t)k * P.b_ld + line) : ((int64_t)line * P.a_ld + k);
+      bool nz = line < R && k < P.K && __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull;
+      const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
+      int ws = 0, bs = 0;
+      uint32_t carry = 0;
+      if (nz) {
+        const int e_line = side ? P.f[line] : P.e[line];
+        const int ex = __ldg((side ? P.b_exp : P.a_exp) + off);
+        const int Bb = 64 - (ex - e_line + P.t - 64 * nl);   // bit of sig * 2^64 that is bit 0 of |a_hat|
+        if (Bb - 1 >= 64 * nl + 64) {
+          nz = false;                                 // rounds to zero
+        } else {
+          ws = Bb >> 5;
+          bs = Bb & 31;
+          const int rbpos = Bb - 1;
+          const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
+          const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
+          uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
+          for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
+          const uint32_t w0 = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws - 2),
+                                              sig_word(limbs32, ps, off, nl, ws - 1), bs);
+          carry = rb & ((sticky != 0u) | (w0 & 1u));
+        }
+      }
+      const uint32_t abase = tlane + (uint32_t)ab * acols;
+      for (uint32_t c0 = 0; c0 < acols; c0 += 32) {  // 16 words = 64 bytes = 32 columns
+        uint32_t col[32];
+#pragma unroll
+        for (int w = 0; w < 16; ++w) {
+          uint32_t x = 0u;
+          if (nz) {
+            const int wi = (int)(c0 >> 1) + w;
+            const uint64_t y = (uint64_t)__funnelshift_r(sig_word(limbs32, ps, off, nl, ws + wi - 2),
+                                                         sig_word(limbs32, ps, off, nl, ws + wi - 1), bs) + carry;
+            x = (uint32_t)y;
+            carry = (uint32_t)(y >> 32);
+          }
+          col[2 * w] = bf16_byte(x & 0xffu) | (bf16_byte((x >> 8) & 0xffu) << 16);
+          col[2 * w + 1] = bf16_byte((x >> 16) & 0xffu) | (bf16_byte(x >> 24) << 16);
+        }
+        tmem_st32(abase + c0, col);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(a_full + ab);
+    }
+    if (!ok) *abort_flag = 1;
+  } else {
+    // ------------------------------------------------------------ epilogues
+    const int ew = warp - 6;
+    const int sub = ew >> 2;                          // column sub-group 0..3
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
+    int ck = 0;
+    bool ok = true;
+    for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
       const int side = tl.y;
       const int R = side ? P.N : P.M;
       const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
       const bool valid = line < R && k < P.K;
-      const uint32_t acols = (uint32_t)P.res_kpad / 2;
-      const int nl = P.nl;
-      const uint64_t* limbs = side ? P.b_limbs : P.a_limbs;
-      const int64_t ps = side ? P.b_ps : P.a_ps;
       const int64_t off = side ? ((int64_t)k * P.b_ld + line) : ((int64_t)line * P.a_ld + k);
-      bool nz = valid && __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull;
-      const bool neg = nz && __ldg((side ? P.b_sign : P.a_sign) + off) != 0;
-      if (half == 0) {
-        // ---- the bytes of |a_hat| into TMEM columns [0, kpad / 2)
-        if (tcount > 0 && ok) ok = mbar_wait(v_free, (uint32_t)((tcount - 1) & 1), abort_flag, T.status);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
-        int ws = 0, bs = 0;
-        uint32_t carry = 0;
-        if (nz) {
-          const int e_line = side ? P.f[line] : P.e[line];
-          const int ex = __ldg((side ? P.b_exp : P.a_exp) + off);
-          const int Bb = 64 - (ex - e_line + P.t - 64 * nl);   // bit of sig * 2^64 that is bit 0 of |a_hat|
-          if (Bb - 1 >= 64 * nl + 64) {
-            nz = false;                               // rounds to zero
-          } else {
-            ws = Bb >> 5;
-            bs = Bb & 31;
-            const int rbpos = Bb - 1;
-            const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
-            const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
-            uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
-            for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
-            const uint32_t w0 = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws - 2),
-                                                sig_word(limbs32, ps, off, nl, ws - 1), bs);
-            carry = rb & ((sticky != 0u) | (w0 & 1u));
-          }
-        }
-        for (uint32_t c0 = 0; c0 < acols; c0 += 32) {  // 16 words = 64 bytes = 32 columns
-          uint32_t col[32];
-#pragma unroll
-          for (int w = 0; w < 16; ++w) {
-            uint32_t x = 0u;
-            if (nz) {
-              const int wi = (int)(c0 >> 1) + w;
-              const uint64_t y = (uint64_t)__funnelshift_r(sig_word(limbs32, ps, off, nl, ws + wi - 2),
-                                                           sig_word(limbs32, ps, off, nl, ws + wi - 1), bs) + carry;
-              x = (uint32_t)y;
-              carry = (uint32_t)(y >> 32);
-            }
-            col[2 * w] = bf16_byte(x & 0xffu) | (bf16_byte((x >> 8) & 0xffu) << 16);
-            col[2 * w + 1] = bf16_byte((x >> 16) & 0xffu) | (bf16_byte(x >> 24) << 16);
-          }
-          tmem_st32(tlane + c0, col);
-        }
-        tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(a_full);
-      }
-      // ---- chunk epilogues: half h takes the 32-column groups g = h, h + 2, ...
+      const float sg = (valid && __ldg((side ? P.b_sign : P.a_sign) + off) != 0) ? -1.f : 1.f;
+      const uint32_t acols = (uint32_t)P.res_kpad / 2;
       const int L1 = P.L1, ncols = P.L1 + 2 * (P.L - P.L1), cw = P.res_cw;
       uint16_t* planes = side ? P.pb : P.pa;
       const int64_t pstride = (int64_t)R * P.Kp;
-      uint16_t* dst = planes + (int64_t)(valid ? line : 0) * P.Kp + (valid ? k : 0);
+      uint16_t* dst0 = planes + (int64_t)(valid ? line : 0) * P.Kp + (valid ? k : 0);
       for (int c = 0; c < P.res_nchunk; ++c, ++ck) {
         const int s = ck & 1, use = ck >> 1;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t trow = tlane + acols + (uint32_t)(s * cw);
+        const uint32_t trow = tlane + 2 * acols + (uint32_t)(s * cw);
         const int j0 = c * cw;
         const int ncolp = min(cw, P.res_npad - j0);    // columns written by the MMAs
-        for (int g = 32 * half; g < ncolp; g += 64) {
+        for (int g = 32 * sub; g < ncolp; g += 128) {
           uint32_t y[32];
           if (g + 32 <= ncolp) {
             tmem_ld32(trow + (uint32_t)g, y);
@@ -904,32 +950,57 @@ __global__ void __launch_bounds__(kRmThreads, 1)
             for (int q = 16; q < 32; ++q) y[q] = 0u;
           }
           if (!valid) continue;
+          const int col0 = j0 + g;
+          if (col0 + 32 <= L1) {
+            // 32 one-limb moduli: planes col0 .. col0 + 31
+            uint16_t* dp = dst0 + (int64_t)col0 * pstride;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int colx = j0 + g + q;
-            if (colx < L1) {
-              const float2 mc = s_mc[colx];
-              float x = fmodf_exact(__uint_as_float(y[q]), mc.x, mc.y);   // |a_hat| mod m in [0, m)
-              x = (2.f * x > mc.x) ? x - mc.x : x;                         // (-m/2, m/2]
-              if (neg && x != 0.f) x = -x;                                 // no -0: planes as the CUDA-core kernel
-              if (2.f * x == -mc.x) x = -x;                                // the even modulus: tie stays +m/2
-              dst[(int64_t)colx * pstride] = (uint16_t)(__float_as_uint(x) >> 16);
-            } else if (colx < ncols && ((colx - L1) & 1) == 0 && q + 1 < 32) {
-              const int l = L1 + ((colx - L1) >> 1);
-              const float2 mc = s_mc[l];
-              const float r0 = fmodf_exact(__uint_as_float(y[q]), mc.x, mc.y);
-              const float r1 = fmodf_exact(__uint_as_float(y[q + 1]), mc.x, mc.y);
-              float x = fmodf_exact(fmaf(128.f, r1, r0), mc.x, mc.y);     // < 2^21: exact
-              x = (2.f * x > mc.x) ? x - mc.x : x;
-              if (neg) x = -x;
-              const int xi = (int)x;
-              const int y0 = xi & 127;
-              const int lo = y0 > 64 ? y0 - 128 : y0;                      // cen(r mod 128)
-              const int hi = (xi - lo) >> 7;
-              const int64_t gp = L1 + 3 * (l - L1);
-              dst[gp * pstride] = (uint16_t)(__float_as_uint((float)lo) >> 16);
-              dst[(gp + 1) * pstride] = (uint16_t)(__float_as_uint((float)hi) >> 16);
-              dst[(gp + 2) * pstride] = (uint16_t)(__float_as_uint((float)(lo + hi)) >> 16);
+            for (int q = 0; q < 32; ++q) {
+              const float4 mc = s_mc[col0 + q];
+              const float r = cmod_f32(sg * __uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
+              *dp = (uint16_t)(__float_as_uint(r) >> 16);
+              dp += pstride;
+            }
+          } else if (col0 >= L1) {
+            // 16 two-limb pairs: moduli l = L1 + (col0 - L1) / 2 + i, planes L1 + 3 (l - L1) + {0, 1, 2}
+            const int lb = L1 + ((col0 - L1) >> 1);
+            uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (lb - L1)) * pstride;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (col0 + 2 * i < ncols) {
+                const float4 mc = s_mc[lb + i];
+                float x = cmod_f32(sg * pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                // balanced base-128 split: x = lo + 128 hi, lo in (-64, 64]
+                float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
+                float lo = fmaf(-128.f, hi, x);
+                if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
+                dp[0] = (uint16_t)(__float_as_uint(lo + 0.0f) >> 16);
+                dp[pstride] = (uint16_t)(__float_as_uint(hi + 0.0f) >> 16);
+                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi + 0.0f) >> 16);
+              }
+              dp += 3 * pstride;
+            }
+          } else {
+            // the group that holds the last one-limb moduli and the first pairs
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int colx = col0 + q;
+              if (colx < L1) {
+                const float4 mc = s_mc[colx];
+                const float r = cmod_f32(sg * __uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
+                dst0[(int64_t)colx * pstride] = (uint16_t)(__float_as_uint(r) >> 16);
+              } else if (colx < ncols && ((colx - L1) & 1) == 0) {
+                const int l = L1 + ((colx - L1) >> 1);
+                const float4 mc = s_mc[l];
+                float x = cmod_f32(sg * pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
+                float lo = fmaf(-128.f, hi, x);
+                if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
+                uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (l - L1)) * pstride;
+                dp[0] = (uint16_t)(__float_as_uint(lo + 0.0f) >> 16);
+                dp[pstride] = (uint16_t)(__float_as_uint(hi + 0.0f) >> 16);
+                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi + 0.0f) >> 16);
+              }
             }
           }
         }
@@ -944,33 +1015,27 @@ __global__ void __launch_bounds__(kRmThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
-// Chunk width and TMEM columns of the warp-specialised tensor-core residues:
-// the bytes take kpad / 2 columns, two slots of cw columns the rest; 256
-// columns (two CTAs per SM) when that needs no more chunks than 512.
+// Chunk width of the warp-specialised tensor-core residues: two byte buffers
+// (kpad / 2 columns each) and two accumulator slots of cw columns (a multiple
+// of 32) within the 512 TMEM columns.
 void residue_mm_geometry(int kpad, int npad, int* cw_out, int* tcols_out) {
-  auto cw_for = [&](int tc) {
-    int cw = (tc - kpad / 2) / 2;
-    cw = cw > 256 ? 256 : cw;
-    cw &= ~31;
-    const int need = (npad + 31) & ~31;
-    return cw < need ? cw : need;
-  };
-  const int c512 = cw_for(512), c256 = cw_for(256);
-  const bool small = c256 >= 32 && (npad + c256 - 1) / c256 == (npad + c512 - 1) / c512;
-  *cw_out = small ? c256 : c512;
-  *tcols_out = small ? 256 : 512;
+  int cw = (512 - kpad) / 2;
+  cw = cw > 256 ? 256 : cw;
+  cw &= ~31;
+  const int need = (npad + 31) & ~31;
+  *cw_out = cw < need ? cw : need;
+  *tcols_out = 512;
 }
 
-int residue_mm_smem_bytes(int cw_max, int lmax, int tcols, int* stages) {
+int residue_mm_smem_bytes(int cw_max, int lmax, int /*tcols*/, int* stages) {
   const uint32_t sb = (uint32_t)cw_max * 128u;
-  const int cap = tcols > 256 ? 227 * 1024 : 113 * 1024;
   for (int st = kRmMaxStages; st >= 2; --st) {
-    const int bytes = (int)RmLayout(sb, st, lmax, tcols).total;
-    if (bytes <= cap) {
+    const int bytes = (int)RmLayout(sb, st, lmax).total;
+    if (bytes <= 227 * 1024) {
       if (stages) *stages = st;
       return bytes;
     }
@@ -979,16 +1044,15 @@ int residue_mm_smem_bytes(int cw_max, int lmax, int tcols, int* stages) {
   return -1;
 }
 
-cudaError_t launch_residues_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int tcols,
+cudaError_t launch_residues_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int /*tcols*/,
                                int sms, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   int stages = 0;
-  const int smem = residue_mm_smem_bytes(cw_max, t.lmax, tcols, &stages);
+  const int smem = residue_mm_smem_bytes(cw_max, t.lmax, 512, &stages);
   if (smem < 0) return cudaErrorInvalidValue;
-  const int per_sm = 512 / tcols;
-  const int grid = std::min(ntiles, sms * per_sm);
+  const int grid = std::min(ntiles, sms);
   k_residue_mm<<<grid, kRmThreads, smem, s>>>(t, reinterpret_cast<const int4*>(tiles), ntiles,
-                                              (uint32_t)cw_max * 128u, stages, tcols);
+                                              (uint32_t)cw_max * 128u, stages);
   return cudaGetLastError();
 }
 

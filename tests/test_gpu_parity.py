@@ -201,16 +201,17 @@ def test_zero_lines_and_tiny_shapes(ozk):
 
 
 def test_p2048_small(ozk):
-    """p = 2048 (the largest precision): 32-limb inputs, 132-digit residue
-    class, two-limb moduli; the CRT both as tensor-core sums (the default at
-    this length) and on 32-lane CUDA-core groups; every stage bit-exact."""
+    """p = 2048 (the largest precision): 32-limb inputs, two-limb moduli; the
+    residues and the CRT both on the tensor cores (the defaults at this length)
+    and on the CUDA cores (132-digit residue class, 32-lane CRT groups); every
+    stage bit-exact."""
     rng = np.random.Generator(np.random.PCG64(2030))
     A = synth.mp_matrix(rng, 20, 24, 2048, -64, 64)
     B = synth.mp_matrix(rng, 24, 18, 2048, -64, 64)
     got, _ = assert_full_parity(ozk, A, B, 2048, truth=False)
-    assert got["plan"].info["crt_mode"] == 2
-    got3, _ = assert_full_parity(ozk, A, B, 2048, truth=False, crt_engine=3)
-    assert got3["plan"].info["crt_mode"] == 0
+    assert got["plan"].info["crt_mode"] == 2 and got["plan"].info["res_mode"] == 2
+    got3, _ = assert_full_parity(ozk, A, B, 2048, truth=False, crt_engine=3, res_engine=3)
+    assert got3["plan"].info["crt_mode"] == 0 and got3["plan"].info["res_mode"] == 0
 
 
 @pytest.mark.parametrize("p", [300, 700])

@@ -98,7 +98,7 @@ def test_argument_errors(ozk, args, status):
 def test_bad_options(ozk):
     h = C.c_void_p()
     for kw in ({"k_chunk": 100}, {"k_chunk": 2048}, {"engine": 7}, {"schedule": 9}, {"crt_engine": 4},
-               {"crt_engine": -1}, {"res_engine": 3}):
+               {"crt_engine": -1}, {"res_engine": 4}):
         st = ozk.lib().ozaki2_plan_create(64, 64, 64, 53, C.byref(ozk.opts(**kw)), C.byref(h))
         assert st == 1, kw
 
@@ -145,3 +145,13 @@ def test_crt_engine_choice(ozk):
     assert ozk.Plan(lo, crt_engine=2).info["crt_mode"] == 2
     assert ozk.Plan((8, 8, 64, 1024)).info["crt_mode"] == 0          # M N < 128
     assert ozk.Plan((64, 64, 64, 53), crt_engine=2).info["crt_mode"] == 0   # L < 32
+
+
+def test_residue_engine_choice(ozk):
+    """The automatic residue choice: the warp-specialised tensor-core kernel for
+    integers of more than 192 bytes, the CUDA cores below; engine 3 forces the
+    CUDA cores, engine 2 asks for the tensor cores up to 448 bytes."""
+    assert ozk.Plan((64, 64, 64, 2048)).info["res_mode"] == 2
+    assert ozk.Plan((64, 64, 64, 1024)).info["res_mode"] == 0
+    assert ozk.Plan((64, 64, 64, 2048), res_engine=3).info["res_mode"] == 0
+    assert ozk.Plan((64, 64, 64, 256), res_engine=2).info["res_mode"] == 2
