@@ -161,7 +161,7 @@ struct ProbHost {
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
                                // 2: tensor-core sums to R digits, then the finish
   int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp;
-  size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [2][upitch] u64
+  size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [4][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_tcols;           // res_mode 2: chunk width, chunks, TMEM columns
 };
@@ -471,7 +471,7 @@ static void layout_workspace(ozaki2_plan_s* pl) {
       const size_t up = align_up((size_t)(h.M * h.N), 8);
       off += align_up(4 * (size_t)h.crt_ngrp * 9 * up, 256);
       h.off_sig = off;
-      off += align_up(16 * up, 256);
+      off += align_up(32 * up, 256);              // four partial quotient sums
     }
   }
   pl->ws_bytes = off;

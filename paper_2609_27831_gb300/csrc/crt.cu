@@ -441,7 +441,8 @@ template <int ND>
 __device__ __forceinline__ void crt_assemble_regs(const ProbDev& P, const CrtView& cv, int64_t idx,
                                                   uint32_t (&R)[ND]) {
   const int64_t up = P.upitch;
-  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx]) >> 32;
+  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx] + P.crt_sig[2 * up + idx] +
+                          P.crt_sig[3 * up + idx]) >> 32;
   const int D = P.D32, ng = P.crt_ngrp;
   uint32_t w0[ND], w1[ND];
 #pragma unroll
@@ -852,6 +853,12 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
 // Block list entry: {problem, block of 128 outputs, 0, 0}.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 128;
+constexpr int kCmQuarters = 4;         // worker groups of the tensor-core CRT sums (partial quotient sums)
+
+// asynchronous 4-byte copy global -> shared (completes at cp.async.wait_group)
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
 
 __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const int4* __restrict__ blk) {
   extern __shared__ __align__(16) uint32_t sf[];
@@ -874,19 +881,23 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   const int64_t idx = (int64_t)b.y * kFinThreads + e;
   if (idx >= (int64_t)P.M * P.N) return;
   const int64_t up = P.upitch;
-  // the group words, independent coalesced loads: words 0..6 of group d / 7
-  // in digit order, and the overlap words 7, 8 of every group
-#pragma unroll 8
+  // the group words, copied asynchronously (all in flight at once; coalesced
+  // across the block): words 0..6 of group d / 7 in digit order, and the
+  // overlap words 7, 8 of every group
   for (int d = 0; d < D; ++d) {
     const int g = d / 7;
-    s_R[d * kFinThreads + e] = g < ng ? __ldg(P.crt_q + ((int64_t)g * 9 + (d - 7 * g)) * up + idx) : 0u;
+    if (g < ng) cp_async4(s_R + d * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + (d - 7 * g)) * up + idx);
+    else s_R[d * kFinThreads + e] = 0u;
   }
-#pragma unroll 4
   for (int g = 0; g < ng; ++g) {
-    s_W[(2 * g) * kFinThreads + e] = __ldg(P.crt_q + ((int64_t)g * 9 + 7) * up + idx);
-    s_W[(2 * g + 1) * kFinThreads + e] = __ldg(P.crt_q + ((int64_t)g * 9 + 8) * up + idx);
+    cp_async4(s_W + (2 * g) * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + 7) * up + idx);
+    cp_async4(s_W + (2 * g + 1) * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + 8) * up + idx);
   }
-  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx]) >> 32;
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+  uint64_t sig = 0;
+#pragma unroll
+  for (int h = 0; h < kCmQuarters; ++h) sig += P.crt_sig[h * up + idx];
+  const uint64_t alpha = sig >> 32;
   // pass 1, least significant digit first: R = (S + alpha~ (2^(32 D) - P)) mod
   // 2^(32 D), and the carries out of R + (2^(32 D) - P) (R >= P), of
   // R + (2^(32 D) - floor(P/2) - 1) and of (R - P) + the same (the sign of the
@@ -959,18 +970,18 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 //               tiles); commits per ring stage and per chunk
 //   warp 2      TMA producer of the tile's v values, 32 moduli x 128 outputs
 //               per copy, into a four-slot ring
-//   warps 3-10  two threads per output (its TMEM lane), halves h = 0, 1:
-//               half h writes the V columns of the copies of its parity (one
+//   warps 3-18  four threads per output (its TMEM lane), groups h = 0..3:
+//               group h writes the V columns of the copies c = h mod 4 (one
 //               tcgen05.st of 32 columns each) and its part of the quotient
 //               sum sum_l v_l floor(2^32 / m_l); then, for every chunk, the
-//               groups of 32 columns of its parity.
+//               32-column groups g = h mod 4.
 // A warp rewrites its V columns only after the commit that follows the
 // previous tile's last MMA, and the next tile's MMAs wait for every warp's V
 // columns (tcgen05.st waited and fenced), so V is never read and written at
-// once; an accumulator slot is reused only after both halves have read it.
+// once; an accumulator slot is reused only after every worker has read it.
 // Tile list entry: {problem, tile, 0, 0}.
 // ---------------------------------------------------------------------------
-constexpr int kCmWorkers = 256;
+constexpr int kCmWorkers = 512;
 constexpr int kCmThreads = 96 + kCmWorkers;
 constexpr int kCmMaxStages = 24;
 constexpr int kCmUMods = 32;                         // moduli per v copy
@@ -1048,7 +1059,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     for (int i = 0; i < 2; ++i) mbar_init(acc_full + i, 1);
     mbar_init(v_full, kCmWorkers);
     mbar_init(v_free, 1);
-    for (int i = 0; i < 2; ++i) mbar_init(acc_free + i, kCmWorkers);   // both halves read every chunk
+    for (int i = 0; i < 2; ++i) mbar_init(acc_free + i, kCmWorkers);   // every worker reads every chunk
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1171,7 +1182,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
   } else {
     // ------------------------------------------------------------ V columns + chunk epilogues
     const int wk = warp - 3;
-    const int half = wk >> 2;
+    const int half = wk >> 2;                         // worker group 0..3
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
@@ -1194,7 +1205,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       const int64_t up = P.upitch;
       uint64_t sig = 0;
       for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
-        if ((uc & 1) != half) continue;             // the other half's copy
+        if ((uc & 3) != half) continue;             // another group's copy
         const int s = uc % kCmUSlots, use = uc / kCmUSlots;
         if (ok) ok = mbar_wait(u_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
@@ -1216,7 +1227,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(v_full);
-      // chunk epilogues: half h takes the 32-column groups g = h, h + 2, ...
+      // chunk epilogues: group h takes the 32-column groups g = h, h + 4, ...
       for (int c = 0; c < P.crt_nchunk; ++c, ++ck) {
         const int s = ck & 1, use = ck >> 1;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
@@ -1225,7 +1236,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         tc_fence_after();
         const uint32_t trow = tlane + vcols + (uint32_t)(s * cw);
         const int ncol = min(cw, P.crt_npad - c * cw);       // columns written by the MMAs
-        for (int g = 32 * half; g < cw; g += 64) {
+        for (int g = 32 * half; g < cw; g += 128) {
           uint64_t acc[7] = {0, 0, 0, 0, 0, 0, 0};
           if (g + 32 <= ncol) {
             uint32_t y[32];

@@ -115,7 +115,7 @@ def test_null_pointer_errors(ozk):
 
 def test_crt_sum_engine_workspace(ozk):
     """crt_engine 2 adds the group sums ([groups of 32 columns][9][M N rounded
-    to 8] uint32) and the two partial quotient sums ([2][M N rounded to 8]
+    to 8] uint32) and the four partial quotient sums ([4][M N rounded to 8]
     uint64) to the workspace where it applies, and nothing where it does not."""
     shape = (256, 256, 64, 1024)
     base = ozk.Plan(shape, crt_engine=3).info
@@ -129,7 +129,7 @@ def test_crt_sum_engine_workspace(ozk):
     cw = min(256, ((512 - kpad // 2) // 2) // 32 * 32, -(-npad // 32) * 32)
     ngrp, up = -(-npad // cw) * cw // 32, 256 * 256
     a256 = lambda x: -(-x // 256) * 256
-    assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(16 * up)
+    assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(32 * up)
     small = (4, 4, 4, 53)                        # M N < 128: the CUDA-core CRT
     assert ozk.Plan(small, crt_engine=2).info["workspace_bytes"] == ozk.Plan(small, crt_engine=3).info["workspace_bytes"]
 
