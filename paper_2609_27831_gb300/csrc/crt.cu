@@ -884,14 +884,15 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   // the group words, copied asynchronously (all in flight at once; coalesced
   // across the block): words 0..6 of group d / 7 in digit order, and the
   // overlap words 7, 8 of every group
+  const uint32_t* const qcol = P.crt_q + idx;   // in a register across the copies' memory clobbers
   for (int d = 0; d < D; ++d) {
     const int g = d / 7;
-    if (g < ng) cp_async4(s_R + d * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + (d - 7 * g)) * up + idx);
+    if (g < ng) cp_async4(s_R + d * kFinThreads + e, qcol + ((int64_t)g * 9 + (d - 7 * g)) * up);
     else s_R[d * kFinThreads + e] = 0u;
   }
   for (int g = 0; g < ng; ++g) {
-    cp_async4(s_W + (2 * g) * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + 7) * up + idx);
-    cp_async4(s_W + (2 * g + 1) * kFinThreads + e, P.crt_q + ((int64_t)g * 9 + 8) * up + idx);
+    cp_async4(s_W + (2 * g) * kFinThreads + e, qcol + ((int64_t)g * 9 + 7) * up);
+    cp_async4(s_W + (2 * g + 1) * kFinThreads + e, qcol + ((int64_t)g * 9 + 8) * up);
   }
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
   uint64_t sig = 0;
@@ -1087,8 +1088,8 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const CUtensorMap* mt = T.tmaps + 2 * T.count + tl.x;
-        const int nkb = P.crt_kpad / 64, cw = P.crt_cw;
-        for (int c = 0; ok && c < P.crt_nchunk; ++c) {
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk;
+        for (int c = 0; ok && c < nchunk; ++c) {
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
             mbar_expect_tx(full + st, (uint32_t)cw * 128u);
@@ -1115,18 +1116,18 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
-        const int nkb = P.crt_kpad / 64, cw = P.crt_cw;
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
         const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
         if (!mbar_wait(v_full, (uint32_t)(tcount & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
-        for (int c = 0; ok && c < P.crt_nchunk; ++c, ++ck) {
+        for (int c = 0; ok && c < nchunk; ++c, ++ck) {
           const int s = ck & 1, use = ck >> 1;
           if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const int ncol = min(cw, P.crt_npad - c * cw);       // a multiple of 16
+          const int ncol = min(cw, npad - c * cw);             // a multiple of 16
           const uint32_t idesc = idesc_bf16(128, ncol);
           const uint32_t d = tmem + vcols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
@@ -1163,7 +1164,8 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const CUtensorMap* mu_ = T.tmaps + 3 * T.count + tl.x;
-        for (int l0 = 0; l0 < P.L; l0 += kCmUMods, ++uc) {
+        const int L = P.L;
+        for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
           const int s = uc % kCmUSlots, use = uc / kCmUSlots;
           if (use > 0 && !mbar_wait(u_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
             ok = false;
@@ -1192,17 +1194,21 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
-      const int L = P.L, cw = P.crt_cw;
+      // the problem's fields in registers before the waits (their memory
+      // clobbers would reload them from global memory after every barrier)
+      const int L = P.L, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
+      const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
+      const int64_t idx = (int64_t)tl.y * 128 + row;
+      const bool valid = idx < (int64_t)P.M * P.N;
+      const int64_t up = P.upitch;
+      uint32_t* const qbase = P.crt_q;
+      uint64_t* const sigbase = P.crt_sig;
       // V may be rewritten once every MMA of the previous tile is done (a
       // half may have had no chunk of that tile to wait for)
       if (tcount > 0 && ok) ok = mbar_wait(v_free, (uint32_t)((tcount - 1) & 1), abort_flag, T.status);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
-      const int64_t idx = (int64_t)tl.y * 128 + row;
-      const bool valid = idx < (int64_t)P.M * P.N;
-      const int64_t up = P.upitch;
       uint64_t sig = 0;
       for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
         if ((uc & 3) != half) continue;             // another group's copy
@@ -1223,19 +1229,19 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         tmem_st32(tlane + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
       }
       if (!ok) break;
-      if (valid) P.crt_sig[half * up + idx] = sig;
+      if (valid) sigbase[half * up + idx] = sig;
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(v_full);
       // chunk epilogues: group h takes the 32-column groups g = h, h + 4, ...
-      for (int c = 0; c < P.crt_nchunk; ++c, ++ck) {
+      for (int c = 0; c < nchunk; ++c, ++ck) {
         const int s = ck & 1, use = ck >> 1;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
         const uint32_t trow = tlane + vcols + (uint32_t)(s * cw);
-        const int ncol = min(cw, P.crt_npad - c * cw);       // columns written by the MMAs
+        const int ncol = min(cw, npad - c * cw);             // columns written by the MMAs
         for (int g = 32 * half; g < cw; g += 128) {
           uint64_t acc[7] = {0, 0, 0, 0, 0, 0, 0};
           if (g + 32 <= ncol) {
@@ -1248,7 +1254,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
             crt_group<16>(y, acc);
           }
           // group sum as 9 words: 7 word sums with carries, then the carry
-          uint32_t* qcol = P.crt_q + (int64_t)((c * cw + g) >> 5) * 9 * up + (valid ? idx : 0);
+          uint32_t* qcol = qbase + (int64_t)((c * cw + g) >> 5) * 9 * up + (valid ? idx : 0);
           uint64_t carry = 0;
 #pragma unroll
           for (int k = 0; k < 7; ++k) {

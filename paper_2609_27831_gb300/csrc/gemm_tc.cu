@@ -217,14 +217,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     while (ok && it.next(j)) {
       const ProbDev& P = T.probs[j.u.prob];
       const int s = j.slot;
+      const int k0 = j.chunk * P.kchunk;
+      const int k1 = min(P.K, k0 + P.kchunk);
       if (uses[s] > 0) {
         if (!mbar_wait(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status)) { ok = false; break; }
       }
       ++uses[s];
       tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(s * kBN);
-      const int k0 = j.chunk * P.kchunk;
-      const int k1 = min(P.K, k0 + P.kchunk);
       bool acc = !j.first;
       for (int k = k0; k < k1; k += kBK) {
         if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
@@ -260,18 +260,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     int uses[2] = {0, 0};
     while (it.next(j)) {
       const int s = j.slot;
-      if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status)) break;
-      ++uses[s];
-      tc_fence_after();
+      // the job's constants in registers before the wait: they load while it
+      // waits, and the barrier's memory clobber does not reload them
       const ProbDev& P = T.probs[j.u.prob];
       const ModConst mc = T.mods[j.u.ell];
       const float mf = (float)mc.m;
+      const int PM = P.M, PN = P.N;
       const int row = j.u.tm * kBM + quad * 32 + lane;
       const uint32_t tbase =
           tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kBN + half * 128);
-      uint16_t* urow = P.u + (int64_t)j.u.ell * P.upitch + (int64_t)row * P.N;
+      uint16_t* urow = P.u + (int64_t)j.u.ell * P.upitch + (int64_t)row * PN;
       const int col_base = j.u.tn * kBN + half * 128;
-      const bool vec_ok = (P.N & 7) == 0;
+      const bool vec_ok = (PN & 7) == 0;
+      // final coefficient; for the tensor-core CRT sums also times
+      // M_l^{-1} mod m_l, so that the stored value is v_l (Sec. 4.4)
+      uint32_t fin = mc.kfin;
+      if (j.last && P.crt_mode == 2)
+        fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
+      if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status)) break;
+      ++uses[s];
+      tc_fence_after();
 #pragma unroll 1
       for (int c = 0; c < 4; ++c) {
         uint32_t v[32];
@@ -285,10 +293,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
           }
           tmem_st32(tbase + (uint32_t)(c * 32), v);
         } else {
-          // final coefficient; for the tensor-core CRT sums also times
-          // M_l^{-1} mod m_l, so that the stored value is v_l (Sec. 4.4)
-          uint32_t fin = mc.kfin;
-          if (P.crt_mode == 2) fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
@@ -296,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             v[i] = r;
           }
           const int col0 = col_base + c * 32;
-          if (row < P.M) {
-            if (vec_ok && col0 + 32 <= P.N) {
+          if (row < PM) {
+            if (vec_ok && col0 + 32 <= PN) {
               uint4* dst = reinterpret_cast<uint4*>(urow + col0);
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
             } else {
 #pragma unroll
               for (int i = 0; i < 32; ++i)
-                if (col0 + i < P.N) urow[col0 + i] = (uint16_t)v[i];
+                if (col0 + i < PN) urow[col0 + i] = (uint16_t)v[i];
             }
           }
         }

@@ -772,8 +772,8 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const CUtensorMap* mt = T.tmaps + 4 * T.count + tl.x;
-        const int nkb = P.res_kpad / 64, cw = P.res_cw;
-        for (int c = 0; ok && c < P.res_nchunk; ++c) {
+        const int nkb = P.res_kpad / 64, cw = P.res_cw, nchunk = P.res_nchunk;
+        for (int c = 0; ok && c < nchunk; ++c) {
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
             mbar_expect_tx(full + st, (uint32_t)cw * 128u);
@@ -799,20 +799,20 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x, ++tcount) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
-        const int nkb = P.res_kpad / 64, cw = P.res_cw;
+        const int nkb = P.res_kpad / 64, cw = P.res_cw, nchunk = P.res_nchunk, npad = P.res_npad;
         const uint32_t acols = (uint32_t)P.res_kpad / 2;
         const int ab = tcount & 1;
         if (!mbar_wait(a_full + ab, (uint32_t)((tcount >> 1) & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
         const uint32_t abase = tmem + (uint32_t)ab * acols;
-        for (int c = 0; ok && c < P.res_nchunk; ++c, ++ck) {
+        for (int c = 0; ok && c < nchunk; ++c, ++ck) {
           const int s = ck & 1, use = ck >> 1;
           if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const int ncol = min(cw, P.res_npad - c * cw);       // a multiple of 16
+          const int ncol = min(cw, npad - c * cw);             // a multiple of 16
           const uint32_t idesc = idesc_bf16(128, ncol);
           const uint32_t d = tmem + 2 * acols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
@@ -925,10 +925,11 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       const float sg = (valid && __ldg((side ? P.b_sign : P.a_sign) + off) != 0) ? -1.f : 1.f;
       const uint32_t acols = (uint32_t)P.res_kpad / 2;
       const int L1 = P.L1, ncols = P.L1 + 2 * (P.L - P.L1), cw = P.res_cw;
+      const int nchunk = P.res_nchunk, npad = P.res_npad;
       uint16_t* planes = side ? P.pb : P.pa;
       const int64_t pstride = (int64_t)R * P.Kp;
       uint16_t* dst0 = planes + (int64_t)(valid ? line : 0) * P.Kp + (valid ? k : 0);
-      for (int c = 0; c < P.res_nchunk; ++c, ++ck) {
+      for (int c = 0; c < nchunk; ++c, ++ck) {
         const int s = ck & 1, use = ck >> 1;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
@@ -936,7 +937,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         tc_fence_after();
         const uint32_t trow = tlane + 2 * acols + (uint32_t)(s * cw);
         const int j0 = c * cw;
-        const int ncolp = min(cw, P.res_npad - j0);    // columns written by the MMAs
+        const int ncolp = min(cw, npad - j0);          // columns written by the MMAs
         for (int g = 32 * sub; g < ncolp; g += 128) {
           uint32_t y[32];
           if (g + 32 <= ncolp) {
