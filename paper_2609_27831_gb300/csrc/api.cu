@@ -160,7 +160,7 @@ struct ProbHost {
   bool skip_a, skip_b;         // planes of that side are written by the caller
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
                                // 2: tensor-core sums to R digits, then the finish
-  int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp;
+  int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot;
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [4][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_tcols;           // res_mode 2: chunk width, chunks, TMEM columns
@@ -357,7 +357,8 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     h.crt_kpad = kpad;
     h.crt_npad = npad;
     h.crt_np = np;
-    h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad) : 0;
+    h.crt_nslot = 2;
+    h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad, &h.crt_nslot) : 0;
     h.crt_nchunk = mm_ok ? (npad + h.crt_cw - 1) / h.crt_cw : 0;
     h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
     const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
@@ -767,7 +768,8 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       return OZ2_EINTERNAL;
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
-    if (h.crt_mode == 2 && (ti.cmt_cw < h.crt_cw || h.crt_cw % 32 != 0 || h.crt_kpad / 2 + 2 * h.crt_cw > 512 ||
+    if (h.crt_mode == 2 && (ti.cmt_cw < h.crt_cw || h.crt_cw % 32 != 0 ||
+                            h.crt_kpad / 2 + h.crt_nslot * h.crt_cw > 512 ||
                             (h.crt_cls <= 8 ? ti.crt_l[h.crt_cls] < h.L
                                             : (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
       return OZ2_EINTERNAL;
@@ -969,6 +971,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_q = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_q) : nullptr;
     P.crt_sig = h.crt_mode == 2 ? reinterpret_cast<uint64_t*>(ws + h.off_sig) : nullptr;
     P.crt_ngrp = h.crt_ngrp;
+    P.crt_nslot = h.crt_nslot;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
     if (rc) return rc;
     rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);

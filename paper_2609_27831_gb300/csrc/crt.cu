@@ -958,8 +958,9 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 //
 // Per tile of 128 consecutive outputs, V lives in tensor memory: TMEM lane r
 // holds output r's row, column l the bf16 pair (v0_l, v1_l).  The columns of
-// Y run in chunks of cw (a multiple of 32, kpad / 2 + 2 cw <= 512) through
-// two TMEM accumulator slots after V; the B blocks (64 k x cw columns) stream
+// Y run in chunks of cw (a multiple of 32) through two TMEM accumulator slots
+// after V (kpad / 2 + 2 cw <= 512), or through one slot when two would make
+// the MMAs narrower than 128 columns; the B blocks (64 k x cw columns) stream
 // through a shared-memory ring.  32 consecutive pieces span exactly 7 words,
 // so group g of 32 columns is the integer
 //   Q_g = sum_{q < 32} Y_{32 g + q} 2^(7 q),   S = sum_g Q_g 2^(224 g),
@@ -967,8 +968,8 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 // Q_g is written on its own as 9 words (7 carried word sums and the carry),
 // and the finish adds the groups and alpha~ (2^(32 D) - P).
 //   warp 0      TMA producer of the B blocks, in (chunk, K block) order
-//   warp 1      MMA issuer: chunk c into slot c & 1 (counted over the CTA's
-//               tiles); commits per ring stage and per chunk
+//   warp 1      MMA issuer: chunks into the slots in turn (one slot: always
+//               slot 0); commits per ring stage, per chunk and per tile
 //   warp 2      TMA producer of the tile's v values, 32 moduli x 128 outputs
 //               per copy, into a four-slot ring
 //   warps 3-18  four threads per output (its TMEM lane), groups h = 0..3:
@@ -1111,17 +1112,19 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     if (lane == 0) {
       int st = 0;
       uint32_t ph = 0;
-      int ck = 0, tcount = 0;
+      int next = 0, uses[2] = {0, 0}, tcount = 0;
       bool ok = true, any = false;
       for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
+        const int nslot = P.crt_nslot;
         const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
         if (!mbar_wait(v_full, (uint32_t)(tcount & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
-        for (int c = 0; ok && c < nchunk; ++c, ++ck) {
-          const int s = ck & 1, use = ck >> 1;
+        for (int c = 0; ok && c < nchunk; ++c) {
+          const int s = nslot == 2 ? next : 0, use = uses[s]++;
+          next = nslot == 2 ? next ^ 1 : 0;
           if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
             ok = false;
             break;
@@ -1189,14 +1192,14 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
     const uint16_t* s_u = reinterpret_cast<const uint16_t*>(sm + lay.u_off);
-    int ck = 0, uc = 0, tcount = 0;
+    int next = 0, uses[2] = {0, 0}, uc = 0, tcount = 0;
     bool ok = true;
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
       // the problem's fields in registers before the waits (their memory
       // clobbers would reload them from global memory after every barrier)
-      const int L = P.L, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
+      const int L = P.L, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad, nslot = P.crt_nslot;
       const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
       const int64_t idx = (int64_t)tl.y * 128 + row;
       const bool valid = idx < (int64_t)P.M * P.N;
@@ -1234,8 +1237,9 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       tc_fence_before();
       mbar_arrive(v_full);
       // chunk epilogues: group h takes the 32-column groups g = h, h + 4, ...
-      for (int c = 0; c < nchunk; ++c, ++ck) {
-        const int s = ck & 1, use = ck >> 1;
+      for (int c = 0; c < nchunk; ++c) {
+        const int s = nslot == 2 ? next : 0, use = uses[s]++;
+        next = nslot == 2 ? next ^ 1 : 0;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
@@ -1351,13 +1355,23 @@ cudaError_t launch_crt_tc(const DevTables& t, int cls, const int32_t* tiles, int
 }
 
 // Chunk width of the tensor-core CRT sums: columns of Y per TMEM slot, a
-// multiple of 32 with V (kpad / 2 columns) and two slots within 512 columns.
-int crt_mm_chunk(int kpad, int npad) {
-  int cw = (512 - kpad / 2) / 2;
-  cw = cw > 256 ? 256 : cw;
-  cw &= ~31;
+// multiple of 32, with V (kpad / 2 columns) and one or two slots within 512
+// columns.
+int crt_mm_chunk(int kpad, int npad, int* nslot) {
+  // two slots (the epilogue of one chunk overlaps the MMAs of the next)
+  // unless that leaves chunks narrower than 128 columns: one slot then, for
+  // MMAs of N >= 128 (narrow MMAs cost as much to issue as they compute)
   const int need = (npad + 31) & ~31;
-  return cw < need ? cw : need;
+  int cw2 = ((512 - kpad / 2) / 2) & ~31;
+  cw2 = cw2 > 256 ? 256 : cw2;
+  if (cw2 >= 128 || cw2 >= need) {
+    if (nslot) *nslot = 2;
+    return cw2 < need ? cw2 : need;
+  }
+  int cw1 = (512 - kpad / 2) & ~31;
+  cw1 = cw1 > 256 ? 256 : cw1;
+  if (nslot) *nslot = 1;
+  return cw1 < need ? cw1 : need;
 }
 
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages) {

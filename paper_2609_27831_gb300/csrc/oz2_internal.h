@@ -87,7 +87,7 @@ struct ProbDev {
   int32_t crt_ngrp;      // crt_mode 2: groups of 32 columns, nchunk cw / 32
   int32_t res_cw;        // res_mode 2: columns of Y per chunk (a multiple of 32)
   int32_t res_nchunk;    // res_mode 2: chunks
-  int32_t pad7;
+  int32_t crt_nslot;     // crt_mode 2: TMEM accumulator slots (1 or 2)
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -162,7 +162,7 @@ int crt_tc_smem_bytes(int cls, int kpad_max, int npad_max, int lmax, int nbuf);
 // accumulators (> 40 digits), blocks of 128 outputs {problem, block}.
 cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int grid,
                           cudaStream_t s);
-int crt_mm_chunk(int kpad, int npad);
+int crt_mm_chunk(int kpad, int npad, int* nslot);
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
 cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
                                    cudaStream_t s);
