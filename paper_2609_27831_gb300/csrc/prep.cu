@@ -838,6 +838,13 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------ byte builders
+    // Per element: S = sig 2^64 as 64-bit limbs S[j] (S[0] = 0, S[j] = limb
+    // j - 1), |a_hat| = bits Bb.. of S plus the round-half-even increment.
+    // Every limb read is unconditional at a clamped address (masked to zero
+    // outside the significand), so the reads of a step are all in flight at
+    // once; the reads that fix the rounding run before the wait for the
+    // buffer.  The element's sign goes onto the bf16 bytes (-0 for a zero
+    // byte is harmless: the epilogue's + 0.0f turns a -0 result into +0).
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
@@ -847,56 +854,61 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
       const int ab = tcount & 1;
+      const int side = tl.y;
+      const int R = side ? P.N : P.M;
+      const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
+      const bool valid = line < R && k < P.K;
+      const uint32_t acols = (uint32_t)P.res_kpad / 2;
+      const int nl = P.nl;
+      const int64_t ps = side ? P.b_ps : P.a_ps;
+      const int64_t off = valid ? (side ? ((int64_t)k * P.b_ld + line) : ((int64_t)line * P.a_ld + k)) : 0;
+      const uint64_t* el = (side ? P.b_limbs : P.a_limbs) + off;
+      auto S = [&](int j) -> uint64_t {            // limb j of sig 2^64, 0 outside
+        const bool in = (unsigned)(j - 1) < (unsigned)nl;
+        const uint64_t v = __ldg(el + (int64_t)(in ? j - 1 : 0) * ps);
+        return in ? v : 0ull;
+      };
+      const uint64_t top = __ldg(el + (int64_t)(nl - 1) * ps);
+      const int ex = __ldg((side ? P.b_exp : P.a_exp) + off);
+      const int e_line = __ldg((side ? P.f : P.e) + (valid ? line : 0));
+      const bool neg = __ldg((side ? P.b_sign : P.a_sign) + off) != 0;
+      int Bb = 64 - (ex - e_line + P.t - 64 * nl);  // bit of S that is bit 0 of |a_hat|
+      const bool nz = valid && top != 0ull && Bb - 1 < 64 * nl + 64;
+      Bb = nz ? Bb : 64;
+      // round bit (bit Bb - 1 of S), sticky bits below it, lowest kept bit
+      const int rbpos = Bb - 1, lr = rbpos >> 6;
+      const uint64_t srb = S(lr), slo = S(Bb >> 6);
+      const uint32_t rb = (uint32_t)(srb >> (rbpos & 63)) & 1u;
+      uint64_t sticky = srb & ((1ull << (rbpos & 63)) - 1ull);
+      for (int j = lr - 1; j >= 1 && !sticky; --j) sticky |= S(j);
+      uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(slo >> (Bb & 63)) & 1u))) : 0u;
+      const int ws = Bb >> 5, bs = Bb & 31, lq = ws >> 1;
+      const bool odd = ws & 1;
+      const uint32_t sgn = neg ? 0x80008000u : 0u;
       if (tcount >= 2 && ok) ok = mbar_wait(a_free + ab, (uint32_t)(((tcount >> 1) - 1) & 1), abort_flag, T.status);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      const int side = tl.y;
-      const int R = side ? P.N : P.M;
-      const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
-      const uint32_t acols = (uint32_t)P.res_kpad / 2;
-      const int nl = P.nl;
-      const uint64_t* limbs = side ? P.b_limbs : P.a_limbs;
-      const int64_t ps = side ? P.b_ps : P.a_ps;
-      const int64_t off = side ? ((int64_t)k * P.b_ld + line) : ((int64_t)line * P.a_ld + k);
-      bool nz = line < R && k < P.K && __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull;
-      const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
-      int ws = 0, bs = 0;
-      uint32_t carry = 0;
-      if (nz) {
-        const int e_line = side ? P.f[line] : P.e[line];
-        const int ex = __ldg((side ? P.b_exp : P.a_exp) + off);
-        const int Bb = 64 - (ex - e_line + P.t - 64 * nl);   // bit of sig * 2^64 that is bit 0 of |a_hat|
-        if (Bb - 1 >= 64 * nl + 64) {
-          nz = false;                                 // rounds to zero
-        } else {
-          ws = Bb >> 5;
-          bs = Bb & 31;
-          const int rbpos = Bb - 1;
-          const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
-          const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
-          uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
-          for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
-          const uint32_t w0 = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws - 2),
-                                              sig_word(limbs32, ps, off, nl, ws - 1), bs);
-          carry = rb & ((sticky != 0u) | (w0 & 1u));
-        }
-      }
       const uint32_t abase = tlane + (uint32_t)ab * acols;
       for (uint32_t c0 = 0; c0 < acols; c0 += 32) {  // 16 words = 64 bytes = 32 columns
+        // 32-bit words ws + 16 it .. ws + 16 it + 16 of S come from limbs lq + 8 it .. + 8
+        uint64_t lm[9];
+        const int j0 = lq + (int)(c0 >> 2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) lm[q] = S(j0 + q);
+        auto word = [&](int x) -> uint32_t {        // word x of the window (x + odd of the limbs)
+          const uint32_t a = (x & 1) ? (uint32_t)(lm[x >> 1] >> 32) : (uint32_t)lm[x >> 1];
+          const uint32_t b = (x & 1) ? (uint32_t)lm[(x + 1) >> 1] : (uint32_t)(lm[x >> 1] >> 32);
+          return odd ? b : a;
+        };
         uint32_t col[32];
 #pragma unroll
         for (int w = 0; w < 16; ++w) {
-          uint32_t x = 0u;
-          if (nz) {
-            const int wi = (int)(c0 >> 1) + w;
-            const uint64_t y = (uint64_t)__funnelshift_r(sig_word(limbs32, ps, off, nl, ws + wi - 2),
-                                                         sig_word(limbs32, ps, off, nl, ws + wi - 1), bs) + carry;
-            x = (uint32_t)y;
-            carry = (uint32_t)(y >> 32);
-          }
-          col[2 * w] = bf16_byte(x & 0xffu) | (bf16_byte((x >> 8) & 0xffu) << 16);
-          col[2 * w + 1] = bf16_byte((x >> 16) & 0xffu) | (bf16_byte(x >> 24) << 16);
+          const uint64_t y = (uint64_t)__funnelshift_r(word(w), word(w + 1), bs) + carry;
+          const uint32_t x = nz ? (uint32_t)y : 0u;
+          carry = (uint32_t)(y >> 32);
+          col[2 * w] = (bf16_byte(x & 0xffu) | (bf16_byte((x >> 8) & 0xffu) << 16)) | sgn;
+          col[2 * w + 1] = (bf16_byte((x >> 16) & 0xffu) | (bf16_byte(x >> 24) << 16)) | sgn;
         }
         tmem_st32(abase + c0, col);
       }
@@ -921,8 +933,6 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       const int R = side ? P.N : P.M;
       const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
       const bool valid = line < R && k < P.K;
-      const int64_t off = side ? ((int64_t)k * P.b_ld + line) : ((int64_t)line * P.a_ld + k);
-      const float sg = (valid && __ldg((side ? P.b_sign : P.a_sign) + off) != 0) ? -1.f : 1.f;
       const uint32_t acols = (uint32_t)P.res_kpad / 2;
       const int L1 = P.L1, ncols = P.L1 + 2 * (P.L - P.L1), cw = P.res_cw;
       const int nchunk = P.res_nchunk, npad = P.res_npad;
@@ -958,7 +968,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const float4 mc = s_mc[col0 + q];
-              const float r = cmod_f32(sg * __uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
+              const float r = cmod_f32(__uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
               *dp = (uint16_t)(__float_as_uint(r) >> 16);
               dp += pstride;
             }
@@ -970,7 +980,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
             for (int i = 0; i < 16; ++i) {
               if (col0 + 2 * i < ncols) {
                 const float4 mc = s_mc[lb + i];
-                float x = cmod_f32(sg * pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                float x = cmod_f32(pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
                 // balanced base-128 split: x = lo + 128 hi, lo in (-64, 64]
                 float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
                 float lo = fmaf(-128.f, hi, x);
@@ -988,12 +998,12 @@ __global__ void __launch_bounds__(kRmThreads, 1)
               const int colx = col0 + q;
               if (colx < L1) {
                 const float4 mc = s_mc[colx];
-                const float r = cmod_f32(sg * __uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
+                const float r = cmod_f32(__uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
                 dst0[(int64_t)colx * pstride] = (uint16_t)(__float_as_uint(r) >> 16);
               } else if (colx < ncols && ((colx - L1) & 1) == 0) {
                 const int l = L1 + ((colx - L1) >> 1);
                 const float4 mc = s_mc[l];
-                float x = cmod_f32(sg * pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                float x = cmod_f32(pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
                 float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
                 float lo = fmaf(-128.f, hi, x);
                 if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
