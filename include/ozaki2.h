@@ -104,8 +104,8 @@ typedef struct {
                      32 <= L <= 448 and M N >= 128 (CUDA cores otherwise); the reduced-product
                      region then holds v_l = (c mod m_l) M_l^{-1} mod m_l, M_l = P / m_l;
                      3: the CRT on the CUDA cores only */
-  int res_engine; /* 0: automatic (default): engine 2 for integers of more than 192 bytes
-                     (p above about 1500), CUDA cores otherwise; 1: residues as an exact bf16
+  int res_engine; /* 0: automatic (default): engine 2 for integers of more than 72 bytes
+                     (p above about 550), CUDA cores otherwise; 1: residues as an exact bf16
                      GEMM of the bytes of a_hat with a table of centered 2^(8b) mod m on the
                      tensor cores where the table has <= 256 rows and <= 256 bytes (CUDA cores
                      otherwise); 2: the same GEMM, warp-specialised (bytes in tensor memory, table

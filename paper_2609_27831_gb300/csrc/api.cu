@@ -398,9 +398,10 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
                   residue_tc_smem_bytes(kpad, npad, L) <= 227 * 1024) ? 1 : 0;
     // warp-specialised form: two byte buffers (kpad / 2 TMEM columns each) and
     // two slots of at least 32 columns; sums exact for <= 512 bytes.  The
-    // automatic choice takes it for integers of more than 192 bytes, where it
-    // beats the dp4a kernel (two-limb moduli dominate and the tiles are long)
-    const bool want_rmm = o.res_engine == 2 || (o.res_engine == 0 && kpad >= 256);
+    // automatic choice takes it where the dp4a kernel would need its 68-digit
+    // class or more (integers of more than 72 bytes): measured at 84 bytes,
+    // 0.99 ms against 1.59 ms at 1024^3; at 68 bytes dp4a wins, 0.62 vs 0.84
+    const bool want_rmm = o.res_engine == 2 || (o.res_engine == 0 && residue_class_w16(h.res_cls) > 36);
     if (want_rmm && kpad + 64 <= 512) h.res_mode = 2;
     h.res_kpad = kpad;
     h.res_npad = npad;

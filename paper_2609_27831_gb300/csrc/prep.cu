@@ -652,8 +652,8 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 //   warps 2-5   one per TMEM lane quadrant: integerize the tile's elements and
 //               write their bytes into A buffer t & 1 once the MMAs of tile
 //               t - 2 are done, so that they run ahead of the epilogue
-//   warps 6-21  four per lane quadrant (sub-groups s = 0..3): for every chunk,
-//               the 32-column groups g = s, s + 4, ...; a group is all
+//   warps 6-21  four per lane quadrant (sub-groups s = 0..3): the tile's
+//               32-column groups in turn (rotated per tile); a group is all
 //               one-limb, all two-limb pairs (L1 is even) or the one mixed
 //               group: reduce mod m_l (round-to-nearest quotient in fp32, the
 //               sign applied first), split two-limb residues, store the bf16
@@ -924,9 +924,9 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
-    int ck = 0;
+    int ck = 0, tcount = 0;
     bool ok = true;
-    for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+    for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
       const int side = tl.y;
@@ -948,7 +948,10 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         const uint32_t trow = tlane + 2 * acols + (uint32_t)(s * cw);
         const int j0 = c * cw;
         const int ncolp = min(cw, npad - j0);          // columns written by the MMAs
-        for (int g = 32 * sub; g < ncolp; g += 128) {
+        // the tile's 32-column groups go round the four sub-groups (rotated
+        // per tile), whatever the chunk width
+        const int gfirst = (sub - c * (cw >> 5) - tcount) & 3;
+        for (int g = 32 * gfirst; g < ncolp; g += 128) {
           uint32_t y[32];
           if (g + 32 <= ncolp) {
             tmem_ld32(trow + (uint32_t)g, y);
@@ -980,14 +983,16 @@ __global__ void __launch_bounds__(kRmThreads, 1)
             for (int i = 0; i < 16; ++i) {
               if (col0 + 2 * i < ncols) {
                 const float4 mc = s_mc[lb + i];
-                float x = cmod_f32(pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                // x + 0.0f: a -0 residue (all-zero bytes) becomes +0; then lo,
+                // hi and lo + hi are never -0
+                const float x = cmod_f32(pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z) + 0.0f;
                 // balanced base-128 split: x = lo + 128 hi, lo in (-64, 64]
                 float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
                 float lo = fmaf(-128.f, hi, x);
                 if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
-                dp[0] = (uint16_t)(__float_as_uint(lo + 0.0f) >> 16);
-                dp[pstride] = (uint16_t)(__float_as_uint(hi + 0.0f) >> 16);
-                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi + 0.0f) >> 16);
+                dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
+                dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
+                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
               }
               dp += 3 * pstride;
             }
@@ -1003,14 +1008,14 @@ __global__ void __launch_bounds__(kRmThreads, 1)
               } else if (colx < ncols && ((colx - L1) & 1) == 0) {
                 const int l = L1 + ((colx - L1) >> 1);
                 const float4 mc = s_mc[l];
-                float x = cmod_f32(pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z);
+                const float x = cmod_f32(pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z) + 0.0f;
                 float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
                 float lo = fmaf(-128.f, hi, x);
                 if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
                 uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (l - L1)) * pstride;
-                dp[0] = (uint16_t)(__float_as_uint(lo + 0.0f) >> 16);
-                dp[pstride] = (uint16_t)(__float_as_uint(hi + 0.0f) >> 16);
-                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi + 0.0f) >> 16);
+                dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
+                dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
+                dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
               }
             }
           }

@@ -157,9 +157,14 @@ def test_crt_engine_choice(ozk):
 
 def test_residue_engine_choice(ozk):
     """The automatic residue choice: the warp-specialised tensor-core kernel for
-    integers of more than 192 bytes, the CUDA cores below; engine 3 forces the
-    CUDA cores, engine 2 asks for the tensor cores up to 448 bytes."""
+    integers of more than 72 bytes (t + 1 bits), the CUDA cores below; engine 3
+    forces the CUDA cores, engine 2 asks for the tensor cores up to 448 bytes."""
     assert ozk.Plan((64, 64, 64, 2048)).info["res_mode"] == 2
-    assert ozk.Plan((64, 64, 64, 1024)).info["res_mode"] == 0
+    assert ozk.Plan((64, 64, 64, 1024)).info["res_mode"] == 2
+    t = ozk.Plan((64, 64, 64, 553)).info["t"]
+    assert -(-(t + 1) // 8) == 72 and ozk.Plan((64, 64, 64, 553)).info["res_mode"] == 0
+    t = ozk.Plan((64, 64, 64, 554)).info["t"]
+    assert -(-(t + 1) // 8) == 73 and ozk.Plan((64, 64, 64, 554)).info["res_mode"] == 2
+    assert ozk.Plan((64, 64, 64, 512)).info["res_mode"] == 0
     assert ozk.Plan((64, 64, 64, 2048), res_engine=3).info["res_mode"] == 0
     assert ozk.Plan((64, 64, 64, 256), res_engine=2).info["res_mode"] == 2
