@@ -101,8 +101,7 @@ typedef struct {
                      and the tables fit in shared memory (CUDA cores otherwise); 2: the column
                      sums of any length as an exact bf16 GEMM on the tensor cores, written as
                      group sums to the workspace and finished on the CUDA cores, where
-                     32 <= L <= 448 and M N >= 128 (CUDA cores otherwise); the reduced-product
-                     region then holds v_l = (c mod m_l) M_l^{-1} mod m_l, M_l = P / m_l;
+                     32 <= L <= 448 and M N >= 128 (CUDA cores otherwise);
                      3: the CRT on the CUDA cores only */
   int res_engine; /* 0: automatic (default): engine 2 for integers of more than 72 bytes
                      (p above about 550), CUDA cores otherwise; 1: residues as an exact bf16
@@ -180,9 +179,9 @@ OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digit
      off[1] column exponents f int32 [N]
      off[2] A planes  bf16 [G][M][Kp]   (Kp = K rounded up to 8; K-major)
      off[3] B planes  bf16 [G][N][Kp]   (transposed: column j of B is row j)
-     off[4] reduced products u  uint16 [L][MNp], MNp = M*N rounded up to a multiple of 8
-            (row-major (i, j) within each modulus row); with crt_engine 2 the
-            values v_l = u_l M_l^{-1} mod m_l instead
+     off[4] reduced products v  uint16 [L][MNp], MNp = M*N rounded up to a multiple of 8
+            (row-major (i, j) within each modulus row): v_l = u_l M_l^{-1} mod m_l,
+            u_l = c mod m_l the reduced product, M_l = P / m_l (the CRT's first step)
    and *kp = Kp.  Plane order: one-limb moduli in plane order, then for each
    two-limb modulus the planes r0, r1, r0 + r1 (balanced base-128 split). */
 OZ2_API int ozaki2_plan_layout(ozaki2_plan plan, int prob, size_t off[5], int64_t* kp);

@@ -28,12 +28,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t m, uint32_t mu) {
-  uint32_t q = __umulhi(x, mu);
-  uint32_t r = x - q * m;
-  return r >= m ? r - m : r;
-}
-
 // two small non-negative integers (<= 256) as a packed bf16 pair (low, high)
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
   return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
@@ -113,9 +107,7 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   for (int i = threadIdx.x; i < L * EPB; i += 256) {
     const int l = i / EPB, e = i - l * EPB;
     const int64_t idx = e0 + e;
-    const uint32_t uu = idx < MN ? (uint32_t)P.u[(int64_t)l * P.upitch + idx] : 0u;
-    const ModConst& mc = T.mods[l];
-    s_v[i] = (uint16_t)barrett32(uu * __ldg(cv.Minv + l), mc.m, mc.mu);
+    s_v[i] = idx < MN ? P.u[(int64_t)l * P.upitch + idx] : (uint16_t)0;   // v_l from the plane GEMM
   }
   __syncthreads();
 
@@ -507,8 +499,9 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
     s_tab[ND + i] = __ldg(cv.negH1 + i);
     s_tab[2 * ND + i] = __ldg(cv.P + i);
   }
-  // v_l = u_l M_l^{-1} mod m_l: 16-byte loads of 8 reduced products; a block
-  // covers 16 x 8 = 128 outputs of 8 moduli per pass, independent loads first
+  // v_l = (c mod m_l) M_l^{-1} mod m_l as the plane GEMM stored it: 16-byte
+  // loads of 8 values; a block covers 16 x 8 = 128 outputs of 8 moduli per
+  // pass, independent loads first
   if (!from_r) {
     const int lane8 = threadIdx.x & 15;                       // which 8 outputs
     const int lrow = threadIdx.x >> 4;                        // modulus within the pass
@@ -536,18 +529,8 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
       for (int j = 0; j < 4; ++j) {
         const int l = l0 + 8 * j + lrow;
         if (l >= L) continue;
-        const ModConst mc = T.mods[l];
-        const uint32_t inv = __ldg(cv.Minv + l);
-        const uint32_t in[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
-        uint32_t o[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t lo = barrett32((in[q] & 0xffffu) * inv, mc.m, mc.mu);
-          const uint32_t hi = barrett32((in[q] >> 16) * inv, mc.m, mc.mu);
-          o[q] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4*>(s_v + l * kEpb1 + 8 * lane8) = make_uint4(o[0], o[1], o[2], o[3]);
-        if (lane8 == 0) s_mu[l] = mc.mu;
+        *reinterpret_cast<uint4*>(s_v + l * kEpb1 + 8 * lane8) = w[j];
+        if (lane8 == 0) s_mu[l] = T.mods[l].mu;
       }
     }
   }
@@ -761,7 +744,7 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
       const CrtView cv = crt_view(T.crt_pool, P);
       for (int l = t; l < P.L; l += kCtThreads) {
         const ModConst& mc = T.mods[l];
-        s_pc[l] = make_uint4(mc.m, mc.mu, __ldg(cv.Minv + l), 0u);
+        s_pc[l] = make_uint4(mc.m, mc.mu, 0u, 0u);
       }
       for (int d = t; d < ND; d += kCtThreads) {
         s_tab[d] = d < P.DS ? __ldg(cv.negP + d) : 0u;
@@ -801,9 +784,8 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
       uint64_t sig = 0;
 #pragma unroll 4
       for (int l = l0; l < l1; ++l) {
-        const uint32_t uu = s_u[l * 128 + e];
+        const uint32_t v = s_u[l * 128 + e];          // v_l from the plane GEMM
         const uint4 pc = s_pc[l];
-        const uint32_t v = barrett32(uu * pc.z, pc.x, pc.y);
         sig += (uint64_t)v * pc.y;
         *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(e, 2 * l, 128)) = bf16_pair(v & 127u, v >> 7);
       }

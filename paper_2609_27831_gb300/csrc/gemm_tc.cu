@@ -272,11 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       uint16_t* urow = P.u + (int64_t)j.u.ell * P.upitch + (int64_t)row * PN;
       const int col_base = j.u.tn * kBN + half * 128;
       const bool vec_ok = (PN & 7) == 0;
-      // final coefficient; for the tensor-core CRT sums also times
-      // M_l^{-1} mod m_l, so that the stored value is v_l (Sec. 4.4)
+      // final coefficient, times M_l^{-1} mod m_l on the last job, so that
+      // the stored value is the CRT's v_l = (c mod m_l) M_l^{-1} mod m_l (Sec. 4.4)
       uint32_t fin = mc.kfin;
-      if (j.last && P.crt_mode == 2)
-        fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
+      if (j.last) fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
       if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status)) break;
       ++uses[s];
       tc_fence_after();
@@ -392,7 +391,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(DevTables T, const int4* __re
     }
     v %= m;
     if (v < 0) v += m;
-    if (P.crt_mode == 2) v = v * __ldg(crt_view(T.crt_pool, P).Minv + u.ell) % m;   // v_l for the CRT sums
+    v = v * __ldg(crt_view(T.crt_pool, P).Minv + u.ell) % m;   // v_l for the CRT
     P.u[(int64_t)u.ell * P.upitch + (int64_t)row * P.N + col] = (uint16_t)v;
   }
 }

@@ -2,8 +2,8 @@
 
 The oracle cannot compute these products whole, so each test runs the full
 product on the GPU and checks sampled entries stage by stage against the
-oracle (the reduced products of every modulus, the output limbs, exponent and
-sign bit for bit) and against the exact product rounded once (<= 1 ulp):
+oracle (the reduced products of every modulus, times M_l^{-1} mod m_l as the
+plane GEMM stores them, the output limbs, exponent and sign bit for bit) and against the exact product rounded once (<= 1 ulp):
   4096^3 at p = 2048 (exponents in [-64, 64]; the CRT as tensor-core sums),
   8192^3 at p = 53 (exponents in [-8, 8]), both with the benchmark's inputs,
   the 64-problem batch (M, N, K log-uniform in [128, 2048], p in {113, 256, 512}),
@@ -46,9 +46,8 @@ def _sampled(ozk, plan, ws, dC, M, N, K, p, pairs, A, B, off=None):
     for (i, j), r in zip(pairs, ref):
         got_u = (u16[torch.arange(L, device=u16.device) * upitch + i * N + j].cpu().numpy().astype(np.int64)
                  & 0xFFFF)
-        want = np.array(r["u"], dtype=np.int64)
-        if plan.info["crt_mode"] == 2:          # the tensor-core CRT sums store v_l
-            want = np.array([(x * pow((P // m) % m, -1, m)) % m for x, m in zip(r["u"], par.moduli)])
+        # the plane GEMM stores v_l = u_l M_l^{-1} mod m_l (the CRT's first step)
+        want = np.array([(x * pow((P // m) % m, -1, m)) % m for x, m in zip(r["u"], par.moduli)])
         assert np.array_equal(got_u, want), (i, j)
         limbs = [int(x) & ((1 << 64) - 1) for x in dC.limbs[:, i, j].cpu().tolist()]
         got = (limbs, int(dC.exp[i, j].item()), int(dC.sign[i, j].item()))

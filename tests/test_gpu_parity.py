@@ -29,6 +29,19 @@ def ozk():
     return pkg
 
 
+def crt_v(u, mods):
+    """v_l = u_l M_l^{-1} mod m_l (M_l = P / m_l), the value the plane GEMM
+    stores for the CRT (Sec. 4.4), from the oracle's reduced products u_l
+    (leading axis l)."""
+    P = 1
+    for m in mods:
+        P *= m
+    inv = np.array([pow((P // m) % m, -1, m) for m in mods], dtype=np.int64)
+    u = np.asarray(u, dtype=np.int64)
+    shape = (-1,) + (1,) * (u.ndim - 1)
+    return (u * inv.reshape(shape)) % np.array(mods, dtype=np.int64).reshape(shape)
+
+
 def run_gpu(ozk, A, B, p, debug=True, **kw):
     """Execute one product; return output and every intermediate."""
     M, K = A["exp"].shape
@@ -83,17 +96,8 @@ def assert_full_parity(ozk, A, B, p, truth=True, **kw):
     assert e_ok.all()
     assert np.array_equal(bf16_to_int(got["pa"]), ref["planes_a"])
     assert np.array_equal(bf16_to_int(got["pb"]), ref["planes_b"])
-    if got["plan"].info["crt_mode"] == 2:
-        # the CRT-sum engine stores v_l = u_l M_l^{-1} mod m_l, M_l = P / m_l
-        mods = ref["par"].moduli
-        P = 1
-        for m in mods:
-            P *= m
-        inv = np.array([pow((P // m) % m, -1, m) for m in mods], dtype=np.int64)
-        want = (ref["u"] * inv[:, None, None]) % np.array(mods, dtype=np.int64)[:, None, None]
-        assert np.array_equal(got["u"].astype(np.int64), want)
-    else:
-        assert np.array_equal(got["u"].astype(np.int64), ref["u"])
+    # the plane GEMM stores v_l = u_l M_l^{-1} mod m_l (the CRT's first step)
+    assert np.array_equal(got["u"].astype(np.int64), crt_v(ref["u"], ref["par"].moduli))
     assert all(got["chat"][i, j] == ref["chat"][i, j] for i in range(M) for j in range(N))
     for key in ("limbs", "exp", "sign"):
         assert np.array_equal(got["C"][key], ref["C"][key]), key
@@ -183,7 +187,8 @@ def test_fp32_accumulation_exactness_torture(ozk, K):
     ai, e = o.integer_line(A, 0, 0, par.t)
     bj, f = o.integer_line(B, 0, 1, par.t)
     ref = o.entry(ai, e, bj, f, par)
-    assert np.all(got["u"].astype(np.int64) == np.array(ref["u"])[:, None, None])
+    v = crt_v(ref["u"], par.moduli)
+    assert np.all(got["u"].astype(np.int64) == v[:, None, None])
     assert all(got["chat"][i, j] == ref["chat"] for i in (0, 63) for j in (0, 63))
     assert o.matrix_entry(got["C"], 5, 7) == (ref["limbs"], ref["exp"], ref["sign"])
 
@@ -351,9 +356,10 @@ def test_gemm_1024_p256_sampled(ozk):
     pairs = [(0, 0), (1023, 1023), (0, 1023), (1023, 0), (511, 257)]
     pairs += [(rnd.randrange(1024), rnd.randrange(1024)) for _ in range(11)]
     ref = o.ozaki2_entries(A, B, 256, pairs)
+    mods = o.Params(1024, 256).moduli
     worst = Fraction(0)
     for (i, j), r in zip(pairs, ref):
-        assert [int(x) for x in got["u"][:, i, j]] == r["u"]
+        assert [int(x) for x in got["u"][:, i, j]] == crt_v(r["u"], mods).tolist()
         assert got["chat"][i, j] == r["chat"]
         assert o.matrix_entry(got["C"], i, j) == (r["limbs"], r["exp"], r["sign"])
         t = o.to_fraction(*o.truth_entry(A, B, i, j, 256))
