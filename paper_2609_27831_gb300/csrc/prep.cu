@@ -193,16 +193,22 @@ __device__ __forceinline__ float centered_f32(uint32_t a, bool neg, float mf, fl
 // Residues of EPT elements over all L moduli from their first NW words, and
 // the plane writes.  The table row of modulus l holds the packed low bytes of
 // 2^(8 b) mod m_l in words [0, W32) and the high bytes in words [W32, 2 W32).
-// s_mc[l] = {m, floor(2^32 / m), 1/m (fp32 bits), m/2 (fp32 bits)}.  One-limb
+// s_mc[l] = {m, floor(2^32 / m), 1/m (fp32 bits), m/2 (fp32 bits)}.  Byte
 // sums stay below 4 NW 255^2 < 2^23 for NW <= 32, so their reduction is done
-// in fp32 there (Barrett beyond); two-limb moduli use Barrett reduction of
-// lo + 256 hi < 2^32.
+// in fp32 there (Barrett beyond, with lo + 256 hi < 2^32 for two-limb moduli).
 template <int NW, int W32, int EPT>
 __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], const bool (&ng)[EPT],
                                                const uint32_t* s_t8, const uint4* s_mc, int L, int L1,
                                                uint16_t* dst, int64_t plane_stride, int nk) {
   static_assert(EPT == 2 || EPT == 4, "two or four elements per thread");
   constexpr int RS = 2 * W32;
+  // per element: s a = fma(s, 2^23 + a, -s 2^23) exactly, +0 for a = 0
+  float sg[EPT], sb[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    sg[e] = ng[e] ? -1.f : 1.f;
+    sb[e] = ng[e] ? 8388608.f : -8388608.f;
+  }
   // one plane of the EPT elements: one vector store when all are in range
   auto put = [&](const uint32_t (&bits)[EPT]) {           // bf16 bits in the low halves
     if (nk == EPT) {
@@ -243,8 +249,22 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
       uint32_t bits[EPT];
       if constexpr (NW <= 32) {                             // a < 4 NW 255^2 < 2^23: fp32 reduction
         const float mf = (float)mcv.x, rcp = __uint_as_float(mcv.z), hm = __uint_as_float(mcv.w);
+        if (mcv.x & 1u) {
+          // odd m: a <= 4 NW 255 250 < 0.973 2^23, so |a rcp - a/m| <=
+          // a 2^-24 (1 + 2^-29) / m < 1/(2m), while a/m is at least 1/(2m)
+          // from every half-integer: the rounded quotient is exact and
+          // r = s a - q m is the centered residue, with no correction step
+          // (an exact zero is +0: x - x and +0 - 0 m round to +0)
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) bits[e] = __float_as_uint(centered_f32(a[e], ng[e], mf, rcp, hm)) >> 16;
+          for (int e = 0; e < EPT; ++e) {
+            const float f = fmaf(sg[e], __uint_as_float(a[e] | 0x4B000000u), sb[e]);
+            const float q = fmaf(f, rcp, 12582912.0f) - 12582912.0f;
+            bits[e] = __float_as_uint(fmaf(-q, mf, f)) >> 16;
+          }
+        } else {                                            // m = 128: ties need the correction
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) bits[e] = __float_as_uint(centered_f32(a[e], ng[e], mf, rcp, hm)) >> 16;
+        }
       } else {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) bits[e] = bf16_bits(centered(barrett32(a[e], mcv.x, mcv.y), mcv.x, ng[e]));
@@ -279,15 +299,40 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
       // balanced base-128 split: r = r0 + 128 r1 with r0 = cen(r mod 128);
       // planes L1 + 3 (l - L1) + {0, 1, 2} = r0, r1, r0 + r1
       uint32_t b0[EPT], b1[EPT], b2[EPT];
+      if constexpr (NW <= 32) {
+        // fp32, exact (m odd): lo <= 4 NW 255^2 and hi < lo are below
+        // 2^23 / (1 + 2^-29), so their rounded quotients are exact and give
+        // centered residues; y = r_lo + 256 r_hi has |y| < 2^21, reduced
+        // exactly the same way; then the split with a round-to-nearest
+        // quotient by 128 (a tie leaves r0 = -64, moved to +64)
+        const float mf = (float)mcv.x, rcp = __uint_as_float(mcv.z);
 #pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int x = centered(barrett32(lo[e] + (hi[e] << 8), mcv.x, mcv.y), mcv.x, ng[e]);
-        const int y = x & 127;
-        const int r0 = y > 64 ? y - 128 : y;
-        const int r1 = (x - r0) >> 7;
-        b0[e] = bf16_bits(r0);
-        b1[e] = bf16_bits(r1);
-        b2[e] = bf16_bits(r0 + r1);
+        for (int e = 0; e < EPT; ++e) {
+          const float fl = fmaf(sg[e], __uint_as_float(lo[e] | 0x4B000000u), sb[e]);
+          const float fh = fmaf(sg[e], __uint_as_float(hi[e] | 0x4B000000u), sb[e]);
+          const float ql = fmaf(fl, rcp, 12582912.0f) - 12582912.0f;
+          const float qh = fmaf(fh, rcp, 12582912.0f) - 12582912.0f;
+          const float y = fmaf(256.f, fmaf(-qh, mf, fh), fmaf(-ql, mf, fl));
+          const float q = fmaf(y, rcp, 12582912.0f) - 12582912.0f;
+          const float x = fmaf(-q, mf, y);
+          float r1 = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
+          float r0 = fmaf(-128.f, r1, x);
+          if (r0 <= -64.f) { r0 += 128.f; r1 -= 1.f; }
+          b0[e] = __float_as_uint(r0) >> 16;
+          b1[e] = __float_as_uint(r1) >> 16;
+          b2[e] = __float_as_uint(r0 + r1) >> 16;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const int x = centered(barrett32(lo[e] + (hi[e] << 8), mcv.x, mcv.y), mcv.x, ng[e]);
+          const int y = x & 127;
+          const int r0 = y > 64 ? y - 128 : y;
+          const int r1 = (x - r0) >> 7;
+          b0[e] = bf16_bits(r0);
+          b1[e] = bf16_bits(r1);
+          b2[e] = bf16_bits(r0 + r1);
+        }
       }
       put(b0);
       put(b1);

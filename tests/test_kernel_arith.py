@@ -1,0 +1,59 @@
+"""Arithmetic facts the CUDA kernels rely on, checked exhaustively on the CPU.
+
+The CUDA-core residue kernel reduces the byte-product sum a (one-limb
+modulus m, a <= 4 * 32 words * 255 * 250 < 2^23) in fp32 with
+q = round(a * rcp), rcp = 1/m rounded to fp32 as the library's host code
+computes it.  For odd m the kernel takes r = a - q m as the centered residue
+without a correction step; that holds exactly when q = round(a / m) for every
+such a, which this test checks for all odd one-limb moduli of the method
+(Sec. 4.3's moduli <= 255) and every reachable a.
+"""
+import numpy as np
+
+from oracle import ozaki2_oracle as o
+
+
+def test_fp32_rounded_quotient_is_exact_for_odd_one_limb_moduli():
+    mods = [m for m in o.Params(1024, 2048).moduli if m <= 255]
+    assert len(mods) == 54 and sum(m % 2 == 0 for m in mods) == 1      # 128 is the even one
+    amax = 4 * 32 * 255 * 250
+    assert amax < 2 ** 23
+    a = np.arange(amax + 1, dtype=np.int64)
+    af = a.astype(np.float64)
+    for m in mods:
+        if m % 2 == 0:
+            continue
+        rcp = np.float64(np.float32(1.0 / m))      # as the host computes it
+        prod = af * rcp                            # exact in binary64 (23 x 24 bits)
+        assert not np.any(prod - np.floor(prod) == 0.5), m
+        q = np.rint(prod).astype(np.int64)
+        q_true = (2 * a + m) // (2 * m)            # round(a / m); no ties for odd m
+        assert np.array_equal(q, q_true), m
+        r = a - q * m
+        assert r.min() >= -(m // 2) and r.max() <= m // 2, m
+
+
+def test_fp32_rounded_quotient_is_exact_for_two_limb_moduli():
+    """Two-limb moduli (odd primes in (255, 16191]): the kernel reduces the
+    low-byte sum (<= 4 * 32 * 255^2) and the high-byte sum separately with the
+    rounded quotient, then y = r_lo + 256 r_hi (|y| < 2^21) the same way.
+    Exhaustive over the low-byte range for the smallest, the largest and a
+    spread of the moduli in between."""
+    mods = [m for m in o.Params(1024, 2048).moduli if m > 255]
+    assert all(m % 2 == 1 for m in mods)
+    pick = sorted(set([mods[0], mods[-1]] + mods[:: max(1, len(mods) // 10)]))
+    amax = 4 * 32 * 255 * 255
+    assert amax * (1 + 2.0 ** -29) < 2 ** 23
+    a = np.arange(amax + 1, dtype=np.int64)
+    af = a.astype(np.float64)
+    for m in pick:
+        rcp = np.float64(np.float32(1.0 / m))
+        q = np.rint(af * rcp).astype(np.int64)
+        assert np.array_equal(q, (2 * a + m) // (2 * m)), m
+    # y = r_lo + 256 r_hi over its whole range, for the same moduli
+    for m in pick:
+        h = (m - 1) // 2
+        y = np.arange(-257 * h, 257 * h + 1, dtype=np.int64)
+        rcp = np.float64(np.float32(1.0 / m))
+        q = np.rint(y.astype(np.float64) * rcp).astype(np.int64)
+        assert np.array_equal(q, np.floor_divide(2 * y + m, 2 * m)), m
