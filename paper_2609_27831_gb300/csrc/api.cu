@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -160,7 +161,7 @@ struct ProbHost {
   bool skip_a, skip_b;         // planes of that side are written by the caller
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
                                // 2: tensor-core sums to R digits, then the finish
-  int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot;
+  int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot, crt_nvbuf;
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [4][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_tcols;           // res_mode 2: chunk width, chunks, TMEM columns
@@ -208,9 +209,9 @@ struct DevState {
   std::vector<int> crt_off;    // per problem, uint32 offset in the pool
   ListRef tct[9];               // tensor-core CRT tile lists (smem = kpad_max, lmax = L max)
   int tct_npad[9] = {0};
-  ListRef cmt;                  // tensor-core CRT sum tiles (smem = largest chunk width)
+  std::vector<ListRef> cmt;     // tensor-core CRT sum tiles, one list per TMEM layout (smem = chunk width)
   ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = groups max)
-  ListRef rmt;                  // warp-specialised tensor-core residue tiles (smem = cw max, lmax = TMEM columns)
+  std::vector<ListRef> rmt;     // warp-specialised tensor-core residue tiles, one list per TMEM layout (smem = cw)
   ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
   int rtt_npad = 0;
   std::vector<void*> res_tab;   // per problem: device address of its residue table
@@ -360,6 +361,9 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     h.crt_nslot = 2;
     h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad, &h.crt_nslot) : 0;
     h.crt_nchunk = mm_ok ? (npad + h.crt_cw - 1) / h.crt_cw : 0;
+    // a second V buffer where it fits beside the accumulator slots: the
+    // next tile's V is built while this tile's chunks are read out
+    h.crt_nvbuf = (mm_ok && kpad + h.crt_nslot * h.crt_cw <= 512) ? 2 : 1;
     h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
     const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
     if (h.crt_mode != 0 && c.tc_table.empty()) {
@@ -536,10 +540,12 @@ struct TableImage {
   size_t o_tct[9] = {0};
   int n_tct[9] = {0}, tct_kpad[9] = {0}, tct_npad[9] = {0}, tct_l[9] = {0};
   std::vector<size_t> o_tctab;
-  size_t o_cmt = 0, o_finl = 0;     // tensor-core CRT sum tiles; finish blocks of long accumulators
-  int n_cmt = 0, cmt_cw = 0, n_finl = 0, finl_dmax = 0, finl_gmax = 0;
-  size_t o_rmt = 0;                 // warp-specialised tensor-core residue tile list
-  int n_rmt = 0, rmt_cw = 0, rmt_tcols = 0;
+  // tensor-core CRT sum tiles and warp-specialised tensor-core residue
+  // tiles: one launch per TMEM layout, {first tile, tiles, chunk width}
+  size_t o_cmt = 0, o_finl = 0;
+  std::vector<std::array<int, 3>> cmt_seg, rmt_seg;
+  int n_finl = 0, finl_dmax = 0, finl_gmax = 0;
+  size_t o_rmt = 0;
   size_t o_rtt = 0;                 // tensor-core residue tile list
   int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
   std::vector<size_t> o_rtab;
@@ -663,7 +669,10 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
   std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
-  std::vector<int4> rtt, cmt, finl, rmt;
+  std::vector<int4> rtt, finl;
+  // tiles of the warp-specialised kernels grouped by TMEM layout (tiles of
+  // one launch share the column map of their buffers and slots)
+  std::map<std::array<int, 3>, std::vector<int4>> cmt_by, rmt_by;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
     if (!h.skip_a) {
@@ -680,10 +689,9 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     for (int side = 0; h.res_mode == 2 && side < 2; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
+      std::vector<int4>& rl = rmt_by[{h.res_kpad, h.res_cw, 0}];
       for (int64_t r = 0; r < R; r += 4)
-        for (int64_t k = 0; k < h.K; k += 32) rmt.push_back(make_int4(pi, side, (int)r, (int)k));
-      ti.rmt_cw = std::max(ti.rmt_cw, h.res_cw);
-      ti.rmt_tcols = std::max(ti.rmt_tcols, h.res_tcols);
+        for (int64_t k = 0; k < h.K; k += 32) rl.push_back(make_int4(pi, side, (int)r, (int)k));
     }
     for (int side = 0; h.res_mode == 1 && side < 2; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
@@ -714,8 +722,8 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       // k_crt1 (its block list), longer accumulators in k_crt_fin_long
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
-      for (int64_t tt = 0; tt < nt; ++tt) cmt.push_back(make_int4(pi, (int)tt, 0, 0));
-      ti.cmt_cw = std::max(ti.cmt_cw, h.crt_cw);
+      std::vector<int4>& cl = cmt_by[{h.crt_kpad, h.crt_cw, h.crt_nslot}];
+      for (int64_t tt = 0; tt < nt; ++tt) cl.push_back(make_int4(pi, (int)tt, 0, 0));
       if (h.crt_cls <= 8) {
         const int epb = crt_class_elems_per_block(h.crt_cls);
         for (int64_t bb = 0; bb < (h.M * h.N + epb - 1) / epb; ++bb)
@@ -769,28 +777,33 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       return OZ2_EINTERNAL;
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
-    if (h.crt_mode == 2 && (ti.cmt_cw < h.crt_cw || h.crt_cw % 32 != 0 ||
-                            h.crt_kpad / 2 + h.crt_nslot * h.crt_cw > 512 ||
+    if (h.crt_mode == 2 && (h.crt_cw % 32 != 0 || h.crt_nvbuf * (h.crt_kpad / 2) + h.crt_nslot * h.crt_cw > 512 ||
                             (h.crt_cls <= 8 ? ti.crt_l[h.crt_cls] < h.L
                                             : (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
       return OZ2_EINTERNAL;
   }
-  if (!cmt.empty() && crt_mm_smem_bytes(ti.cmt_cw, pl->lmax, nullptr) < 0) return OZ2_EINTERNAL;
+  std::vector<int4> cmt, rmt;
+  for (const auto& kv : cmt_by) {
+    if (crt_mm_smem_bytes(kv.first[1], pl->lmax, nullptr) < 0) return OZ2_EINTERNAL;
+    ti.cmt_seg.push_back({(int)cmt.size(), (int)kv.second.size(), kv.first[1]});
+    cmt.insert(cmt.end(), kv.second.begin(), kv.second.end());
+  }
+  for (const auto& kv : rmt_by) {
+    if (residue_mm_smem_bytes(kv.first[1], pl->lmax, 512, nullptr) < 0) return OZ2_EINTERNAL;
+    ti.rmt_seg.push_back({(int)rmt.size(), (int)kv.second.size(), kv.first[1]});
+    rmt.insert(rmt.end(), kv.second.begin(), kv.second.end());
+  }
   if (!finl.empty() && 3 * ti.finl_dmax * 4 + (ti.finl_dmax + 2 * ti.finl_gmax) * 128 * 4 > 200 * 1024)
     return OZ2_EINTERNAL;
   ti.o_cmt = ti.b.add(cmt.data(), cmt.size() * 16);
-  ti.n_cmt = (int)cmt.size();
   ti.o_finl = ti.b.add(finl.data(), finl.size() * 16);
   ti.n_finl = (int)finl.size();
   ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
   ti.n_rtt = (int)rtt.size();
   for (const ProbHost& h : pl->probs)
-    if (h.res_mode == 2 && (ti.rmt_cw < h.res_cw || ti.rmt_tcols < h.res_tcols || h.res_cw % 32 != 0 ||
-                            h.res_kpad + 2 * h.res_cw > h.res_tcols))
+    if (h.res_mode == 2 && (h.res_cw % 32 != 0 || h.res_kpad + 2 * h.res_cw > h.res_tcols))
       return OZ2_EINTERNAL;
-  if (!rmt.empty() && residue_mm_smem_bytes(ti.rmt_cw, pl->lmax, ti.rmt_tcols, nullptr) < 0) return OZ2_EINTERNAL;
   ti.o_rmt = ti.b.add(rmt.data(), rmt.size() * 16);
-  ti.n_rmt = (int)rmt.size();
   ti.o_rtab.assign(pl->rtabs.size(), 0);
   for (size_t i = 0; i < pl->rtabs.size(); ++i)
     ti.o_rtab[i] = ti.b.add(pl->rtabs[i].bits.data(), pl->rtabs[i].bits.size() * 2, 1024);
@@ -835,10 +848,14 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     d.tct[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_tct[i]), ti.n_tct[i], ti.tct_kpad[i], ti.tct_l[i]};
     d.tct_npad[i] = ti.tct_npad[i];
   }
-  d.cmt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt), ti.n_cmt, ti.cmt_cw, 0};
+  d.cmt.clear();
+  for (const auto& sg : ti.cmt_seg)
+    d.cmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt) + 4 * sg[0], sg[1], sg[2], 0});
   d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
   d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
-  d.rmt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rmt), ti.n_rmt, ti.rmt_cw, ti.rmt_tcols};
+  d.rmt.clear();
+  for (const auto& sg : ti.rmt_seg)
+    d.rmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rmt) + 4 * sg[0], sg[1], sg[2], 512});
   d.rtt_npad = ti.rtt_npad;
   d.res_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
@@ -973,6 +990,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_sig = h.crt_mode == 2 ? reinterpret_cast<uint64_t*>(ws + h.off_sig) : nullptr;
     P.crt_ngrp = h.crt_ngrp;
     P.crt_nslot = h.crt_nslot;
+    P.crt_nvbuf = h.crt_nvbuf;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
     if (rc) return rc;
     rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);
@@ -1038,7 +1056,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     if (d.res[c].n) OZ2_CU(launch_residues(tab, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
   if (d.rtt.n)
     OZ2_CU(launch_residues_tc(tab, d.rtt.ptr, d.rtt.n, d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
-  if (d.rmt.n) OZ2_CU(launch_residues_mm(tab, d.rmt.ptr, d.rmt.n, d.rmt.smem, d.rmt.lmax, d.sms, s));
+  for (const ListRef& r : d.rmt) OZ2_CU(launch_residues_mm(tab, r.ptr, r.n, r.smem, r.lmax, d.sms, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
   if (pl->opts.engine == OZ2_ENGINE_SIMT) {
     DevTables t2 = tab;
@@ -1054,8 +1072,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     }
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
-  if (d.cmt.n)
-    OZ2_CU(launch_crt_mm(tab, d.cmt.ptr, d.cmt.n, d.cmt.smem, d.sms, s));
+  for (const ListRef& r : d.cmt) OZ2_CU(launch_crt_mm(tab, r.ptr, r.n, r.smem, d.sms, s));
   if (d.finl.n) OZ2_CU(launch_crt_finish_long(tab, d.finl.ptr, d.finl.n, d.finl.smem, d.finl.lmax, s));
   for (int c = 0; c < kCrtClassCount; ++c)
     if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
@@ -1262,11 +1279,11 @@ int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
   c += (d.scan_rows.n || d.scan_cols.n) ? 1 : 0;
   for (int i = 0; i < 6; ++i) c += d.res[i].n ? 1 : 0;
   c += d.rtt.n ? 1 : 0;
-  c += d.rmt.n ? 1 : 0;
+  c += (int)d.rmt.size();
   if (pl->opts.engine == OZ2_ENGINE_SIMT) c += 1;
   else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += 1;
   else c += (int)d.plain.size();
-  c += d.cmt.n ? 1 : 0;
+  c += (int)d.cmt.size();
   c += d.finl.n ? 1 : 0;
   for (int i = 0; i < kCrtClassCount; ++i) c += d.crt[i].n ? 1 : 0;
   for (int i = 0; i < 9; ++i) c += d.tct[i].n ? 1 : 0;

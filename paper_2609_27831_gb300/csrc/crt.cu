@@ -981,8 +981,8 @@ struct CmLayout {
     mu_off = u_off + kCmUSlots * kCmUBytes;                 // floor(2^32 / m_l) [lmax]
     bar_off = mu_off + (((uint32_t)lmax * 4 + 15u) & ~15u);
     // barriers: full, empty [kCmMaxStages], u_full, u_free [kCmUSlots], acc_full, acc_free [2],
-    // v_full, v_free, drain; then the abort flag and the TMEM slot
-    total = 1024 + bar_off + (2 * kCmMaxStages + 2 * kCmUSlots + 7) * 8 + 16;
+    // v_full, v_free [2], drain; then the abort flag and the TMEM slot
+    total = 1024 + bar_off + (2 * kCmMaxStages + 2 * kCmUSlots + 9) * 8 + 16;
     if (total < (uint32_t)kCmMinSmem) total = kCmMinSmem;
   }
 };
@@ -1024,11 +1024,11 @@ __global__ void __launch_bounds__(kCmThreads, 1)
   uint64_t* u_free = u_full + kCmUSlots;                      // [kCmUSlots] (128 arrivals: one half)
   uint64_t* acc_full = u_free + kCmUSlots;                    // [2] chunk in slot done
   uint64_t* acc_free = acc_full + 2;                          // [2] slot read out (256 arrivals)
-  uint64_t* v_full = acc_free + 2;                            // V columns written (256 arrivals)
-  uint64_t* v_free = v_full + 1;                              // MMAs of the tile done (V may be rewritten)
-  uint64_t* drain = v_full + 2;                               // abort drain of the MMA pipe
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(v_full + 3);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(v_full + 3) + 1;
+  uint64_t* v_full = acc_free + 2;                            // [2] V buffer written (every worker)
+  uint64_t* v_free = v_full + 2;                              // [2] MMAs reading the buffer done
+  uint64_t* drain = v_full + 4;                               // abort drain of the MMA pipe
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(v_full + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(v_full + 5) + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1041,8 +1041,10 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       mbar_init(u_free + i, 128);
     }
     for (int i = 0; i < 2; ++i) mbar_init(acc_full + i, 1);
-    mbar_init(v_full, kCmWorkers);
-    mbar_init(v_free, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(v_full + i, kCmWorkers);
+      mbar_init(v_free + i, 1);
+    }
     for (int i = 0; i < 2; ++i) mbar_init(acc_free + i, kCmWorkers);   // every worker reads every chunk
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -1094,16 +1096,19 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     if (lane == 0) {
       int st = 0;
       uint32_t ph = 0;
-      int next = 0, uses[2] = {0, 0}, tcount = 0;
+      int next = 0, uses[2] = {0, 0}, vnext = 0, vuses[2] = {0, 0};
       bool ok = true, any = false;
       for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
-        const int nslot = P.crt_nslot;
+        const int nslot = P.crt_nslot, nvbuf = P.crt_nvbuf;
         const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
-        if (!mbar_wait(v_full, (uint32_t)(tcount & 1), abort_flag, T.status)) { ok = false; break; }
+        const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
+        vnext = nvbuf == 2 ? vnext ^ 1 : 0;
+        if (!mbar_wait(v_full + vb, (uint32_t)(vuse & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
+        const uint32_t vbase = tmem + (uint32_t)vb * vcols;
         for (int c = 0; ok && c < nchunk; ++c) {
           const int s = nslot == 2 ? next : 0, use = uses[s]++;
           next = nslot == 2 ? next ^ 1 : 0;
@@ -1114,14 +1119,14 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           tc_fence_after();
           const int ncol = min(cw, npad - c * cw);             // a multiple of 16
           const uint32_t idesc = idesc_bf16(128, ncol);
-          const uint32_t d = tmem + vcols + (uint32_t)(s * cw);
+          const uint32_t d = tmem + (uint32_t)nvbuf * vcols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
             tc_fence_after();
             const uint64_t db = desc_sw128(sRing + st * stage_bytes);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              umma_bf16_ta(d, tmem + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
+              umma_bf16_ta(d, vbase + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
             umma_commit(empty + st);
             any = true;
             if (++st == stages) { st = 0; ph ^= 1u; }
@@ -1129,8 +1134,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           if (ok) umma_commit(acc_full + s);
         }
         if (!ok) break;
-        umma_commit(v_free);
-        ++tcount;
+        umma_commit(v_free + vb);
       }
       if (!ok && any) {
         // drain issued MMAs before TMEM is released
@@ -1174,33 +1178,36 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
     const uint16_t* s_u = reinterpret_cast<const uint16_t*>(sm + lay.u_off);
-    int next = 0, uses[2] = {0, 0}, uc = 0, tcount = 0;
+    int next = 0, uses[2] = {0, 0}, uc = 0, vnext = 0, vuses[2] = {0, 0}, ecount = 0;
     bool ok = true;
-    for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
+    // V of tile i into its buffer: the group's v copies (c = h mod 4) as bf16
+    // 7-bit halves, and the group's part of the quotient sum
+    auto build = [&](int i) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
       // the problem's fields in registers before the waits (their memory
       // clobbers would reload them from global memory after every barrier)
-      const int L = P.L, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad, nslot = P.crt_nslot;
+      const int L = P.L, nvbuf = P.crt_nvbuf;
       const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
       const int64_t idx = (int64_t)tl.y * 128 + row;
       const bool valid = idx < (int64_t)P.M * P.N;
       const int64_t up = P.upitch;
-      uint32_t* const qbase = P.crt_q;
       uint64_t* const sigbase = P.crt_sig;
-      // V may be rewritten once every MMA of the previous tile is done (a
-      // half may have had no chunk of that tile to wait for)
-      if (tcount > 0 && ok) ok = mbar_wait(v_free, (uint32_t)((tcount - 1) & 1), abort_flag, T.status);
+      const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
+      vnext = nvbuf == 2 ? vnext ^ 1 : 0;
+      // the buffer may be rewritten once every MMA of its previous tile is done
+      if (vuse > 0 && ok) ok = mbar_wait(v_free + vb, (uint32_t)((vuse - 1) & 1), abort_flag, T.status);
       ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
+      if (!ok) return;
       tc_fence_after();
+      const uint32_t vrow = tlane + (uint32_t)vb * vcols;
       uint64_t sig = 0;
       for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
         if ((uc & 3) != half) continue;             // another group's copy
         const int s = uc % kCmUSlots, use = uc / kCmUSlots;
         if (ok) ok = mbar_wait(u_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
+        if (!ok) return;
         const uint16_t* su = s_u + s * (kCmUMods * 128);
         uint32_t pr[kCmUMods];
 #pragma unroll
@@ -1211,24 +1218,35 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           pr[q] = bf16_small(v & 127u) | (bf16_small(v >> 7) << 16);
         }
         mbar_arrive(u_free + s);
-        tmem_st32(tlane + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
+        tmem_st32(vrow + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
       }
-      if (!ok) break;
       if (valid) sigbase[half * up + idx] = sig;
       tmem_wait_st();
       tc_fence_before();
-      mbar_arrive(v_full);
-      // chunk epilogues: group h takes the 32-column groups g = h, h + 4, ...
+      mbar_arrive(v_full + vb);
+    };
+    // chunk epilogues of tile i: the tile's 32-column groups in turn over the
+    // four groups (rotated per tile)
+    auto epilogue = [&](int i) {
+      const int4 tl = tiles[i];
+      const ProbDev& P = T.probs[tl.x];
+      const int cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad, nslot = P.crt_nslot;
+      const uint32_t acc0 = (uint32_t)P.crt_nvbuf * ((uint32_t)P.crt_kpad / 2);
+      const int64_t idx = (int64_t)tl.y * 128 + row;
+      const bool valid = idx < (int64_t)P.M * P.N;
+      const int64_t up = P.upitch;
+      uint32_t* const qbase = P.crt_q;
       for (int c = 0; c < nchunk; ++c) {
         const int s = nslot == 2 ? next : 0, use = uses[s]++;
         next = nslot == 2 ? next ^ 1 : 0;
         if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
         ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
+        if (!ok) return;
         tc_fence_after();
-        const uint32_t trow = tlane + vcols + (uint32_t)(s * cw);
+        const uint32_t trow = tlane + acc0 + (uint32_t)(s * cw);
         const int ncol = min(cw, npad - c * cw);             // columns written by the MMAs
-        for (int g = 32 * half; g < cw; g += 128) {
+        const int gfirst = (half - c * (cw >> 5) - ecount) & 3;
+        for (int g = 32 * gfirst; g < cw; g += 128) {
           uint64_t acc[7] = {0, 0, 0, 0, 0, 0, 0};
           if (g + 32 <= ncol) {
             uint32_t y[32];
@@ -1256,7 +1274,20 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         tc_fence_before();
         mbar_arrive(acc_free + s);
       }
+      ++ecount;
+    };
+    // With two V buffers (uniform within a launch) the next tile's V is built
+    // before this tile's chunks are read, so its MMAs overlap the epilogue;
+    // that order waits for the MMAs of the tile before this one only.  With
+    // one buffer it would wait for this tile's MMAs, whose later chunks wait
+    // for this tile's epilogue: tiles then go strictly in turn.
+    const bool two = blockIdx.x < ntiles && T.probs[tiles[blockIdx.x].x].crt_nvbuf == 2;
+    if (two && blockIdx.x < ntiles) build(blockIdx.x);
+    for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+      if (!two) build(i);
+      else if (i + (int)gridDim.x < ntiles) build(i + gridDim.x);
       if (!ok) break;
+      epilogue(i);
     }
     if (!ok) *abort_flag = 1;
   }

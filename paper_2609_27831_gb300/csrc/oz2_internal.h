@@ -74,7 +74,7 @@ struct ProbDev {
   int32_t crt_kpad;      // tensor-core CRT: K = 2L padded to a multiple of 64
   int32_t crt_npad;      // tensor-core CRT: 7-bit pieces of S padded to a multiple of 16
   int32_t crt_np;        // tensor-core CRT: 7-bit pieces of S (columns of Y)
-  int32_t pad4;
+  int32_t crt_nvbuf;     // crt_mode 2: V buffers in TMEM (2 where kpad + nslot cw <= 512)
   int64_t upitch;        // row pitch of u [L][upitch]: M*N rounded up to a multiple of 8
   int32_t res_mode;      // 0: residues on the CUDA cores; 1: byte GEMM on the tensor cores;
                          // 2: the byte GEMM, warp-specialised (bytes in TMEM, table streamed)
