@@ -718,22 +718,15 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.tct_npad[h.crt_cls] = std::max(ti.tct_npad[h.crt_cls], h.crt_npad);
       ti.tct_l[h.crt_cls] = std::max(ti.tct_l[h.crt_cls], h.L);
     } else if (h.crt_mode == 2) {
-      // sums on the tensor cores, then the finish: one-lane classes in
-      // k_crt1 (its block list), longer accumulators in k_crt_fin_long
+      // sums on the tensor cores, then the finish from the group sums
+      // (k_crt_fin_long: every word copied in at once, then the digits in order)
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
       std::vector<int4>& cl = cmt_by[{h.crt_kpad, h.crt_cw, h.crt_nslot}];
       for (int64_t tt = 0; tt < nt; ++tt) cl.push_back(make_int4(pi, (int)tt, 0, 0));
-      if (h.crt_cls <= 8) {
-        const int epb = crt_class_elems_per_block(h.crt_cls);
-        for (int64_t bb = 0; bb < (h.M * h.N + epb - 1) / epb; ++bb)
-          crt[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
-        ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
-      } else {
-        for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
-        ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
-        ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
-      }
+      for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
+      ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
+      ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
     } else {
       const int epb = crt_class_elems_per_block(h.crt_cls);
       const int64_t nb = (h.M * h.N + epb - 1) / epb;
@@ -778,8 +771,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
     if (h.crt_mode == 2 && (h.crt_cw % 32 != 0 || h.crt_nvbuf * (h.crt_kpad / 2) + h.crt_nslot * h.crt_cw > 512 ||
-                            (h.crt_cls <= 8 ? ti.crt_l[h.crt_cls] < h.L
-                                            : (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
+                            ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))
       return OZ2_EINTERNAL;
   }
   std::vector<int4> cmt, rmt;

@@ -274,11 +274,18 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
   }
 }
 
+// e_i + f_j of output idx (row i, column j), loaded where a kernel starts so
+// that the rounding does not wait for it
+__device__ __forceinline__ int crt_ef(const ProbDev& P, int64_t idx) {
+  const int64_t row = idx / P.N, col = idx - row * P.N;
+  return __ldg(P.e + row) + __ldg(P.f + col);
+}
+
 // Round |c_hat| (nd digits in column e of s_mag, highest nonzero digit `top`,
 // -1 for zero) times 2^(e_i + f_j - 2t) to p bits, round-half-even, and write
-// output idx (limbs, exponent and sign, or a binary64 value).
+// output idx (limbs, exponent and sign, or a binary64 value); ef = e_i + f_j.
 __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t* s_mag, int ldm, int e, int nd,
-                                             int top, bool neg, int64_t idx) {
+                                             int top, bool neg, int64_t idx, int ef) {
   const int64_t row = idx / P.N, col = idx - row * P.N;
   auto mag_word = [&](int w) -> uint32_t {
     return (w >= 0 && w < nd) ? s_mag[w * ldm + e] : 0u;
@@ -337,7 +344,7 @@ __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t
     }
     limb0 = 1ull << 63;
   }
-  const int eo = n + P.e[row] + P.f[col] - 2 * P.t;
+  const int eo = n + ef - 2 * P.t;
   if (kind1) {
     double out;
     const int bexp = eo - 1 + 1023;
@@ -362,7 +369,7 @@ __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t
 // and P.  s_mag: scratch column e of a [ND][ldm] digit array.
 template <int ND>
 __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], const uint32_t* s_tab,
-                                           uint32_t* s_mag, int ldm, int e, int64_t idx, int32_t* status) {
+                                           uint32_t* s_mag, int ldm, int e, int64_t idx, int ef, int32_t* status) {
   const int D = P.D32;
   const uint32_t* negP = s_tab;
   const uint32_t* negH1 = s_tab + ND;
@@ -412,7 +419,7 @@ __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], 
     s_mag[d * ldm + e] = R[d];
     if (R[d]) top = d;
   }
-  crt_round_write(P, s_mag, ldm, e, ND, top, neg, idx);
+  crt_round_write(P, s_mag, ldm, e, ND, top, neg, idx, ef);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,37 +431,6 @@ __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], 
 // the whole CRT and rounding of its output with the digits in registers and
 // sequential exact carries.
 // ---------------------------------------------------------------------------
-// R = (sum_g Q_g 2^(224 g) + alpha~ (2^(32 D) - P)) mod 2^(32 D) from the
-// group sums of the tensor-core CRT (crt_mode 2): group g holds 9 words
-// starting at word 7 g, so word d collects word d - 7 g of group g = d / 7
-// and, for d mod 7 < 2, word d - 7 (g - 1) of the group before.  Digits in
-// registers (D <= ND).
-template <int ND>
-__device__ __forceinline__ void crt_assemble_regs(const ProbDev& P, const CrtView& cv, int64_t idx,
-                                                  uint32_t (&R)[ND]) {
-  const int64_t up = P.upitch;
-  const uint64_t alpha = (P.crt_sig[idx] + P.crt_sig[up + idx] + P.crt_sig[2 * up + idx] +
-                          P.crt_sig[3 * up + idx]) >> 32;
-  const int D = P.D32, ng = P.crt_ngrp;
-  uint32_t w0[ND], w1[ND];
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {                   // independent loads first
-    const int g = d / 7, k = d - 7 * g;
-    w0[d] = (d < D && g < ng) ? __ldg(P.crt_q + ((int64_t)g * 9 + k) * up + idx) : 0u;
-    w1[d] = (d < D && k < 2 && g >= 1 && g - 1 < ng) ? __ldg(P.crt_q + ((int64_t)(g - 1) * 9 + k + 7) * up + idx) : 0u;
-  }
-  uint64_t carry = 0;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    R[d] = 0u;
-    if (d < D) {
-      const uint64_t x = carry + alpha * __ldg(cv.negP + d) + w0[d] + w1[d];
-      R[d] = (uint32_t)x;
-      carry = x >> 32;
-    }
-  }
-}
-
 constexpr int kEpb1 = 128;
 
 // acc[d] += sum_l v_l M_l[d] for the first NM digits (the rest of M_l is zero)
@@ -486,14 +462,15 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   const int L = P.L;
   const int D = P.D32;
   const CrtView cv = crt_view(T.crt_pool, P);
+  const int e = threadIdx.x;
+  const int64_t idx = e0 + e;
+  const int ef = idx < MN ? crt_ef(P, idx) : 0;               // early: used by the rounding
   uint16_t* s_v = reinterpret_cast<uint16_t*>(s1);          // [L][kEpb1] (16-byte rows)
   uint32_t* s_M = s1 + L * (kEpb1 / 2);                       // [L][ND]
   uint32_t* s_mu = s_M + L * ND;                              // [L]
   uint32_t* s_tab = s_mu + L;                                 // [3][ND]: negP, negH1, P
   uint32_t* s_mag = s_tab + 3 * ND;                           // [ND][kEpb1]
-  const bool from_r = P.crt_mode == 2;     // S already summed in chunks on the tensor cores
-  if (!from_r)
-    for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
+  for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
   for (int i = threadIdx.x; i < ND; i += kEpb1) {
     s_tab[i] = __ldg(cv.negP + i);
     s_tab[ND + i] = __ldg(cv.negH1 + i);
@@ -502,7 +479,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   // v_l = (c mod m_l) M_l^{-1} mod m_l as the plane GEMM stored it: 16-byte
   // loads of 8 values; a block covers 16 x 8 = 128 outputs of 8 moduli per
   // pass, independent loads first
-  if (!from_r) {
+  {
     const int lane8 = threadIdx.x & 15;                       // which 8 outputs
     const int lrow = threadIdx.x >> 4;                        // modulus within the pass
     const bool full = e0 + kEpb1 <= MN;
@@ -535,15 +512,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
     }
   }
   __syncthreads();
-  const int e = threadIdx.x;
-  const int64_t idx = e0 + e;
   if (idx >= MN) return;
-  if (from_r) {
-    uint32_t R[ND];
-    crt_assemble_regs<ND>(P, cv, idx, R);
-    crt_finish<ND>(P, R, s_tab, s_mag, kEpb1, e, idx, T.status);
-    return;
-  }
 
   // quotient estimate alpha~ in {alpha - 1, alpha}
   uint64_t sig = 0;
@@ -567,7 +536,7 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
       c = x >> 32;
     }
   }
-  crt_finish<ND>(P, R, s_tab, s_mag, kEpb1, e, idx, T.status);
+  crt_finish<ND>(P, R, s_tab, s_mag, kEpb1, e, idx, ef, T.status);
 }
 
 
@@ -722,7 +691,7 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
         cr = x >> 32;
       }
       const int64_t idx = (int64_t)tp.y * 128 + er;
-      if (idx < (int64_t)P.M * P.N) crt_finish<ND>(P, R, s_tab, s_dig, 128, er, idx, T.status);
+      if (idx < (int64_t)P.M * P.N) crt_finish<ND>(P, R, s_tab, s_dig, 128, er, idx, crt_ef(P, idx), T.status);
     }
     __syncthreads();
   };
@@ -862,6 +831,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   const int e = threadIdx.x;
   const int64_t idx = (int64_t)b.y * kFinThreads + e;
   if (idx >= (int64_t)P.M * P.N) return;
+  const int ef = crt_ef(P, idx);
   const int64_t up = P.upitch;
   // the group words, copied asynchronously (all in flight at once; coalesced
   // across the block): words 0..6 of group d / 7 in digit order, and the
@@ -928,7 +898,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     dst[0] = neg;
     for (int d = 0; d < D; ++d) dst[1 + d] = s_R[d * kFinThreads + e];
   }
-  crt_round_write(P, s_R, kFinThreads, e, D, top, neg, idx);
+  crt_round_write(P, s_R, kFinThreads, e, D, top, neg, idx, ef);
 }
 
 // ---------------------------------------------------------------------------
