@@ -96,7 +96,7 @@ typedef struct {
   int schedule;   /* OZ2_SCHED_* */
   int timing;     /* nonzero: record per-stage CUDA events (ozaki2_last_timings) */
   int crt_engine; /* 0: automatic (default): engine 2 where the CRT accumulator needs more than
-                     40 32-bit digits, CUDA cores otherwise; 1: CRT column sums as an exact bf16
+                     24 32-bit digits (p above about 300), CUDA cores otherwise; 1: CRT column sums as an exact bf16
                      GEMM on the tensor cores where 2L <= 256, the accumulator has <= 40 digits
                      and the tables fit in shared memory (CUDA cores otherwise); 2: the column
                      sums of any length as an exact bf16 GEMM on the tensor cores, written as

@@ -345,9 +345,10 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int npad = (int)align_up((size_t)np, 16);
     const bool tc_ok = o.crt_engine == 1 && h.crt_cls <= 8 && kpad <= 256 && npad <= 256 &&
                        crt_tc_smem_bytes(h.crt_cls, kpad, npad, L, 1) <= 227 * 1024;
-    // automatic choice: the tensor-core sums where the accumulator needs more
-    // than the 40 digits of the one-lane CUDA-core CRT (lane groups otherwise)
-    const bool want_mm = o.crt_engine == 2 || (o.crt_engine == 0 && h.crt_cls > 8);
+    // automatic choice: the tensor-core sums above 24 accumulator digits
+    // (measured at 1024^3: equal at 21 digits, 0.266 vs 0.334 ms at 25, 0.42
+    // vs 0.67 ms at 33), the one-lane CUDA-core CRT below
+    const bool want_mm = o.crt_engine == 2 || (o.crt_engine == 0 && h.D32 > 24);
     // sums of any length: fp32 column sums exact for 2L 127^2 < 2^24, and V
     // for 128 outputs (kpad bf16 each) plus the rings must fit in shared memory
     // (the u copies are boxes of 32 moduli x 128 outputs: at least that many;

@@ -221,9 +221,9 @@ def test_p2048_small(ozk):
 
 @pytest.mark.parametrize("p", [300, 700])
 def test_crt_engines_bit_exact(ozk, p):
-    """The CRT engines (automatic, CUDA cores only, tensor-core column sums in
-    one kernel) give the same CRT integers and outputs, and all match the
-    oracle."""
+    """The CRT engines (automatic: the tensor-core sums above 24 digits, CUDA
+    cores only, tensor-core column sums in one kernel) give the same CRT
+    integers and outputs, and all match the oracle."""
     rng = np.random.Generator(np.random.PCG64(2010 + p))
     A = synth.mp_matrix(rng, 140, 60, p, -30, 30)
     B = synth.mp_matrix(rng, 60, 20, p, -30, 30)
@@ -238,9 +238,9 @@ def test_crt_engines_bit_exact(ozk, p):
 @pytest.mark.parametrize("shape", [(140, 20, 60, 300), (70, 45, 50, 700), (40, 36, 30, 1024),
                                    (20, 18, 24, 2048), (9, 15, 7, 130)])
 def test_crt_sum_engine_stages(ozk, shape):
-    """CRT sums on the tensor cores (crt_engine 2): one-lane finish (<= 40
-    digits) and the long finish (> 40 digits), one to five 128-column chunks,
-    ragged last tiles; every stage bit-exact against the oracle."""
+    """CRT sums on the tensor cores (crt_engine 2) and their finish from the
+    group sums, accumulators of 12 to 133 digits, one to five chunks, ragged
+    last tiles; every stage bit-exact against the oracle."""
     M, N, K, p = shape
     rng = np.random.Generator(np.random.PCG64(2040 + p))
     A = synth.mp_matrix(rng, M, K, p, -30, 30)

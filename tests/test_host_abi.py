@@ -143,11 +143,12 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
 
 
 def test_crt_engine_choice(ozk):
-    """The automatic CRT choice: tensor-core sums only where the accumulator
-    needs more than 40 digits; engine 3 keeps the CUDA cores; engine 2 asks for
-    the sums wherever the shape qualifies (L >= 32, M N >= 128)."""
-    lo, hi = (64, 64, 64, 256), (64, 64, 64, 1024)
-    assert ozk.Plan(lo).info["crt_digits"] <= 40 and ozk.Plan(lo).info["crt_mode"] == 0
+    """The automatic CRT choice: tensor-core sums where the accumulator needs
+    more than 24 digits; engine 3 keeps the CUDA cores; engine 2 asks for the
+    sums wherever the shape qualifies (L >= 32, M N >= 128)."""
+    lo, mid, hi = (64, 64, 64, 256), (64, 64, 64, 384), (64, 64, 64, 1024)
+    assert ozk.Plan(lo).info["crt_digits"] <= 24 and ozk.Plan(lo).info["crt_mode"] == 0
+    assert ozk.Plan(mid).info["crt_digits"] > 24 and ozk.Plan(mid).info["crt_mode"] == 2
     assert ozk.Plan(hi).info["crt_digits"] > 40 and ozk.Plan(hi).info["crt_mode"] == 2
     assert ozk.Plan(hi, crt_engine=3).info["crt_mode"] == 0
     assert ozk.Plan(lo, crt_engine=2).info["crt_mode"] == 2
