@@ -190,7 +190,7 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # one ncu capture of the committed kernels on the same workload; the source
 # summaries are under profiles/.  A kernel changed since its capture has None.
 NCU_TRAFFIC = {
-    "gemm_1024_p256": {"residues": 444.22016e6, "gemm": 564.279552e6, "crt": 168.749056e6},
+    "gemm_1024_p256": {"residues": 444.22016e6, "gemm": 564.279552e6, "crt_sums": None, "crt_finish": None},
 }
 
 
@@ -204,8 +204,15 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
       multiply-add rate.
     gemm: 2 M N K G flops of the G plane products, against the measured bf16
       tensor peak (the integer planes are exact bf16 operands).
-    crt: the 32 x 32 -> 64-bit multiply-adds of sum_l v_l M_l, L per output
-      and digit of M_l: M N L ceil(bits(P)/32), against the IMAD.WIDE rate.
+    crt (CUDA-core CRT): the 32 x 32 -> 64-bit multiply-adds of
+      sum_l v_l M_l, L per output and digit of M_l: M N L ceil(bits(P)/32),
+      against the IMAD.WIDE rate.
+    crt_sums (tensor-core CRT): the exact bf16 products of the column sums
+      Y = V B, 2 M N (2L) np flops with np 7-bit pieces of P, against the
+      bf16 tensor peak.
+    crt_finish (after the sums): the bytes it moves, the group words it reads
+      (D + 2 ceil(D/7) per output), the four 8-byte partial quotient sums and
+      the output (8 nl + 5 bytes), against HBM.
     scan: the bytes of the two exponent vectors' inputs, against HBM.
     """
     peaks, src = load_peaks()
@@ -227,8 +234,27 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
     res_macs = (M + N) * K * math.ceil((t + 1) / 8) * (L1 + 2 * L2)
     alu("residues", "k_residue (integerize + byte-table residues + plane writes)", res_macs,
         SMS * DP4A_MACS_PER_SM_CLK * clk, "byteMAC")
-    alu("crt", "k_crt1 / k_crt (direct CRT sum + quotient correction + rounding)", M * N * L * md,
-        SMS * IMAD_WIDE_PER_SM_CLK * clk, "imad64")
+    if "crt" in stages:
+        alu("crt", "k_crt1 / k_crt (direct CRT sum + quotient correction + rounding)", M * N * L * md,
+            SMS * IMAD_WIDE_PER_SM_CLK * clk, "imad64")
+    if "crt_sums" in stages:
+        np_ = info["crt_pieces"]
+        fl = 2.0 * M * N * (2 * L) * np_
+        ach = fl / (stages["crt_sums"] / 1e3) / 1e12
+        pk = float(peaks["bf16_tflops"])
+        out["crt_sums"] = {"kernel": "k_crt_mm (CRT column sums as an exact bf16 GEMM + group carries)",
+                           "bound": "tensor", "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s",
+                           "frac": round(ach / pk, 4), "peak_source": f"bf16_tflops burst, {src}",
+                           "traffic": traffic.get("crt_sums")}
+        D = info["crt_digits"]
+        nl = -(-p // 64)
+        fb = M * N * (4 * (D + 2 * -(-D // 7)) + 32 + 8 * nl + 5)
+        ach = fb / (stages["crt_finish"] / 1e3) / 1e9
+        pk = float(peaks["hbm_gbs"])
+        out["crt_finish"] = {"kernel": "k_crt_fin_long (CRT finish from the group sums + rounding)",
+                             "bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
+                             "frac": round(ach / pk, 4), "peak_source": f"hbm_gbs, {src}",
+                             "traffic": traffic.get("crt_finish")}
     flops = 2.0 * M * N * K * G
     ach = flops / (stages["gemm"] / 1e3) / 1e12
     pk = float(peaks["bf16_tflops"])
@@ -304,7 +330,7 @@ def run_ours(args):
         starts[s].record(stream)
         plan.execute(dA, dB, dC, ws)
         ends[s].record(stream)
-        stage.append(plan.timings())
+        stage.append({**plan.timings(), **plan.crt_split()})
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
@@ -379,12 +405,19 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (library stage events on the launch stream)
     med = {k: statistics.median(s_[k] for s_ in stage) for k in stage[0]}
-    stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
-    kernels = stage_rooflines(plan.info, M, N, K, p, stages, WORK["workload"])
+    info = dict(plan.info)
+    if info["crt_mode"] == 2:        # two kernels: the sums on the tensor cores, then the finish
+        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt_sums", "crt_finish")}
+        Pm = 1
+        for m in plan.moduli():
+            Pm *= m
+        info["crt_pieces"] = (Pm.bit_length() + 6) // 7 + 1
+    else:
+        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
+    kernels = stage_rooflines(info, M, N, K, p, stages, WORK["workload"])
     dom = max(stages, key=stages.get)
     roof = dict(kernels[dom])
     roof["stage_ms"] = {k: round(v, 4) for k, v in stages.items()}
-    info = plan.info
     gemm_tflops = 2.0 * M * N * K * info["G"] / (stages["gemm"] / 1e3) / 1e12
 
     line = {

@@ -96,7 +96,7 @@ typedef struct {
   int schedule;   /* OZ2_SCHED_* */
   int timing;     /* nonzero: record per-stage CUDA events (ozaki2_last_timings) */
   int crt_engine; /* 0: automatic (default): engine 2 where the CRT accumulator needs more than
-                     24 32-bit digits (p above about 300), CUDA cores otherwise; 1: CRT column sums as an exact bf16
+                     20 32-bit digits (p above about 240), CUDA cores otherwise; 1: CRT column sums as an exact bf16
                      GEMM on the tensor cores where 2L <= 256, the accumulator has <= 40 digits
                      and the tables fit in shared memory (CUDA cores otherwise); 2: the column
                      sums of any length as an exact bf16 GEMM on the tensor cores, written as
@@ -256,6 +256,12 @@ OZ2_API int ozaki2_check(ozaki2_plan plan, void* stream);
    residues + plane writes), [2] plane GEMMs with fused mod-reduce, [3] CRT and
    rounding, [4] total.  Synchronises on the recorded events. */
 OZ2_API int ozaki2_last_timings(ozaki2_plan plan, float ms[5]);
+
+/* The CRT stage of the same execute split in two, in milliseconds: [0] the
+   column sums on the tensor cores (crt_engine 2; about 0 where none ran),
+   [1] the rest (the finish from the group sums, or the whole CUDA-core CRT).
+   Synchronises on the recorded events. */
+OZ2_API int ozaki2_last_crt_split(ozaki2_plan plan, float ms[2]);
 
 /* ---------------------------------------------------------------------------
  * binary64 mode (p = 53): C = A B for row-major double matrices, computed

@@ -180,6 +180,13 @@ class Plan:
         check(lib().ozaki2_last_timings(self._h, ms), "ozaki2_last_timings")
         return dict(zip(["scan", "residues", "gemm", "crt", "total"], list(ms)))
 
+    def crt_split(self):
+        """The CRT stage of the last timed execute: tensor-core column sums
+        (about 0 where none ran) and the rest, in ms."""
+        ms = (C.c_float * 2)()
+        check(lib().ozaki2_last_crt_split(self._h, ms), "ozaki2_last_crt_split")
+        return {"crt_sums": ms[0], "crt_finish": ms[1]}
+
 
 def gemm(A: MPMatrix, B: MPMatrix, p: int | None = None, stream=None, **kw) -> MPMatrix:
     """C = A B rounded to p bits (default: A's precision) through a cached plan."""

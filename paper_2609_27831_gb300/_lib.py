@@ -81,6 +81,7 @@ _SIGS = {
     "ozaki2_release_cache": (C.c_int, []),
     "ozaki2_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ozaki2_last_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "ozaki2_last_crt_split": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "ozaki2_dgemm_fwd": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.POINTER(Opts),
                                     C.POINTER(C.c_void_p), C.c_void_p]),

@@ -211,6 +211,7 @@ struct DevState {
   int tct_npad[9] = {0};
   std::vector<ListRef> cmt;     // tensor-core CRT sum tiles, one list per TMEM layout (smem = chunk width)
   ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = groups max)
+  ListRef fsh[9];               // finish blocks of one-lane classes after the tensor-core sums
   std::vector<ListRef> rmt;     // warp-specialised tensor-core residue tiles, one list per TMEM layout (smem = cw)
   ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
   int rtt_npad = 0;
@@ -238,7 +239,9 @@ struct ozaki2_plan_s {
   oz2::DevState dev;
   oz2::LaunchBlock lb;
   std::vector<uint32_t*> dbg_chat;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // stage boundaries: scan, residues, GEMM, CRT, end; [5] between the
+  // tensor-core CRT sums and the rest of the CRT stage
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timed = false;
 };
 
@@ -345,10 +348,10 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int npad = (int)align_up((size_t)np, 16);
     const bool tc_ok = o.crt_engine == 1 && h.crt_cls <= 8 && kpad <= 256 && npad <= 256 &&
                        crt_tc_smem_bytes(h.crt_cls, kpad, npad, L, 1) <= 227 * 1024;
-    // automatic choice: the tensor-core sums above 24 accumulator digits
-    // (measured at 1024^3: equal at 21 digits, 0.266 vs 0.334 ms at 25, 0.42
-    // vs 0.67 ms at 33), the one-lane CUDA-core CRT below
-    const bool want_mm = o.crt_engine == 2 || (o.crt_engine == 0 && h.D32 > 24);
+    // automatic choice: the tensor-core sums above 20 accumulator digits
+    // (measured at 1024^3: 0.238 vs 0.248 ms at 21 digits, 0.27 vs 0.33 at 25,
+    // 0.42 vs 0.67 at 33; 0.21 vs 0.18 at 17), the one-lane CUDA-core CRT below
+    const bool want_mm = o.crt_engine == 2 || (o.crt_engine == 0 && h.D32 > 20);
     // sums of any length: fp32 column sums exact for 2L 127^2 < 2^24, and V
     // for 128 outputs (kpad bf16 each) plus the rings must fit in shared memory
     // (the u copies are boxes of 32 moduli x 128 outputs: at least that many;
@@ -545,6 +548,8 @@ struct TableImage {
   // tiles: one launch per TMEM layout, {first tile, tiles, chunk width}
   size_t o_cmt = 0, o_finl = 0;
   std::vector<std::array<int, 3>> cmt_seg, rmt_seg;
+  size_t o_fsh[9] = {0};            // short finish blocks per one-lane class (after the tensor-core sums)
+  int n_fsh[9] = {0};
   int n_finl = 0, finl_dmax = 0, finl_gmax = 0;
   size_t o_rmt = 0;
   size_t o_rtt = 0;                 // tensor-core residue tile list
@@ -669,7 +674,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
 
   // block lists
   std::vector<int4> scan_rows, scan_cols, simt;
-  std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9);
+  std::vector<std::vector<int4>> res(6), crt(kCrtClassCount), tct(9), fsh(9);
   std::vector<int4> rtt, finl;
   // tiles of the warp-specialised kernels grouped by TMEM layout (tiles of
   // one launch share the column map of their buffers and slots)
@@ -719,15 +724,22 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.tct_npad[h.crt_cls] = std::max(ti.tct_npad[h.crt_cls], h.crt_npad);
       ti.tct_l[h.crt_cls] = std::max(ti.tct_l[h.crt_cls], h.L);
     } else if (h.crt_mode == 2) {
-      // sums on the tensor cores, then the finish from the group sums
-      // (k_crt_fin_long: every word copied in at once, then the digits in order)
+      // sums on the tensor cores, then the finish from the group sums: R in
+      // registers up to 24 digits (k_crt_fin_short), else in shared memory
+      // (k_crt_fin_long, ahead from 28 digits on: at 37 digits 1.53 vs 1.75
+      // ms at 2048^3, its 40 registers keep more warps resident); both load
+      // every group word at once
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
       std::vector<int4>& cl = cmt_by[{h.crt_kpad, h.crt_cw, h.crt_nslot}];
       for (int64_t tt = 0; tt < nt; ++tt) cl.push_back(make_int4(pi, (int)tt, 0, 0));
-      for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
-      ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
-      ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
+      if (h.crt_cls <= 4) {
+        for (int64_t bb = 0; bb < nt; ++bb) fsh[h.crt_cls].push_back(make_int4(pi, (int)bb, 0, 0));
+      } else {
+        for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
+        ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
+        ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
+      }
     } else {
       const int epb = crt_class_elems_per_block(h.crt_cls);
       const int64_t nb = (h.M * h.N + epb - 1) / epb;
@@ -772,7 +784,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
     if (h.crt_mode == 2 && (h.crt_cw % 32 != 0 || h.crt_nvbuf * (h.crt_kpad / 2) + h.crt_nslot * h.crt_cw > 512 ||
-                            ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))
+                            (h.crt_cls > 4 && (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
       return OZ2_EINTERNAL;
   }
   std::vector<int4> cmt, rmt;
@@ -789,6 +801,10 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   if (!finl.empty() && 3 * ti.finl_dmax * 4 + (ti.finl_dmax + 2 * ti.finl_gmax) * 128 * 4 > 200 * 1024)
     return OZ2_EINTERNAL;
   ti.o_cmt = ti.b.add(cmt.data(), cmt.size() * 16);
+  for (int c = 0; c < 9; ++c) {
+    ti.o_fsh[c] = ti.b.add(fsh[c].data(), fsh[c].size() * 16);
+    ti.n_fsh[c] = (int)fsh[c].size();
+  }
   ti.o_finl = ti.b.add(finl.data(), finl.size() * 16);
   ti.n_finl = (int)finl.size();
   ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
@@ -845,6 +861,7 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   for (const auto& sg : ti.cmt_seg)
     d.cmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt) + 4 * sg[0], sg[1], sg[2], 0});
   d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
+  for (int c = 0; c < 9; ++c) d.fsh[c] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_fsh[c]), ti.n_fsh[c], 0, 0};
   d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
   d.rmt.clear();
   for (const auto& sg : ti.rmt_seg)
@@ -1066,6 +1083,9 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
   for (const ListRef& r : d.cmt) OZ2_CU(launch_crt_mm(tab, r.ptr, r.n, r.smem, d.sms, s));
+  if (timing) OZ2_CU(cudaEventRecord(pl->ev[5], s));
+  for (int c = 0; c < 9; ++c)
+    if (d.fsh[c].n) OZ2_CU(launch_crt_fin_short(tab, c, d.fsh[c].ptr, d.fsh[c].n, s));
   if (d.finl.n) OZ2_CU(launch_crt_finish_long(tab, d.finl.ptr, d.finl.n, d.finl.smem, d.finl.lmax, s));
   for (int c = 0; c < kCrtClassCount; ++c)
     if (d.crt[c].n) OZ2_CU(launch_crt(tab, c, d.crt[c].ptr, d.crt[c].n, d.crt[c].lmax, s));
@@ -1278,6 +1298,7 @@ int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
   else c += (int)d.plain.size();
   c += (int)d.cmt.size();
   c += d.finl.n ? 1 : 0;
+  for (int i = 0; i < 9; ++i) c += d.fsh[i].n ? 1 : 0;
   for (int i = 0; i < kCrtClassCount; ++i) c += d.crt[i].n ? 1 : 0;
   for (int i = 0; i < 9; ++i) c += d.tct[i].n ? 1 : 0;
   *n = c;
@@ -1379,6 +1400,14 @@ int ozaki2_last_timings(ozaki2_plan pl, float ms[5]) {
   for (int i = 0; i < 4; ++i)
     if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return OZ2_ECUDA;
   if (cudaEventElapsedTime(&ms[4], pl->ev[0], pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
+  return OZ2_OK;
+}
+
+int ozaki2_last_crt_split(ozaki2_plan pl, float ms[2]) {
+  if (!pl || !ms || !pl->timed || !pl->ev[0]) return OZ2_EINVAL;
+  if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
+  if (cudaEventElapsedTime(&ms[0], pl->ev[3], pl->ev[5]) != cudaSuccess) return OZ2_ECUDA;
+  if (cudaEventElapsedTime(&ms[1], pl->ev[5], pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
   return OZ2_OK;
 }
 

@@ -901,6 +901,57 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   crt_round_write(P, s_R, kFinThreads, e, D, top, neg, idx, ef);
 }
 
+// The finish of short accumulators (D <= ND digits, used up to 24) after the
+// tensor-core CRT sums, R in registers: every group word and the four partial
+// quotient sums are loaded at once (coalesced across the block), then
+// R = (sum_g Q_g 2^(224 g) + alpha~ (2^(32 D) - P)) mod 2^(32 D), then the same
+// unrolled steps as k_crt1 (crt_finish).  Group g holds 9 words starting at
+// word 7 g, so word d collects word d - 7 g of group g = d / 7 and, for
+// d mod 7 < 2, word d - 7 (g - 1) of the group before.
+template <int ND>
+__global__ void __launch_bounds__(kFinThreads) k_crt_fin_short(DevTables T, const int4* __restrict__ blk) {
+  __shared__ uint32_t s_tab[3 * ND];              // 2^(32 D) - P, 2^(32 D) - floor(P/2) - 1, P
+  __shared__ uint32_t s_mag[ND * kFinThreads];    // rounding scratch
+  const int4 b = blk[blockIdx.x];
+  const ProbDev& P = T.probs[b.x];
+  const CrtView cv = crt_view(T.crt_pool, P);
+  const int D = P.D32, ng = P.crt_ngrp;
+  for (int i = threadIdx.x; i < ND; i += kFinThreads) {
+    s_tab[i] = i < D ? __ldg(cv.negP + i) : 0u;
+    s_tab[ND + i] = i < D ? __ldg(cv.negH1 + i) : 0u;
+    s_tab[2 * ND + i] = i < D ? __ldg(cv.P + i) : 0u;
+  }
+  const int e = threadIdx.x;
+  const int64_t idx = (int64_t)b.y * kFinThreads + e;
+  const bool valid = idx < (int64_t)P.M * P.N;
+  const int64_t up = P.upitch;
+  const uint32_t* const qcol = P.crt_q + (valid ? idx : 0);
+  const uint64_t* const scol = P.crt_sig + (valid ? idx : 0);
+  uint32_t w0[ND], w1[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {                   // independent loads first
+    const int g = d / 7, k = d - 7 * g;
+    w0[d] = (d < D && g < ng) ? __ldg(qcol + ((int64_t)g * 9 + k) * up) : 0u;
+    w1[d] = (d < D && k < 2 && g >= 1 && g - 1 < ng) ? __ldg(qcol + ((int64_t)(g - 1) * 9 + k + 7) * up) : 0u;
+  }
+  uint64_t sig = 0;
+#pragma unroll
+  for (int h = 0; h < kCmQuarters; ++h) sig += __ldg(scol + h * up);
+  const int ef = valid ? crt_ef(P, idx) : 0;
+  __syncthreads();
+  if (!valid) return;
+  const uint64_t alpha = sig >> 32;
+  uint32_t R[ND];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const uint64_t x = carry + alpha * s_tab[d] + w0[d] + w1[d];
+    R[d] = d < D ? (uint32_t)x : 0u;
+    carry = x >> 32;
+  }
+  crt_finish<ND>(P, R, s_tab, s_mag, kFinThreads, e, idx, ef, T.status);
+}
+
 // ---------------------------------------------------------------------------
 // CRT sums of any length on the tensor cores (crt_mode 2).  As in k_crt_tc,
 // S = sum_l v_l M_l = sum_j 128^j Y_j with Y = V B (K = 2L: the 7-bit halves
@@ -963,9 +1014,15 @@ __device__ __forceinline__ uint32_t f2u_exact24(uint32_t bits) {
   return f >= 8388608.0f ? bits - 0x4A800000u : __float_as_uint(f + 8388608.0f) - 0x4B000000u;
 }
 
-// bf16 bits of an integer 0 <= x < 256: 2^23 + x has x in its low mantissa bits
-__device__ __forceinline__ uint32_t bf16_small(uint32_t x) {
-  return __float_as_uint(__uint_as_float(0x4B000000u | x) - 8388608.0f) >> 16;
+
+// {bf16(v mod 128), bf16(floor(v / 128))} for v < 2^14 (low half, high half):
+// 2^23 + x has x in its low mantissa bits; both halves are exact in bf16
+__device__ __forceinline__ uint32_t bf16_halves7(uint32_t v) {
+  const float f0 = __uint_as_float(0x4B000000u | (v & 127u)) - 8388608.0f;
+  const float f1 = __uint_as_float(0x4B000000u | (v >> 7)) - 8388608.0f;
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f1), "f"(f0));
+  return r;
 }
 
 // Add 32 pieces y[q] 2^(7 q) of one group into the 7 word accumulators.
@@ -973,6 +1030,27 @@ template <int NQ>
 __device__ __forceinline__ void crt_group(const uint32_t* y, uint64_t (&acc)[7]) {
 #pragma unroll
   for (int q = 0; q < NQ; ++q) acc[(7 * q) >> 5] += (uint64_t)f2u_exact24(y[q]) << ((7 * q) & 31);
+}
+
+// sum over the pieces q < NQ in word w of 0x4B000000 2^(7 q mod 32)
+template <int NQ>
+__device__ __forceinline__ constexpr uint64_t crt_group_bias(int w) {
+  uint64_t b = 0;
+  for (int q = 0; q < NQ; ++q)
+    if (((7 * q) >> 5) == w) b += 0x4B000000ull << ((7 * q) & 31);
+  return b;
+}
+
+// The same for sums below 2^23 (2L 127^2 < 2^23): the bits of y + 2^23 are
+// 0x4B000000 + y, one add per piece; the 0x4B000000 terms come off once per
+// word (modulo 2^64, the true word sums fit).
+template <int NQ>
+__device__ __forceinline__ void crt_group_small(const uint32_t* y, uint64_t (&acc)[7]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    acc[(7 * q) >> 5] += (uint64_t)__float_as_uint(__uint_as_float(y[q]) + 8388608.0f) << ((7 * q) & 31);
+#pragma unroll
+  for (int w = 0; w < 7; ++w) acc[w] -= crt_group_bias<NQ>(w);
 }
 
 __global__ void __launch_bounds__(kCmThreads, 1)
@@ -1180,12 +1258,26 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         if (!ok) return;
         const uint16_t* su = s_u + s * (kCmUMods * 128);
         uint32_t pr[kCmUMods];
+        if (l0 + kCmUMods <= L) {                   // a full copy: no bounds
 #pragma unroll
-        for (int q = 0; q < kCmUMods; ++q) {
-          const int l = l0 + q;
-          const uint32_t v = l < L ? (uint32_t)su[q * 128 + row] : 0u;
-          sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
-          pr[q] = bf16_small(v & 127u) | (bf16_small(v >> 7) << 16);
+          for (int q4 = 0; q4 < kCmUMods / 4; ++q4) {
+            const uint4 mu4 = *reinterpret_cast<const uint4*>(s_mu + l0 + 4 * q4);
+            const uint32_t mu[4] = {mu4.x, mu4.y, mu4.z, mu4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint32_t v = su[(4 * q4 + j) * 128 + row];
+              sig += (uint64_t)v * mu[j];
+              pr[4 * q4 + j] = bf16_halves7(v);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < kCmUMods; ++q) {
+            const int l = l0 + q;
+            const uint32_t v = l < L ? (uint32_t)su[q * 128 + row] : 0u;
+            sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
+            pr[q] = bf16_halves7(v);
+          }
         }
         mbar_arrive(u_free + s);
         tmem_st32(vrow + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
@@ -1202,6 +1294,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       const ProbDev& P = T.probs[tl.x];
       const int cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad, nslot = P.crt_nslot;
       const uint32_t acc0 = (uint32_t)P.crt_nvbuf * ((uint32_t)P.crt_kpad / 2);
+      const bool small = 2 * P.L * 127 * 127 < (1 << 23);   // every column sum below 2^23
       const int64_t idx = (int64_t)tl.y * 128 + row;
       const bool valid = idx < (int64_t)P.M * P.N;
       const int64_t up = P.upitch;
@@ -1221,11 +1314,13 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           if (g + 32 <= ncol) {
             uint32_t y[32];
             tmem_ld32(trow + (uint32_t)g, y);
-            crt_group<32>(y, acc);
+            if (small) crt_group_small<32>(y, acc);
+            else crt_group<32>(y, acc);
           } else if (g < ncol) {                      // 16 columns left
             uint32_t y[16];
             tmem_ld16(trow + (uint32_t)g, y);
-            crt_group<16>(y, acc);
+            if (small) crt_group_small<16>(y, acc);
+            else crt_group<16>(y, acc);
           }
           // group sum as 9 words: 7 word sums with carries, then the carry
           uint32_t* qcol = qbase + (int64_t)((c * cw + g) >> 5) * 9 * up + (valid ? idx : 0);
@@ -1388,6 +1483,24 @@ cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int n
   if (nblk == 0) return cudaSuccess;
   const int smem = 3 * dmax * 4 + dmax * kFinThreads * 4 + 2 * gmax * kFinThreads * 4;
   k_crt_fin_long<<<nblk, kFinThreads, smem, s>>>(t, reinterpret_cast<const int4*>(blk));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_crt_fin_short(const DevTables& t, int cls, const int32_t* blk, int nblk, cudaStream_t s) {
+  if (nblk == 0) return cudaSuccess;
+  const int4* bl = reinterpret_cast<const int4*>(blk);
+  switch (cls) {
+    case 0: k_crt_fin_short<8><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 1: k_crt_fin_short<12><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 2: k_crt_fin_short<16><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 3: k_crt_fin_short<20><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 4: k_crt_fin_short<24><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 5: k_crt_fin_short<28><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 6: k_crt_fin_short<32><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 7: k_crt_fin_short<36><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    case 8: k_crt_fin_short<40><<<nblk, kFinThreads, 0, s>>>(t, bl); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

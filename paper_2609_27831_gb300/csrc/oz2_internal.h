@@ -164,6 +164,8 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
                           cudaStream_t s);
 int crt_mm_chunk(int kpad, int npad, int* nslot);
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
+// the finish of one-lane classes (0..8: <= 40 digits) after the tensor-core sums
+cudaError_t launch_crt_fin_short(const DevTables& t, int cls, const int32_t* blk, int nblk, cudaStream_t s);
 cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
                                    cudaStream_t s);
 // Tensor-core residues: persistent tiles of 4 lines x 32 k.

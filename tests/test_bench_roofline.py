@@ -1,0 +1,40 @@
+"""Host arithmetic of the benchmark's per-kernel roofline objects (CPU)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _info(**kw):
+    base = {"L": 70, "L1": 54, "G": 102, "t": 282, "crt_digits": 21}
+    base.update(kw)
+    return base
+
+
+def test_cuda_core_crt_stage():
+    M = N = K = 1024
+    st = {"scan": 0.02, "residues": 0.2, "gemm": 0.18, "crt": 0.25}
+    out = bench.stage_rooflines(_info(), M, N, K, 256, st, "none")
+    assert set(out) == {"scan", "residues", "gemm", "crt"}
+    assert out["crt"]["bound"] == "alu"
+    # M N L (D - 2) multiply-adds in 0.25 ms
+    assert out["crt"]["achieved"] == pytest.approx(M * N * 70 * 19 / 0.25e-3 / 1e12, rel=1e-3)
+    assert out["gemm"]["achieved"] == pytest.approx(2.0 * M * N * K * 102 / 0.18e-3 / 1e12, rel=1e-3)
+
+
+def test_tensor_core_crt_stages():
+    M = N = K = 1024
+    st = {"scan": 0.02, "residues": 0.2, "gemm": 0.18, "crt_sums": 0.15, "crt_finish": 0.09}
+    out = bench.stage_rooflines(_info(crt_pieces=83), M, N, K, 256, st, "none")
+    assert set(out) == {"scan", "residues", "gemm", "crt_sums", "crt_finish"}
+    s, f = out["crt_sums"], out["crt_finish"]
+    assert s["bound"] == "tensor" and f["bound"] == "hbm"
+    assert s["achieved"] == pytest.approx(2.0 * M * N * 140 * 83 / 0.15e-3 / 1e12, abs=0.05)
+    # group words D + 2 ceil(D/7), four 8-byte partial sums, 4 limbs + exponent + sign out
+    per = 4 * (21 + 2 * 3) + 32 + 8 * 4 + 5
+    assert f["achieved"] == pytest.approx(M * N * per / 0.09e-3 / 1e9, abs=0.05)
+    assert 0 < f["frac"] < 1.5 and 0 < s["frac"] < 1.5

@@ -221,7 +221,7 @@ def test_p2048_small(ozk):
 
 @pytest.mark.parametrize("p", [300, 700])
 def test_crt_engines_bit_exact(ozk, p):
-    """The CRT engines (automatic: the tensor-core sums above 24 digits, CUDA
+    """The CRT engines (automatic: the tensor-core sums above 20 digits, CUDA
     cores only, tensor-core column sums in one kernel) give the same CRT
     integers and outputs, and all match the oracle."""
     rng = np.random.Generator(np.random.PCG64(2010 + p))

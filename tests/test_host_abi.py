@@ -144,11 +144,13 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
 
 def test_crt_engine_choice(ozk):
     """The automatic CRT choice: tensor-core sums where the accumulator needs
-    more than 24 digits; engine 3 keeps the CUDA cores; engine 2 asks for the
+    more than 20 digits; engine 3 keeps the CUDA cores; engine 2 asks for the
     sums wherever the shape qualifies (L >= 32, M N >= 128)."""
-    lo, mid, hi = (64, 64, 64, 256), (64, 64, 64, 384), (64, 64, 64, 1024)
-    assert ozk.Plan(lo).info["crt_digits"] <= 24 and ozk.Plan(lo).info["crt_mode"] == 0
-    assert ozk.Plan(mid).info["crt_digits"] > 24 and ozk.Plan(mid).info["crt_mode"] == 2
+    lo, mid, hi = (64, 64, 64, 200), (64, 64, 64, 384), (64, 64, 64, 1024)
+    assert ozk.Plan(lo).info["crt_digits"] <= 20 and ozk.Plan(lo).info["crt_mode"] == 0
+    assert ozk.Plan((1024, 1024, 1024, 256)).info["crt_digits"] == 21
+    assert ozk.Plan((1024, 1024, 1024, 256)).info["crt_mode"] == 2
+    assert ozk.Plan(mid).info["crt_digits"] > 20 and ozk.Plan(mid).info["crt_mode"] == 2
     assert ozk.Plan(hi).info["crt_digits"] > 40 and ozk.Plan(hi).info["crt_mode"] == 2
     assert ozk.Plan(hi, crt_engine=3).info["crt_mode"] == 0
     assert ozk.Plan(lo, crt_engine=2).info["crt_mode"] == 2
