@@ -164,7 +164,7 @@ struct ProbHost {
   int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot, crt_nvbuf;
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [4][upitch] u64
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
-  int res_cw, res_nchunk, res_tcols;           // res_mode 2: chunk width, chunks, TMEM columns
+  int res_cw, res_nchunk, res_nabuf;           // res_mode 2: chunk width, chunks, byte buffers
 };
 
 // Tensor-core residue table [npad][kpad] (bf16 bits): row l (one-limb) =
@@ -414,9 +414,9 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     h.res_kpad = kpad;
     h.res_npad = npad;
     h.res_cw = h.res_nchunk = 0;
-    h.res_tcols = 0;
+    h.res_nabuf = 0;
     if (h.res_mode == 2) {
-      residue_mm_geometry(kpad, npad, &h.res_cw, &h.res_tcols);
+      residue_mm_geometry(kpad, npad, &h.res_cw, &h.res_nabuf);
       h.res_nchunk = (npad + h.res_cw - 1) / h.res_cw;
     }
     const int rows = h.res_mode == 2 ? h.res_cw * h.res_nchunk : npad;
@@ -695,7 +695,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     for (int side = 0; h.res_mode == 2 && side < 2; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
-      std::vector<int4>& rl = rmt_by[{h.res_kpad, h.res_cw, 0}];
+      std::vector<int4>& rl = rmt_by[{h.res_kpad, h.res_cw, h.res_nabuf}];
       for (int64_t r = 0; r < R; r += 4)
         for (int64_t k = 0; k < h.K; k += 32) rl.push_back(make_int4(pi, side, (int)r, (int)k));
     }
@@ -810,7 +810,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.o_rtt = ti.b.add(rtt.data(), rtt.size() * 16);
   ti.n_rtt = (int)rtt.size();
   for (const ProbHost& h : pl->probs)
-    if (h.res_mode == 2 && (h.res_cw % 32 != 0 || h.res_kpad + 2 * h.res_cw > h.res_tcols))
+    if (h.res_mode == 2 && (h.res_cw % 32 != 0 || h.res_nabuf * (h.res_kpad / 2) + 2 * h.res_cw > 512))
       return OZ2_EINTERNAL;
   ti.o_rmt = ti.b.add(rmt.data(), rmt.size() * 16);
   ti.o_rtab.assign(pl->rtabs.size(), 0);
@@ -978,6 +978,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.res_npad = h.res_npad;
     P.res_cw = h.res_cw;
     P.res_nchunk = h.res_nchunk;
+    P.res_nabuf = h.res_nabuf;
     if (h.res_mode != 0) {
       // mode 1: the whole table in K blocks; mode 2: K block x cw columns
       const int rows = pl->rtabs[h.res_key].rows;

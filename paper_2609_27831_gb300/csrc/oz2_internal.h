@@ -88,6 +88,8 @@ struct ProbDev {
   int32_t res_cw;        // res_mode 2: columns of Y per chunk (a multiple of 32)
   int32_t res_nchunk;    // res_mode 2: chunks
   int32_t crt_nslot;     // crt_mode 2: TMEM accumulator slots (1 or 2)
+  int32_t res_nabuf;     // res_mode 2: byte buffers (A) in TMEM (2 or 4)
+  int32_t pad9;
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -175,7 +177,7 @@ int residue_tc_smem_bytes(int kpad, int npad, int lmax);
 // Warp-specialised tensor-core residues (res_mode 2): the same tiles.
 cudaError_t launch_residues_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int tcols,
                                int sms, cudaStream_t s);
-void residue_mm_geometry(int kpad, int npad, int* cw, int* tcols);
+void residue_mm_geometry(int kpad, int npad, int* cw, int* nabuf);
 int residue_mm_smem_bytes(int cw_max, int lmax, int tcols, int* stages);
 
 // Internal plan variants used by the binary64 mode.

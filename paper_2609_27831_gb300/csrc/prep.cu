@@ -690,14 +690,16 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 // the A operand (two bf16 bytes per 32-bit column, two buffers), the table
 // streams through a shared-memory ring as B in blocks of 64 bytes x cw
 // columns, and Y runs in chunks of cw columns through two accumulator slots:
-//   [A0: kpad/2][A1: kpad/2][slot 0: cw][slot 1: cw]  <= 512 TMEM columns.
+//   [A0 .. A(nabuf-1): kpad/2 each][slot 0: cw][slot 1: cw]  <= 512 TMEM columns
+// with nabuf = 2 or 4 byte buffers (uniform within a launch).
 //   warp 0      TMA producer of the table blocks
-//   warp 1      MMA issuer: tile t reads A buffer t & 1; chunk c into slot
-//               c & 1; commits per ring stage, per chunk and per tile
-//   warps 2-5   one per TMEM lane quadrant: integerize the tile's elements and
-//               write their bytes into A buffer t & 1 once the MMAs of tile
-//               t - 2 are done, so that they run ahead of the epilogue
-//   warps 6-21  four per lane quadrant (sub-groups s = 0..3): the tile's
+//   warp 1      MMA issuer: tile t reads A buffer t mod nabuf; chunk c into
+//               slot c & 1; commits per ring stage, per chunk and per tile
+//   warps 2-9   two builder groups of one warp per TMEM lane quadrant, group
+//               t & 1 for tile t: integerize the tile's elements and write
+//               their bytes into A buffer t mod nabuf once the MMAs of tile
+//               t - nabuf are done, so that two tiles are built at once
+//   warps 10-21 three per lane quadrant (sub-groups s = 0..2): the tile's
 //               32-column groups in turn (rotated per tile); a group is all
 //               one-limb, all two-limb pairs (L1 is even) or the one mixed
 //               group: reduce mod m_l (round-to-nearest quotient in fp32, the
@@ -705,8 +707,8 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 //               planes through incremental plane pointers.
 // Tile list entry: {problem, side, first line, first k}.
 // ---------------------------------------------------------------------------
-constexpr int kRmBuilders = 128;
-constexpr int kRmEpi = 512;
+constexpr int kRmBuilders = 256;                  // two groups of four warps
+constexpr int kRmEpi = 384;                       // three warps per lane quadrant
 constexpr int kRmThreads = 64 + kRmBuilders + kRmEpi;
 constexpr int kRmMaxStages = 16;
 
@@ -715,9 +717,9 @@ struct RmLayout {
   __host__ __device__ RmLayout(uint32_t stage_bytes, int stages, int lmax) {
     mc_off = (uint32_t)stages * stage_bytes;                 // {m, 1/m, m/2, 0} as floats [lmax]
     bar_off = mc_off + (uint32_t)lmax * 16;
-    // barriers: full, empty [kRmMaxStages], acc_full, acc_free, a_full, a_free [2], drain;
-    // then the abort flag and the TMEM slot
-    total = 1024 + bar_off + (2 * kRmMaxStages + 9) * 8 + 16;
+    // barriers: full, empty [kRmMaxStages], acc_full, acc_free [2], a_full, a_free [4],
+    // drain; then the abort flag and the TMEM slot
+    total = 1024 + bar_off + (2 * kRmMaxStages + 13) * 8 + 16;
     if (total < 116u * 1024u) total = 116u * 1024u;          // one CTA per SM: all 512 TMEM columns
   }
 };
@@ -766,11 +768,11 @@ __global__ void __launch_bounds__(kRmThreads, 1)
   uint64_t* empty = bars + kRmMaxStages;                      // [kRmMaxStages]
   uint64_t* acc_full = bars + 2 * kRmMaxStages;               // [2]
   uint64_t* acc_free = acc_full + 2;                          // [2] (kRmEpi arrivals)
-  uint64_t* a_full = acc_full + 4;                            // [2] (kRmBuilders arrivals)
-  uint64_t* a_free = acc_full + 6;                            // [2] MMAs of the buffer's tile done
-  uint64_t* drain = acc_full + 8;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_full + 9);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 9) + 1;
+  uint64_t* a_full = acc_full + 4;                            // [4] (one builder group's arrivals)
+  uint64_t* a_free = acc_full + 8;                            // [4] MMAs of the buffer's tile done
+  uint64_t* drain = acc_full + 12;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(acc_full + 13);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 13) + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   {
@@ -788,7 +790,9 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     for (int i = 0; i < 2; ++i) {
       mbar_init(acc_full + i, 1);
       mbar_init(acc_free + i, kRmEpi);
-      mbar_init(a_full + i, kRmBuilders);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(a_full + i, kRmBuilders / 2);
       mbar_init(a_free + i, 1);
     }
     mbar_init(drain, 1);
@@ -846,8 +850,9 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         const ProbDev& P = T.probs[tl.x];
         const int nkb = P.res_kpad / 64, cw = P.res_cw, nchunk = P.res_nchunk, npad = P.res_npad;
         const uint32_t acols = (uint32_t)P.res_kpad / 2;
-        const int ab = tcount & 1;
-        if (!mbar_wait(a_full + ab, (uint32_t)((tcount >> 1) & 1), abort_flag, T.status)) { ok = false; break; }
+        const int nabuf = P.res_nabuf;
+        const int ab = tcount % nabuf, ause = tcount / nabuf;
+        if (!mbar_wait(a_full + ab, (uint32_t)(ause & 1), abort_flag, T.status)) { ok = false; break; }
         tc_fence_after();
         const uint32_t abase = tmem + (uint32_t)ab * acols;
         for (int c = 0; ok && c < nchunk; ++c, ++ck) {
@@ -859,7 +864,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           tc_fence_after();
           const int ncol = min(cw, npad - c * cw);             // a multiple of 16
           const uint32_t idesc = idesc_bf16(128, ncol);
-          const uint32_t d = tmem + 2 * acols + (uint32_t)(s * cw);
+          const uint32_t d = tmem + (uint32_t)nabuf * acols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
             tc_fence_after();
@@ -881,24 +886,29 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         for (uint32_t t = 0; t < kSpinLimit && !mbar_try_wait(drain, 0u); ++t) {}
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 10) {
     // ------------------------------------------------------------ byte builders
     // Per element: S = sig 2^64 as 64-bit limbs S[j] (S[0] = 0, S[j] = limb
     // j - 1), |a_hat| = bits Bb.. of S plus the round-half-even increment.
     // Every limb read is unconditional at a clamped address (masked to zero
     // outside the significand), so the reads of a step are all in flight at
-    // once; the reads that fix the rounding run before the wait for the
-    // buffer.  The element's sign goes onto the bf16 bytes (-0 for a zero
-    // byte is harmless: the epilogue's + 0.0f turns a -0 result into +0).
+    // once: the exponents first, then one batch with the limbs of the first
+    // 32 columns and the two below them (the round bit and the first sticky
+    // limbs), before the wait for the buffer.  The element's sign goes onto the
+    // bf16 bytes (-0 for a zero byte is harmless: the epilogue's + 0.0f turns a
+    // -0 result into +0).  Group bg takes the tiles t with t & 1 == bg.
+    const int bg = (warp - 2) >> 2;
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
     bool ok = true;
     int tcount = 0;
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x, ++tcount) {
+      if ((tcount & 1) != bg) continue;
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
-      const int ab = tcount & 1;
+      const int nabuf = P.res_nabuf;
+      const int ab = tcount % nabuf, ause = tcount / nabuf;
       const int side = tl.y;
       const int R = side ? P.N : P.M;
       const int line = tl.z + (row >> 5), k = tl.w + (row & 31);
@@ -920,17 +930,22 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       int Bb = 64 - (ex - e_line + P.t - 64 * nl);  // bit of S that is bit 0 of |a_hat|
       const bool nz = valid && top != 0ull && Bb - 1 < 64 * nl + 64;
       Bb = nz ? Bb : 64;
-      // round bit (bit Bb - 1 of S), sticky bits below it, lowest kept bit
-      const int rbpos = Bb - 1, lr = rbpos >> 6;
-      const uint64_t srb = S(lr), slo = S(Bb >> 6);
-      const uint32_t rb = (uint32_t)(srb >> (rbpos & 63)) & 1u;
-      uint64_t sticky = srb & ((1ull << (rbpos & 63)) - 1ull);
-      for (int j = lr - 1; j >= 1 && !sticky; --j) sticky |= S(j);
-      uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(slo >> (Bb & 63)) & 1u))) : 0u;
       const int ws = Bb >> 5, bs = Bb & 31, lq = ws >> 1;
       const bool odd = ws & 1;
+      // limbs lq - 2 .. lq + 8: the round bit (bit Bb - 1, in limb lq or
+      // lq - 1), the first sticky limbs and the first 32 columns' window
+      uint64_t lm0[11];
+#pragma unroll
+      for (int q = 0; q < 11; ++q) lm0[q] = S(lq - 2 + q);
+      const int rbpos = Bb - 1;
+      const bool rb_hi = (rbpos >> 6) == lq;       // round bit in limb lq (else lq - 1)
+      const uint64_t srb = rb_hi ? lm0[2] : lm0[1];
+      const uint32_t rb = (uint32_t)(srb >> (rbpos & 63)) & 1u;
+      uint64_t sticky = (srb & ((1ull << (rbpos & 63)) - 1ull)) | (rb_hi ? lm0[1] : 0ull) | lm0[0];
+      for (int j = lq - 3; j >= 1 && !sticky; --j) sticky |= S(j);
+      uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(lm0[2] >> (Bb & 63)) & 1u))) : 0u;
       const uint32_t sgn = neg ? 0x80008000u : 0u;
-      if (tcount >= 2 && ok) ok = mbar_wait(a_free + ab, (uint32_t)(((tcount >> 1) - 1) & 1), abort_flag, T.status);
+      if (ause > 0 && ok) ok = mbar_wait(a_free + ab, (uint32_t)((ause - 1) & 1), abort_flag, T.status);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
@@ -938,9 +953,14 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       for (uint32_t c0 = 0; c0 < acols; c0 += 32) {  // 16 words = 64 bytes = 32 columns
         // 32-bit words ws + 16 it .. ws + 16 it + 16 of S come from limbs lq + 8 it .. + 8
         uint64_t lm[9];
-        const int j0 = lq + (int)(c0 >> 2);
+        if (c0 == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) lm[q] = S(j0 + q);
+          for (int q = 0; q < 9; ++q) lm[q] = lm0[2 + q];
+        } else {
+          const int j0 = lq + (int)(c0 >> 2);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) lm[q] = S(j0 + q);
+        }
         auto word = [&](int x) -> uint32_t {        // word x of the window (x + odd of the limbs)
           const uint32_t a = (x & 1) ? (uint32_t)(lm[x >> 1] >> 32) : (uint32_t)lm[x >> 1];
           const uint32_t b = (x & 1) ? (uint32_t)lm[(x + 1) >> 1] : (uint32_t)(lm[x >> 1] >> 32);
@@ -964,8 +984,8 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     if (!ok) *abort_flag = 1;
   } else {
     // ------------------------------------------------------------ epilogues
-    const int ew = warp - 6;
-    const int sub = ew >> 2;                          // column sub-group 0..3
+    const int ew = warp - 10;
+    const int sub = ew >> 2;                          // column sub-group 0..2
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
     const uint32_t tlane = tmem + ((uint32_t)(quad * 32) << 16);
@@ -980,7 +1000,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       const bool valid = line < R && k < P.K;
       const uint32_t acols = (uint32_t)P.res_kpad / 2;
       const int L1 = P.L1, ncols = P.L1 + 2 * (P.L - P.L1), cw = P.res_cw;
-      const int nchunk = P.res_nchunk, npad = P.res_npad;
+      const int nchunk = P.res_nchunk, npad = P.res_npad, nabuf = P.res_nabuf;
       uint16_t* planes = side ? P.pb : P.pa;
       const int64_t pstride = (int64_t)R * P.Kp;
       uint16_t* dst0 = planes + (int64_t)(valid ? line : 0) * P.Kp + (valid ? k : 0);
@@ -990,13 +1010,13 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t trow = tlane + 2 * acols + (uint32_t)(s * cw);
+        const uint32_t trow = tlane + (uint32_t)nabuf * acols + (uint32_t)(s * cw);
         const int j0 = c * cw;
         const int ncolp = min(cw, npad - j0);          // columns written by the MMAs
-        // the tile's 32-column groups go round the four sub-groups (rotated
+        // the tile's 32-column groups go round the three sub-groups (rotated
         // per tile), whatever the chunk width
-        const int gfirst = (sub - c * (cw >> 5) - tcount) & 3;
-        for (int g = 32 * gfirst; g < ncolp; g += 128) {
+        const int gfirst = ((sub - c * (cw >> 5) - tcount) % 3 + 3) % 3;
+        for (int g = 32 * gfirst; g < ncolp; g += 96) {
           uint32_t y[32];
           if (g + 32 <= ncolp) {
             tmem_ld32(trow + (uint32_t)g, y);
@@ -1080,16 +1100,26 @@ __global__ void __launch_bounds__(kRmThreads, 1)
   }
 }
 
-// Chunk width of the warp-specialised tensor-core residues: two byte buffers
-// (kpad / 2 columns each) and two accumulator slots of cw columns (a multiple
-// of 32) within the 512 TMEM columns.
-void residue_mm_geometry(int kpad, int npad, int* cw_out, int* tcols_out) {
-  int cw = (512 - kpad) / 2;
-  cw = cw > 256 ? 256 : cw;
-  cw &= ~31;
+// Chunk width of the warp-specialised tensor-core residues: nabuf byte
+// buffers (kpad / 2 columns each) and two accumulator slots of cw columns (a
+// multiple of 32) within the 512 TMEM columns; four buffers (two tiles built
+// at once, two in the MMAs) where that takes no more chunks than two.
+void residue_mm_geometry(int kpad, int npad, int* cw_out, int* nabuf_out) {
   const int need = (npad + 31) & ~31;
-  *cw_out = cw < need ? cw : need;
-  *tcols_out = 512;
+  auto width = [&](int nab) {
+    int cw = (512 - nab * (kpad / 2)) / 2;
+    cw = cw > 256 ? 256 : cw;
+    cw &= ~31;
+    return cw < need ? cw : need;
+  };
+  const int cw2 = width(2), cw4 = width(4);
+  if (cw4 >= 32 && (npad + cw4 - 1) / cw4 <= (npad + cw2 - 1) / cw2) {
+    *cw_out = cw4;
+    *nabuf_out = 4;
+  } else {
+    *cw_out = cw2;
+    *nabuf_out = 2;
+  }
 }
 
 int residue_mm_smem_bytes(int cw_max, int lmax, int /*tcols*/, int* stages) {
