@@ -1257,30 +1257,34 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
         const uint16_t* su = s_u + s * (kCmUMods * 128);
-        uint32_t pr[kCmUMods];
-        if (l0 + kCmUMods <= L) {                   // a full copy: no bounds
+        // pieces of 8 moduli in a rolled loop (small code), V columns
+        // l0 + 8 pc .. + 7 (zero beyond L)
+#pragma unroll 1
+        for (int pc = 0; pc < kCmUMods; pc += 8) {
+          const int lp = l0 + pc;
+          uint32_t pr[8];
+          if (lp + 8 <= L) {                          // a full piece: no bounds
+            const uint4 mua = *reinterpret_cast<const uint4*>(s_mu + lp);
+            const uint4 mub = *reinterpret_cast<const uint4*>(s_mu + lp + 4);
+            const uint32_t mu[8] = {mua.x, mua.y, mua.z, mua.w, mub.x, mub.y, mub.z, mub.w};
 #pragma unroll
-          for (int q4 = 0; q4 < kCmUMods / 4; ++q4) {
-            const uint4 mu4 = *reinterpret_cast<const uint4*>(s_mu + l0 + 4 * q4);
-            const uint32_t mu[4] = {mu4.x, mu4.y, mu4.z, mu4.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const uint32_t v = su[(4 * q4 + j) * 128 + row];
+            for (int j = 0; j < 8; ++j) {
+              const uint32_t v = su[(pc + j) * 128 + row];
               sig += (uint64_t)v * mu[j];
-              pr[4 * q4 + j] = bf16_halves7(v);
+              pr[j] = bf16_halves7(v);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int l = lp + j;
+              const uint32_t v = l < L ? (uint32_t)su[(pc + j) * 128 + row] : 0u;
+              sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
+              pr[j] = bf16_halves7(v);
             }
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < kCmUMods; ++q) {
-            const int l = l0 + q;
-            const uint32_t v = l < L ? (uint32_t)su[q * 128 + row] : 0u;
-            sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
-            pr[q] = bf16_halves7(v);
-          }
+          tmem_st8(vrow + (uint32_t)lp, pr);
         }
         mbar_arrive(u_free + s);
-        tmem_st32(vrow + (uint32_t)l0, pr);          // V columns l0 .. l0 + 31 (zero beyond L)
       }
       if (valid) sigbase[half * up + idx] = sig;
       tmem_wait_st();
@@ -1311,16 +1315,20 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int gfirst = (half - c * (cw >> 5) - ecount) & 3;
         for (int g = 32 * gfirst; g < cw; g += 128) {
           uint64_t acc[7] = {0, 0, 0, 0, 0, 0, 0};
-          if (g + 32 <= ncol) {
+          if (g < ncol) {
             uint32_t y[32];
-            tmem_ld32(trow + (uint32_t)g, y);
+            if (g + 32 <= ncol) {
+              tmem_ld32(trow + (uint32_t)g, y);
+            } else {                                  // 16 columns left: the rest are zero pieces
+              uint32_t y16[16];
+              tmem_ld16(trow + (uint32_t)g, y16);
+#pragma unroll
+              for (int q = 0; q < 16; ++q) y[q] = y16[q];
+#pragma unroll
+              for (int q = 16; q < 32; ++q) y[q] = 0u;
+            }
             if (small) crt_group_small<32>(y, acc);
             else crt_group<32>(y, acc);
-          } else if (g < ncol) {                      // 16 columns left
-            uint32_t y[16];
-            tmem_ld16(trow + (uint32_t)g, y);
-            if (small) crt_group_small<16>(y, acc);
-            else crt_group<16>(y, acc);
           }
           // group sum as 9 words: 7 word sums with carries, then the carry
           uint32_t* qcol = qbase + (int64_t)((c * cw + g) >> 5) * 9 * up + (valid ? idx : 0);
