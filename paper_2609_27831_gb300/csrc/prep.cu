@@ -216,18 +216,20 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
     sg[e] = ng[e] ? -1.f : 1.f;
     sb[e] = ng[e] ? 8388608.f : -8388608.f;
   }
-  // one plane of the EPT elements: one vector store when all are in range
-  auto put = [&](const uint32_t (&bits)[EPT]) {           // bf16 bits in the low halves
+  // one plane of the EPT elements: one vector store when all are in range;
+  // bits[e] holds the value's bf16 bits in its high half (an exact fp32), two
+  // of them packed by one byte permutation
+  auto put = [&](const uint32_t (&bits)[EPT]) {
     if (nk == EPT) {
       if (EPT == 4) {
-        st_plane4(dst, make_uint2(bits[0] | (bits[1] << 16), bits[2] | (bits[3] << 16)));
+        st_plane4(dst, make_uint2(__byte_perm(bits[0], bits[1], 0x7632), __byte_perm(bits[2], bits[3], 0x7632)));
       } else {
-        st_plane2(dst, bits[0] | (bits[1] << 16));
+        st_plane2(dst, __byte_perm(bits[0], bits[1], 0x7632));
       }
     } else {
 #pragma unroll
       for (int e = 0; e < EPT; ++e)
-        if (e < nk) st_plane(dst + e, bits[e]);
+        if (e < nk) st_plane(dst + e, bits[e] >> 16);
     }
     dst += plane_stride;
   };
@@ -266,15 +268,15 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
           for (int e = 0; e < EPT; ++e) {
             const float f = fmaf(sg[e], __uint_as_float(a[e] | 0x4B000000u), sb[e]);
             const float q = fmaf(f, rcp, 12582912.0f) - 12582912.0f;
-            bits[e] = __float_as_uint(fmaf(-q, mf, f)) >> 16;
+            bits[e] = __float_as_uint(fmaf(-q, mf, f));
           }
         } else {                                            // m = 128: ties need the correction
 #pragma unroll
-          for (int e = 0; e < EPT; ++e) bits[e] = __float_as_uint(centered_f32(a[e], ng[e], mf, rcp, hm)) >> 16;
+          for (int e = 0; e < EPT; ++e) bits[e] = __float_as_uint(centered_f32(a[e], ng[e], mf, rcp, hm));
         }
       } else {
 #pragma unroll
-        for (int e = 0; e < EPT; ++e) bits[e] = bf16_bits(centered(barrett32(a[e], mcv.x, mcv.y), mcv.x, ng[e]));
+        for (int e = 0; e < EPT; ++e) bits[e] = bf16_bits(centered(barrett32(a[e], mcv.x, mcv.y), mcv.x, ng[e])) << 16;
       }
       put(bits);                                            // plane l
     } else {
@@ -312,22 +314,29 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
         // centered residues; y = r_lo + 256 r_hi has |y| < 2^21, reduced
         // exactly the same way; then the split with a round-to-nearest
         // quotient by 128 (a tie leaves r0 = -64, moved to +64)
+        // Up to 24 words lo <= 24 4 255^2 and 256 |r_hi| <= 256 8095 keep
+        // y = s lo + 256 r_hi below 2^23 / (1 + 2^-29): lo needs no reduction
+        // of its own.
         const float mf = (float)mcv.x, rcp = __uint_as_float(mcv.z);
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
           const float fl = fmaf(sg[e], __uint_as_float(lo[e] | 0x4B000000u), sb[e]);
           const float fh = fmaf(sg[e], __uint_as_float(hi[e] | 0x4B000000u), sb[e]);
-          const float ql = fmaf(fl, rcp, 12582912.0f) - 12582912.0f;
           const float qh = fmaf(fh, rcp, 12582912.0f) - 12582912.0f;
-          const float y = fmaf(256.f, fmaf(-qh, mf, fh), fmaf(-ql, mf, fl));
+          float yl = fl;
+          if constexpr (NW > 24) {
+            const float ql = fmaf(fl, rcp, 12582912.0f) - 12582912.0f;
+            yl = fmaf(-ql, mf, fl);
+          }
+          const float y = fmaf(256.f, fmaf(-qh, mf, fh), yl);
           const float q = fmaf(y, rcp, 12582912.0f) - 12582912.0f;
           const float x = fmaf(-q, mf, y);
           float r1 = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
           float r0 = fmaf(-128.f, r1, x);
           if (r0 <= -64.f) { r0 += 128.f; r1 -= 1.f; }
-          b0[e] = __float_as_uint(r0) >> 16;
-          b1[e] = __float_as_uint(r1) >> 16;
-          b2[e] = __float_as_uint(r0 + r1) >> 16;
+          b0[e] = __float_as_uint(r0);
+          b1[e] = __float_as_uint(r1);
+          b2[e] = __float_as_uint(r0 + r1);
         }
       } else {
 #pragma unroll
@@ -336,9 +345,9 @@ __device__ __forceinline__ void residue_planes(const uint32_t (&w)[EPT][W32], co
           const int y = x & 127;
           const int r0 = y > 64 ? y - 128 : y;
           const int r1 = (x - r0) >> 7;
-          b0[e] = bf16_bits(r0);
-          b1[e] = bf16_bits(r1);
-          b2[e] = bf16_bits(r0 + r1);
+          b0[e] = bf16_bits(r0) << 16;
+          b1[e] = bf16_bits(r1) << 16;
+          b2[e] = bf16_bits(r0 + r1) << 16;
         }
       }
       put(b0);

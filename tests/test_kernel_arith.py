@@ -35,15 +35,17 @@ def test_fp32_rounded_quotient_is_exact_for_odd_one_limb_moduli():
 
 def test_fp32_rounded_quotient_is_exact_for_two_limb_moduli():
     """Two-limb moduli (odd primes in (255, 16191]): the kernel reduces the
-    low-byte sum (<= 4 * 32 * 255^2) and the high-byte sum separately with the
-    rounded quotient, then y = r_lo + 256 r_hi (|y| < 2^21) the same way.
-    Exhaustive over the low-byte range for the smallest, the largest and a
-    spread of the moduli in between."""
+    high-byte sum with the rounded quotient, then y = s lo + 256 r_hi the same
+    way; up to 24 words |y| <= 24 * 4 * 255^2 + 256 * 8095 < 2^23 / (1 + 2^-29)
+    (beyond, up to 32 words, the low-byte sum is reduced first and |y| < 2^21).
+    Exhaustive over |y| <= 4 * 32 * 255^2 (which covers both) for the smallest,
+    the largest and a spread of the moduli in between."""
     mods = [m for m in o.Params(1024, 2048).moduli if m > 255]
     assert all(m % 2 == 1 for m in mods)
     pick = sorted(set([mods[0], mods[-1]] + mods[:: max(1, len(mods) // 10)]))
     amax = 4 * 32 * 255 * 255
     assert amax * (1 + 2.0 ** -29) < 2 ** 23
+    assert 24 * 4 * 255 * 255 + 256 * 8095 <= amax
     a = np.arange(amax + 1, dtype=np.int64)
     af = a.astype(np.float64)
     for m in pick:
