@@ -84,44 +84,6 @@ __device__ __forceinline__ uint32_t sig_word(const uint32_t* __restrict__ limbs3
   return __ldg(limbs32 + 2 * ((int64_t)(j >> 1) * ps + off) + (j & 1));
 }
 
-// Digits of |a_hat| = floor(sig 2^sh) + rnd for one element, 16 bits each
-// (the round-half-even increment rnd is added with a carry through the
-// digits).  Returns false for a zero element.
-template <int W16>
-__device__ __forceinline__ bool element_digits(const uint32_t* __restrict__ limbs32, int64_t ps,
-                                               int64_t off, int nl, int exp_el, int e_line, int t,
-                                               uint32_t (&dig)[W16]) {
-#pragma unroll
-  for (int d = 0; d < W16; ++d) dig[d] = 0u;
-  const int sh = exp_el - e_line + t - 64 * nl;   // <= t - 64 nl
-  // E = sig * 2^64 (two zero words below); bit 0 of floor(sig 2^sh) is bit B of E, B >= 31
-  const int B = 64 - sh;
-  if (B - 1 >= 64 * nl + 64) return true;       // |a| 2^(t - e) < 1/2: rounds to 0
-  const int ws = B >> 5, bs = B & 31;
-#pragma unroll
-  for (int w = 0; w < W16 / 2; ++w) {
-    const uint32_t lo = sig_word(limbs32, ps, off, nl, ws + w - 2);
-    const uint32_t hi = sig_word(limbs32, ps, off, nl, ws + w - 1);
-    const uint32_t x = __funnelshift_r(lo, hi, bs);
-    dig[2 * w] = x & 0xffffu;
-    dig[2 * w + 1] = x >> 16;
-  }
-  // round-half-even: round bit = bit B-1 of E, sticky = the bits below it
-  const int rbpos = B - 1;
-  const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
-  const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
-  uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
-  for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
-  uint32_t c = rb & ((sticky != 0u) | (dig[0] & 1u));
-#pragma unroll
-  for (int d = 0; d < W16; ++d) {                // |a_hat| <= 2^t fits the W16 digits
-    const uint32_t x = dig[d] + c;
-    dig[d] = x & 0xffffu;
-    c = x >> 16;
-  }
-  return true;
-}
-
 // Plane stores of the CUDA-core residues as global-space stores: the compiler
 // then knows they cannot alias the shared-memory tables, and may read the next
 // modulus's table row ahead of them (about 1 % at 1024^3, p = 256).
@@ -152,23 +114,40 @@ __device__ __forceinline__ int centered(uint32_t r, uint32_t m, bool neg) {
 // the round-half-even increment carried through the words).  A zero element
 // gives zero words.
 template <int W32>
-__device__ __forceinline__ void element_words(const uint32_t* __restrict__ limbs32, int64_t ps, int64_t off,
+__device__ __forceinline__ void element_words(const uint64_t* __restrict__ limbs, int64_t ps, int64_t off,
                                               int nl, int exp_el, int e_line, int t, uint32_t (&wd)[W32]) {
 #pragma unroll
   for (int w = 0; w < W32; ++w) wd[w] = 0u;
   const int sh = exp_el - e_line + t - 64 * nl;   // <= t - 64 nl
-  const int B = 64 - sh;                          // bit of sig * 2^64 that is bit 0 of the magnitude
+  const int B = 64 - sh;                          // bit of S = sig 2^64 that is bit 0 of the magnitude
   if (B - 1 >= 64 * nl + 64) return;              // |a| 2^(t - e) < 1/2: rounds to 0
-  const int ws = B >> 5, bs = B & 31;
+  // 64-bit limbs S[j] (S[0] = 0, S[j] = limb j - 1; 0 outside, with no
+  // read), all in flight at once: lq - 2 .. lq + W32/2 cover the round bit
+  // (limb lq or lq - 1), the first sticky limbs and the words ws .. ws + W32
+  // of the magnitude
+  auto S = [&](int j) -> uint64_t {
+    return (unsigned)(j - 1) < (unsigned)nl ? __ldg(limbs + (int64_t)(j - 1) * ps + off) : 0ull;
+  };
+  const int ws = B >> 5, bs = B & 31, lq = ws >> 1;
+  const bool odd = ws & 1;
+  constexpr int NLM = W32 / 2 + 3;
+  uint64_t lm[NLM];
 #pragma unroll
-  for (int w = 0; w < W32; ++w)
-    wd[w] = __funnelshift_r(sig_word(limbs32, ps, off, nl, ws + w - 2), sig_word(limbs32, ps, off, nl, ws + w - 1), bs);
+  for (int q = 0; q < NLM; ++q) lm[q] = S(lq - 2 + q);
+  auto word = [&](int x) -> uint32_t {            // word ws + x of S
+    const uint32_t a = (x & 1) ? (uint32_t)(lm[2 + (x >> 1)] >> 32) : (uint32_t)lm[2 + (x >> 1)];
+    const uint32_t b = (x & 1) ? (uint32_t)lm[2 + ((x + 1) >> 1)] : (uint32_t)(lm[2 + (x >> 1)] >> 32);
+    return odd ? b : a;
+  };
+#pragma unroll
+  for (int w = 0; w < W32; ++w) wd[w] = __funnelshift_r(word(w), word(w + 1), bs);
   const int rbpos = B - 1;
-  const uint32_t rw = sig_word(limbs32, ps, off, nl, (rbpos >> 5) - 2);
-  const uint32_t rb = (rw >> (rbpos & 31)) & 1u;
-  uint32_t sticky = rw & ((1u << (rbpos & 31)) - 1u);
-  for (int j = (rbpos >> 5) - 3; j >= 0 && !sticky; --j) sticky |= sig_word(limbs32, ps, off, nl, j);
-  uint32_t c = rb & ((sticky != 0u) | (wd[0] & 1u));
+  const bool rb_hi = (rbpos >> 6) == lq;          // round bit in limb lq (else lq - 1)
+  const uint64_t srb = rb_hi ? lm[2] : lm[1];
+  const uint32_t rb = (uint32_t)(srb >> (rbpos & 63)) & 1u;
+  uint64_t sticky = (srb & ((1ull << (rbpos & 63)) - 1ull)) | (rb_hi ? lm[1] : 0ull) | lm[0];
+  for (int j = lq - 3; j >= 1 && !sticky; --j) sticky |= S(j);
+  uint32_t c = rb & ((sticky != 0ull) | (wd[0] & 1u));
 #pragma unroll
   for (int w = 0; w < W32; ++w) {                 // |a_hat| <= 2^t fits the W32 words
     const uint32_t x = wd[w] + c;
@@ -399,7 +378,6 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
   const int32_t* exps = side ? P.b_exp : P.a_exp;
   const int8_t* signs = side ? P.b_sign : P.a_sign;
   const int nl = P.nl;
-  const uint32_t* limbs32 = reinterpret_cast<const uint32_t*>(limbs);
   const int e_line = side ? P.f[r] : P.e[r];
 
   uint32_t w[EPT][W32];
@@ -409,7 +387,7 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
     const int64_t off = off0 + e * stride_k;
     ng[e] = false;
     if (e < nk && __ldg(limbs + (int64_t)(nl - 1) * ps + off) != 0ull) {
-      element_words<W32>(limbs32, ps, off, nl, __ldg(exps + off), e_line, P.t, w[e]);
+      element_words<W32>(limbs, ps, off, nl, __ldg(exps + off), e_line, P.t, w[e]);
       ng[e] = __ldg(signs + off) != 0;
     } else {
 #pragma unroll
