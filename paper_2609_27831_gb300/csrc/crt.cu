@@ -424,9 +424,9 @@ __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], 
 
 // ---------------------------------------------------------------------------
 // One lane per output element (CRT accumulators of up to 40 digits).  The
-// warps of a block cooperate on the staging: the reduced products of 128
-// consecutive outputs are read coalesced and turned into v_l, and the digit
-// table M_l and the quotient constants are staged in shared memory, where
+// warps of a block cooperate on the staging: the values v_l of 128
+// consecutive outputs (as the plane GEMM stored them) are read coalesced, and
+// the digit table M_l and the quotient constants are staged in shared memory, where
 // every lane of a warp reads the same word (broadcast).  Each lane then runs
 // the whole CRT and rounding of its output with the digits in registers and
 // sequential exact carries.
@@ -550,8 +550,8 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
 // accumulator are exact.
 //
 // One CTA per tile of 128 consecutive outputs, 8 warps, sized for two CTAs
-// per SM.  Thread 0 loads the piece table B and the tile's reduced products
-// u with TMA; all threads build V (two threads per output, half of the moduli
+// per SM.  Thread 0 loads the piece table B and the tile's values v_l with
+// TMA; all threads build V (two threads per output, half of the moduli
 // each) together with the quotient estimate; thread 0 issues the MMAs; the
 // epilogue splits the columns of Y between the two warps of each TMEM lane
 // quadrant, carries sum_j 128^j Y_j into 32-bit digits, merges the halves and

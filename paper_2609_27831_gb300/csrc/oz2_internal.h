@@ -50,7 +50,7 @@ struct ProbDev {
   int32_t* f;            // [N] column exponents of B
   uint16_t* pa;          // bf16 bits [G][M][Kp]
   uint16_t* pb;          // bf16 bits [G][N][Kp]
-  uint16_t* u;           // [L][M][N]
+  uint16_t* u;           // [L][upitch]: v_l = u_l M_l^{-1} mod m_l per output (the plane GEMM's result)
   // shape and parameters
   int32_t M, N, K, p, nl, t;
   int32_t L, L1, G, Kp;
@@ -166,7 +166,7 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
                           cudaStream_t s);
 int crt_mm_chunk(int kpad, int npad, int* nslot);
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
-// the finish of one-lane classes (0..8: <= 40 digits) after the tensor-core sums
+// the finish of one-lane classes after the tensor-core sums (the host uses it up to 24 digits)
 cudaError_t launch_crt_fin_short(const DevTables& t, int cls, const int32_t* blk, int nblk, cudaStream_t s);
 cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
                                    cudaStream_t s);
