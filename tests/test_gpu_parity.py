@@ -280,14 +280,18 @@ def test_crt_sum_engine_one_chunk_many_tiles(ozk):
         assert np.array_equal(g2["C"][key], g0["C"][key])
 
 
-def test_crt_sum_engine_batched(ozk):
+@pytest.mark.parametrize("res_engine", [0, 2])
+def test_crt_sum_engine_batched(ozk, res_engine):
     """A batch whose problems have different modulus counts and digit lengths
-    (tables switch between tiles of one CTA) through the tensor-core sums."""
+    through the tensor-core sums: four TMEM layouts of the CRT sums (one
+    launch each; tables switch between tiles of one CTA within a layout), and
+    with res_engine 2 four layouts of the tensor-core residues as well (two and
+    four byte buffers)."""
     rng = np.random.Generator(np.random.PCG64(2046))
     shapes = [(70, 40, 30, 256), (33, 60, 17, 1024), (40, 30, 50, 512), (5, 5, 5, 53)]
     mats = [(synth.mp_matrix(rng, M, K, p, -8, 8), synth.mp_matrix(rng, K, N, p, -8, 8))
             for (M, N, K, p) in shapes]
-    plan = ozk.Plan(shapes, crt_engine=2)
+    plan = ozk.Plan(shapes, crt_engine=2, res_engine=res_engine)
     ws = plan.workspace()
     trip = [(ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), ozk.MPMatrix.empty(M, N, p))
             for (M, N, K, p), (A, B) in zip(shapes, mats)]
