@@ -212,8 +212,8 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
       Y = V B, 2 M N (2L) np flops with np 7-bit pieces of P, against the
       bf16 tensor peak.
     crt_finish (after the sums): the bytes it moves, the group words it reads
-      (D + 2 ceil(D/7) per output), the four 8-byte partial quotient sums and
-      the output (8 nl + 5 bytes), against HBM.
+      (D + 2 ceil(D/7) per output), the 4-byte quotient estimate and the
+      output (8 nl + 5 bytes), against HBM.
     scan: the bytes of the two exponent vectors' inputs, against HBM.
     """
     peaks, src = load_peaks()
@@ -249,7 +249,7 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
                            "traffic": traffic.get("crt_sums")}
         D = info["crt_digits"]
         nl = -(-p // 64)
-        fb = M * N * (4 * (D + 2 * -(-D // 7)) + 32 + 8 * nl + 5)
+        fb = M * N * (4 * (D + 2 * -(-D // 7)) + 4 + 8 * nl + 5)
         ach = fb / (stages["crt_finish"] / 1e3) / 1e9
         pk = float(peaks["hbm_gbs"])
         out["crt_finish"] = {"kernel": "k_crt_fin_long (CRT finish from the group sums + rounding)",

@@ -162,7 +162,7 @@ struct ProbHost {
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
                                // 2: tensor-core sums to R digits, then the finish
   int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot, crt_nvbuf;
-  size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient sums [4][upitch] u64
+  size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient estimates [upitch] uint32
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_nabuf;           // res_mode 2: chunk width, chunks, byte buffers
 };
@@ -346,6 +346,10 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     const int np = (big_bitlen(c.P) + 6) / 7 + 1;
     const int kpad = (int)align_up((size_t)2 * L, 64);
     const int npad = (int)align_up((size_t)np, 16);
+    // the tensor-core sums carry five more columns at the end of their last
+    // 32-column group: the 7-bit pieces of floor(2^28 / m_l), whose column
+    // sums give the quotient estimate
+    const int npad_mm = (int)align_up((size_t)np + 5, 32);
     const bool tc_ok = o.crt_engine == 1 && h.crt_cls <= 8 && kpad <= 256 && npad <= 256 &&
                        crt_tc_smem_bytes(h.crt_cls, kpad, npad, L, 1) <= 227 * 1024;
     // automatic choice: the tensor-core sums above 20 accumulator digits
@@ -360,18 +364,20 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
                        kpad / 2 + 2 * 32 <= 512;
     h.crt_mode = tc_ok ? 1 : (mm_ok ? 2 : 0);
     h.crt_kpad = kpad;
-    h.crt_npad = npad;
+    h.crt_npad = h.crt_mode == 2 ? npad_mm : npad;
     h.crt_np = np;
     h.crt_nslot = 2;
-    h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad, &h.crt_nslot) : 0;
-    h.crt_nchunk = mm_ok ? (npad + h.crt_cw - 1) / h.crt_cw : 0;
+    h.crt_cw = mm_ok ? crt_mm_chunk(kpad, npad_mm, &h.crt_nslot) : 0;
+    h.crt_nchunk = mm_ok ? (npad_mm + h.crt_cw - 1) / h.crt_cw : 0;
     // a second V buffer where it fits beside the accumulator slots: the
     // next tile's V is built while this tile's chunks are read out
     h.crt_nvbuf = (mm_ok && kpad + h.crt_nslot * h.crt_cw <= 512) ? 2 : 1;
     h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
     const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
+    if (h.crt_mode != 0 && !c.tc_table.empty() && (c.rows != rows || c.npad != h.crt_npad))
+      return OZ2_EINTERNAL;                      // one table per modulus set and CRT engine
     if (h.crt_mode != 0 && c.tc_table.empty()) {
-      c.kpad = kpad; c.npad = npad; c.np = np; c.rows = rows;
+      c.kpad = kpad; c.npad = h.crt_npad; c.np = np; c.rows = rows;
       c.tc_table.assign((size_t)rows * kpad, 0);
       const auto& mlist = modulus_list();
       auto bf = [](uint32_t x) -> uint16_t {   // exact for x <= 256
@@ -393,6 +399,18 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
         for (int j = 0; j < np; ++j) {
           c.tc_table[(size_t)j * kpad + 2 * l] = bf(piece[j]);
           c.tc_table[(size_t)j * kpad + 2 * l + 1] = j ? bf(piece[j - 1]) : 0;
+        }
+        if (h.crt_mode == 2) {
+          // columns npad_mm - 5 .. npad_mm - 1: F_l = floor(2^28 / m_l) < 2^24
+          // in four 7-bit pieces, so that sum_k 128^k Y_k = sum_l v_l F_l
+          const uint32_t F = (uint32_t)((1u << 28) / mlist[l]);
+          const int ca = npad_mm - 5;
+          for (int k = 0; k < 5; ++k) {
+            const uint32_t f0 = k < 4 ? (F >> (7 * k)) & 127u : 0u;
+            const uint32_t f1 = k >= 1 ? (F >> (7 * (k - 1))) & 127u : 0u;
+            c.tc_table[(size_t)(ca + k) * kpad + 2 * l] = bf(f0);
+            c.tc_table[(size_t)(ca + k) * kpad + 2 * l + 1] = bf(f1);
+          }
         }
       }
     }
@@ -481,7 +499,7 @@ static void layout_workspace(ozaki2_plan_s* pl) {
       const size_t up = align_up((size_t)(h.M * h.N), 8);
       off += align_up(4 * (size_t)h.crt_ngrp * 9 * up, 256);
       h.off_sig = off;
-      off += align_up(32 * up, 256);              // four partial quotient sums
+      off += align_up(4 * up, 256);               // quotient estimates
     }
   }
   pl->ws_bytes = off;
@@ -998,7 +1016,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_nchunk = h.crt_nchunk;
     P.crt_cw = h.crt_cw;
     P.crt_q = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_q) : nullptr;
-    P.crt_sig = h.crt_mode == 2 ? reinterpret_cast<uint64_t*>(ws + h.off_sig) : nullptr;
+    P.crt_alpha = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_sig) : nullptr;
     P.crt_ngrp = h.crt_ngrp;
     P.crt_nslot = h.crt_nslot;
     P.crt_nvbuf = h.crt_nvbuf;

@@ -804,7 +804,6 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
 // Block list entry: {problem, block of 128 outputs, 0, 0}.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 128;
-constexpr int kCmQuarters = 4;         // worker groups of the tensor-core CRT sums (partial quotient sums)
 
 // asynchronous 4-byte copy global -> shared (completes at cp.async.wait_group)
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
@@ -847,10 +846,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     cp_async4(s_W + (2 * g + 1) * kFinThreads + e, qcol + ((int64_t)g * 9 + 8) * up);
   }
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-  uint64_t sig = 0;
-#pragma unroll
-  for (int h = 0; h < kCmQuarters; ++h) sig += P.crt_sig[h * up + idx];
-  const uint64_t alpha = sig >> 32;
+  const uint64_t alpha = P.crt_alpha[idx];
   // pass 1, least significant digit first: R = (S + alpha~ (2^(32 D) - P)) mod
   // 2^(32 D), and the carries out of R + (2^(32 D) - P) (R >= P), of
   // R + (2^(32 D) - floor(P/2) - 1) and of (R - P) + the same (the sign of the
@@ -902,14 +898,14 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 }
 
 // The finish of short accumulators (D <= ND digits, used up to 24) after the
-// tensor-core CRT sums, R in registers: every group word and the four partial
-// quotient sums are loaded at once (coalesced across the block), then
+// tensor-core CRT sums, R in registers: every group word and the quotient
+// estimate are loaded at once (coalesced across the block), then
 // R = (sum_g Q_g 2^(224 g) + alpha~ (2^(32 D) - P)) mod 2^(32 D), then the same
 // unrolled steps as k_crt1 (crt_finish).  Group g holds 9 words starting at
 // word 7 g, so word d collects word d - 7 g of group g = d / 7 and, for
 // d mod 7 < 2, word d - 7 (g - 1) of the group before.
 template <int ND>
-__global__ void __launch_bounds__(kFinThreads) k_crt_fin_short(DevTables T, const int4* __restrict__ blk) {
+__global__ void __launch_bounds__(kFinThreads, (ND <= 24 ? 6 : 1)) k_crt_fin_short(DevTables T, const int4* __restrict__ blk) {
   __shared__ uint32_t s_tab[3 * ND];              // 2^(32 D) - P, 2^(32 D) - floor(P/2) - 1, P
   __shared__ uint32_t s_mag[ND * kFinThreads];    // rounding scratch
   const int4 b = blk[blockIdx.x];
@@ -926,7 +922,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_short(DevTables T, cons
   const bool valid = idx < (int64_t)P.M * P.N;
   const int64_t up = P.upitch;
   const uint32_t* const qcol = P.crt_q + (valid ? idx : 0);
-  const uint64_t* const scol = P.crt_sig + (valid ? idx : 0);
+
   uint32_t w0[ND], w1[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {                   // independent loads first
@@ -934,13 +930,10 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_short(DevTables T, cons
     w0[d] = (d < D && g < ng) ? __ldg(qcol + ((int64_t)g * 9 + k) * up) : 0u;
     w1[d] = (d < D && k < 2 && g >= 1 && g - 1 < ng) ? __ldg(qcol + ((int64_t)(g - 1) * 9 + k + 7) * up) : 0u;
   }
-  uint64_t sig = 0;
-#pragma unroll
-  for (int h = 0; h < kCmQuarters; ++h) sig += __ldg(scol + h * up);
+  const uint64_t alpha = __ldg(P.crt_alpha + (valid ? idx : 0));
   const int ef = valid ? crt_ef(P, idx) : 0;
   __syncthreads();
   if (!valid) return;
-  const uint64_t alpha = sig >> 32;
   uint32_t R[ND];
   uint64_t carry = 0;
 #pragma unroll
@@ -976,10 +969,12 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_short(DevTables T, cons
 //   warp 2      TMA producer of the tile's v values, 32 moduli x 128 outputs
 //               per copy, into a four-slot ring
 //   warps 3-18  four threads per output (its TMEM lane), groups h = 0..3:
-//               group h writes the V columns of the copies c = h mod 4 (one
-//               tcgen05.st of 32 columns each) and its part of the quotient
-//               sum sum_l v_l floor(2^32 / m_l); then, for every chunk, the
-//               32-column groups g = h mod 4.
+//               group h writes the V columns of the copies c = h mod 4 (in
+//               pieces of 8 columns); then the tile's 32-column groups in
+//               turn.  The last group's columns 27..31 are the sums of the
+//               pieces of floor(2^28 / m_l): the quotient estimate
+//               alpha~ = floor(sum_l v_l floor(2^28 / m_l) / 2^28), in
+//               {alpha - 1, alpha}, written per output for the finish.
 // A warp rewrites its V columns only after the commit that follows the
 // previous tile's last MMA, and the next tile's MMAs wait for every warp's V
 // columns (tcgen05.st waited and fenced), so V is never read and written at
@@ -1063,7 +1058,6 @@ __global__ void __launch_bounds__(kCmThreads, 1)
   uint8_t* sm = smem_raw + (base - raw);
   const CmLayout lay(stage_bytes, stages, T.lmax);
   const uint32_t sRing = base + lay.ring_off;                 // B ring [stages][cw cols][128 B]
-  uint32_t* s_mu = reinterpret_cast<uint32_t*>(sm + lay.mu_off);
   const uint32_t sU = base + lay.u_off;                       // v ring [kCmUSlots][32][128] uint16
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);
   uint64_t* full = bars;                                      // [kCmMaxStages]
@@ -1098,7 +1092,6 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int l = threadIdx.x; l < T.lmax; l += kCmThreads) s_mu[l] = __ldg(&T.mods[l].mu);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                  : "memory");
@@ -1237,10 +1230,6 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       // clobbers would reload them from global memory after every barrier)
       const int L = P.L, nvbuf = P.crt_nvbuf;
       const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
-      const int64_t idx = (int64_t)tl.y * 128 + row;
-      const bool valid = idx < (int64_t)P.M * P.N;
-      const int64_t up = P.upitch;
-      uint64_t* const sigbase = P.crt_sig;
       const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
       vnext = nvbuf == 2 ? vnext ^ 1 : 0;
       // the buffer may be rewritten once every MMA of its previous tile is done
@@ -1249,7 +1238,6 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       if (!ok) return;
       tc_fence_after();
       const uint32_t vrow = tlane + (uint32_t)vb * vcols;
-      uint64_t sig = 0;
       for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
         if ((uc & 3) != half) continue;             // another group's copy
         const int s = uc % kCmUSlots, use = uc / kCmUSlots;
@@ -1264,29 +1252,19 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           const int lp = l0 + pc;
           uint32_t pr[8];
           if (lp + 8 <= L) {                          // a full piece: no bounds
-            const uint4 mua = *reinterpret_cast<const uint4*>(s_mu + lp);
-            const uint4 mub = *reinterpret_cast<const uint4*>(s_mu + lp + 4);
-            const uint32_t mu[8] = {mua.x, mua.y, mua.z, mua.w, mub.x, mub.y, mub.z, mub.w};
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const uint32_t v = su[(pc + j) * 128 + row];
-              sig += (uint64_t)v * mu[j];
-              pr[j] = bf16_halves7(v);
-            }
+            for (int j = 0; j < 8; ++j) pr[j] = bf16_halves7(su[(pc + j) * 128 + row]);
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int l = lp + j;
-              const uint32_t v = l < L ? (uint32_t)su[(pc + j) * 128 + row] : 0u;
-              sig += (uint64_t)v * (l < L ? s_mu[l] : 0u);
-              pr[j] = bf16_halves7(v);
+              pr[j] = bf16_halves7(l < L ? (uint32_t)su[(pc + j) * 128 + row] : 0u);
             }
           }
           tmem_st8(vrow + (uint32_t)lp, pr);
         }
         mbar_arrive(u_free + s);
       }
-      if (valid) sigbase[half * up + idx] = sig;
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(v_full + vb);
@@ -1326,6 +1304,17 @@ __global__ void __launch_bounds__(kCmThreads, 1)
               for (int q = 0; q < 16; ++q) y[q] = y16[q];
 #pragma unroll
               for (int q = 16; q < 32; ++q) y[q] = 0u;
+            }
+            if (c * cw + g + 32 == npad) {
+              // the last group's columns 27..31 hold sum_k 128^k Y = sum_l v_l
+              // floor(2^28 / m_l): alpha~ = floor of it / 2^28, in {alpha - 1,
+              // alpha} (its error is below L 2^14 / 2^28); then they are cleared
+              uint64_t a = 0;
+#pragma unroll
+              for (int k = 4; k >= 0; --k) a = (a << 7) + f2u_exact24(y[27 + k]);
+              if (valid) P.crt_alpha[idx] = (uint32_t)(a >> 28);
+#pragma unroll
+              for (int k = 27; k < 32; ++k) y[k] = 0u;
             }
             if (small) crt_group_small<32>(y, acc);
             else crt_group<32>(y, acc);

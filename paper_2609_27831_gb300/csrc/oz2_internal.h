@@ -83,7 +83,7 @@ struct ProbDev {
   int32_t crt_nchunk;    // crt_mode 2: chunks of crt_cw columns of Y
   int32_t crt_cw;        // crt_mode 2: columns of Y per chunk (a multiple of 32)
   uint32_t* crt_q;       // crt_mode 2: group sums Q_g as [ngrp][9][upitch] words
-  uint64_t* crt_sig;     // crt_mode 2: four partial quotient sums [4][upitch]
+  uint32_t* crt_alpha;   // crt_mode 2: quotient estimates alpha~ [upitch]
   int32_t crt_ngrp;      // crt_mode 2: groups of 32 columns, nchunk cw / 32
   int32_t res_cw;        // res_mode 2: columns of Y per chunk (a multiple of 32)
   int32_t res_nchunk;    // res_mode 2: chunks

@@ -34,7 +34,7 @@ def test_tensor_core_crt_stages():
     s, f = out["crt_sums"], out["crt_finish"]
     assert s["bound"] == "tensor" and f["bound"] == "hbm"
     assert s["achieved"] == pytest.approx(2.0 * M * N * 140 * 83 / 0.15e-3 / 1e12, abs=0.05)
-    # group words D + 2 ceil(D/7), four 8-byte partial sums, 4 limbs + exponent + sign out
-    per = 4 * (21 + 2 * 3) + 32 + 8 * 4 + 5
+    # group words D + 2 ceil(D/7), the 4-byte quotient estimate, 4 limbs + exponent + sign out
+    per = 4 * (21 + 2 * 3) + 4 + 8 * 4 + 5
     assert f["achieved"] == pytest.approx(M * N * per / 0.09e-3 / 1e9, abs=0.05)
     assert 0 < f["frac"] < 1.5 and 0 < s["frac"] < 1.5

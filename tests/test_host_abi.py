@@ -116,9 +116,10 @@ def test_null_pointer_errors(ozk):
 @pytest.mark.parametrize("p, cw_want", [(1024, 160), (2048, 160)])
 def test_crt_sum_engine_workspace(ozk, p, cw_want):
     """crt_engine 2 adds the group sums ([groups of 32 columns][9][M N rounded
-    to 8] uint32) and the four partial quotient sums ([4][M N rounded to 8]
-    uint64) to the workspace where it applies, and nothing where it does not.
-    The chunk width: two TMEM slots beside V (kpad / 2 of 512 columns) unless
+    to 8] uint32) and the quotient estimates ([M N rounded to 8] uint32) to
+    the workspace where it applies, and nothing where it does not.  The table
+    has np 7-bit pieces of P and five quotient columns, padded to groups of 32;
+    the chunk width: two TMEM slots beside V (kpad / 2 of 512 columns) unless
     that makes them narrower than 128 columns, then one slot."""
     shape = (256, 256, 64, p)
     base = ozk.Plan(shape, crt_engine=3).info
@@ -128,8 +129,9 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
         P *= m
     L = plan.info["L"]
     kpad = -(-2 * L // 64) * 64
-    npad = -(-(-(-P.bit_length() // 7) + 1) // 16) * 16
-    need = -(-npad // 32) * 32
+    np_ = -(-P.bit_length() // 7) + 1
+    npad = -(-(np_ + 5) // 32) * 32
+    need = npad
     cw = min(256, ((512 - kpad // 2) // 2) // 32 * 32)
     if cw < 128 and cw < need:
         cw = min(256, (512 - kpad // 2) // 32 * 32)
@@ -137,7 +139,7 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
     assert cw == cw_want
     ngrp, up = -(-npad // cw) * cw // 32, 256 * 256
     a256 = lambda x: -(-x // 256) * 256
-    assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(32 * up)
+    assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(4 * up)
     small = (4, 4, 4, 53)                        # M N < 128: the CUDA-core CRT
     assert ozk.Plan(small, crt_engine=2).info["workspace_bytes"] == ozk.Plan(small, crt_engine=3).info["workspace_bytes"]
 
