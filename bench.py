@@ -190,8 +190,8 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # one ncu capture of the committed kernels on the same workload; the source
 # summaries are under profiles/.  A kernel changed since its capture has None.
 NCU_TRAFFIC = {
-    "gemm_1024_p256": {"residues": 443.90144e6, "gemm": 564.279552e6, "crt_sums": 248.991744e6,
-                       "crt_finish": 157.4016e6},
+    "gemm_1024_p256": {"residues": 443.90144e6, "gemm": 564.279552e6, "crt_sums": 223.868672e6,
+                       "crt_finish": 123.980288e6},
 }
 
 
