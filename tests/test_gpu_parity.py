@@ -369,6 +369,7 @@ def test_gemm_1024_p256_sampled(ozk):
         t = o.to_fraction(*o.truth_entry(A, B, i, j, 256))
         worst = max(worst, o.ulp_distance(o.to_fraction(r["limbs"], r["exp"], r["sign"]), t, 256))
     assert worst <= 1
+    print(f"max ulp 1024x1024x1024 p=256: {float(worst):.4f} over {len(pairs)} sampled entries")
     # the integer planes of a 256 x 256 corner, in full
     par = o.Params(1024, 256)
     for i in (0, 100, 1023):
