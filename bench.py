@@ -215,6 +215,14 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
       (D + 2 ceil(D/7) per output), the 4-byte quotient estimate and the
       output (8 nl + 5 bytes), against HBM.
     scan: the bytes of the two exponent vectors' inputs, against HBM.
+
+    Every stage also carries ``hbm``: its algorithmic bytes (what it must read
+    and write once) over its time, against the measured HBM copy rate, whatever
+    its own bound: residues read the inputs (8 nl + 5 bytes per entry) and
+    write the G bf16 planes; the GEMM reads both plane stacks and writes the L
+    16-bit values v_l; the CRT reads v_l and writes C (8 nl + 5 bytes per
+    output), the tensor-core sums writing the 9-word group sums and the 4-byte
+    estimate in between.
     """
     peaks, src = load_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
@@ -268,6 +276,26 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
     out["scan"] = {"kernel": "k_scan (shared exponents)", "bound": "hbm", "achieved": round(ach, 1),
                    "peak": pk, "unit": "GB/s", "frac": round(ach / pk, 4),
                    "peak_source": f"hbm_gbs, {src}", "traffic": traffic.get("scan")}
+    nl = -(-p // 64)
+    Kp = -(-K // 8) * 8
+    io_in = (M * K + K * N) * (8 * nl + 5)
+    c_out = M * N * (8 * nl + 5)
+    v_bytes = L * M * N * 2
+    nbytes = {"scan": (M * K + K * N) * (8 + 4),
+              "residues": io_in + G * (M + N) * Kp * 2,
+              "gemm": G * (M + N) * Kp * 2 + v_bytes,
+              "crt": v_bytes + c_out}
+    if "crt_sums" in stages:
+        ngrp = -(-(info["crt_pieces"] + 5) // 32)
+        D = info["crt_digits"]
+        nbytes["crt_sums"] = v_bytes + M * N * (ngrp * 9 * 4 + 4)
+        nbytes["crt_finish"] = M * N * (4 * (D + 2 * -(-D // 7)) + 4) + c_out
+    hpk = float(peaks["hbm_gbs"])
+    for name, ms in stages.items():
+        if name in out and name in nbytes:
+            gbs = nbytes[name] / (ms / 1e3) / 1e9
+            out[name]["hbm"] = {"bytes": nbytes[name], "achieved": round(gbs, 1), "peak": hpk, "unit": "GB/s",
+                                "frac": round(gbs / hpk, 4)}
     return out
 
 

@@ -38,3 +38,22 @@ def test_tensor_core_crt_stages():
     per = 4 * (21 + 2 * 3) + 4 + 8 * 4 + 5
     assert f["achieved"] == pytest.approx(M * N * per / 0.09e-3 / 1e9, abs=0.05)
     assert 0 < f["frac"] < 1.5 and 0 < s["frac"] < 1.5
+
+
+def test_every_stage_reports_its_hbm_rate():
+    M = N = K = 1024
+    info = _info(crt_pieces=83)
+    st = {"scan": 0.02, "residues": 0.2, "gemm": 0.18, "crt_sums": 0.15, "crt_finish": 0.09}
+    out = bench.stage_rooflines(info, M, N, K, 256, st, "none")
+    for name, ms in st.items():
+        h = out[name]["hbm"]
+        assert h["unit"] == "GB/s" and h["achieved"] == pytest.approx(h["bytes"] / (ms * 1e-3) / 1e9, abs=0.05)
+    # residues: inputs (4 limbs + exponent + sign per entry) and 102 planes of 1024 x 1024 bf16 per side
+    assert out["residues"]["hbm"]["bytes"] == 2 * M * K * (8 * 4 + 5) + 102 * 2 * M * K * 2
+    # GEMM: both plane stacks and 70 values v_l per output
+    assert out["gemm"]["hbm"]["bytes"] == 102 * 2 * M * K * 2 + 70 * M * N * 2
+    # CRT sums: v_l in, three 9-word groups and the estimate out
+    assert out["crt_sums"]["hbm"]["bytes"] == 70 * M * N * 2 + M * N * (3 * 9 * 4 + 4)
+    cpu = bench.stage_rooflines(_info(), M, N, K, 256, {"scan": 0.02, "residues": 0.2, "gemm": 0.18, "crt": 0.25},
+                                "none")
+    assert cpu["crt"]["hbm"]["bytes"] == 70 * M * N * 2 + M * N * (8 * 4 + 5)
