@@ -33,7 +33,9 @@ rounding is round-half-even; two-limb moduli are the primes in (255, 16191].
 Matrix format: see ``synth`` (limb planes [nl, R, C], exp [R, C], sign [R, C];
 value = (-1)^sign * sig * 2^(exp - 64 nl)).
 
-Every function is parity-pinned by ``tests/test_oracle_pins.py``.
+Every function is parity-pinned: the multiple-precision path by
+``tests/test_oracle_pins.py``, the binary64 mode by
+``tests/test_oracle_fp64_pins.py``.
 """
 from __future__ import annotations
 

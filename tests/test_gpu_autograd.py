@@ -43,6 +43,21 @@ def _fd_grad_A(X, Y, G, i, k):
     return float((loss(h) - loss(-h)) / (2 * h))
 
 
+def _fd_grad_B(X, Y, G, k, j):
+    """Exact central difference of <G, A B> in B_kj."""
+    h = Fraction(1, 5)
+    def loss(delta):
+        tot = Fraction(0)
+        for i in range(X.shape[0]):
+            s = Fraction(0)
+            for kk in range(X.shape[1]):
+                b = Fraction(float(Y[kk, j])) + (delta if kk == k else 0)
+                s += Fraction(float(X[i, kk])) * b
+            tot += Fraction(float(G[i, j])) * s
+        return tot
+    return float((loss(h) - loss(-h)) / (2 * h))
+
+
 @pytest.mark.parametrize("M,N,K", [(24, 16, 40), (130, 70, 300), (64, 300, 33)])
 def test_forward_backward_against_oracle(ag, M, N, K):
     rng = np.random.Generator(np.random.PCG64(3000 + M))
@@ -68,6 +83,8 @@ def test_forward_backward_against_oracle(ag, M, N, K):
         assert _ulps(dB[k, j], o.exact_dot_double(X[:, k], G[:, j])) <= 1
     i, k = 1, 2
     assert _ulps(dA[i, k], _fd_grad_A(X, Y, G, i, k)) <= 1
+    k, j = 3, 1
+    assert _ulps(dB[k, j], _fd_grad_B(X, Y, G, k, j)) <= 1
 
 
 def test_backward_only_one_side(ag):
