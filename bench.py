@@ -1,23 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the Ozaki-II multiple-precision GEMM on GB300.
 
-Workload: one M = N = K = 1024 product at p = 256 bits (256 random
-significand bits with the top bit set, random sign, exponents i.i.d. uniform
-in [-32, 32]; seeded synthetic data).  A step is one whole product: exponent
-scan, integerization + residues, the grouped plane GEMM with fused
-mod-reduce, CRT and rounding.  `value` is whole-job 2MNK per second with the
-inputs resident in HBM; `e2e` times the same products through the C ABI with
-host buffers: every step copies A and B from pinned host memory and C back,
-inside the timed region, double-buffered so that the copies of neighbouring
-steps overlap the product.  L2 is flushed (a 512 MiB write) between the
-device-resident steps, outside the timed events.
+Default workload: the largest single-GPU configuration, one M = N = K = 4096
+product at p = 2048 bits (2048 random significand bits with the top bit set,
+random sign, exponents i.i.d. uniform in [-64, 64]; seeded synthetic data),
+with the residue planes streamed through the workspace in groups of moduli.
+A step is one whole product: exponent scan, integerization + residues, the
+grouped plane GEMMs with fused mod-reduce, CRT and rounding.  `value` is
+whole-job 2MNK per second with the inputs resident in HBM; `e2e` times the
+same products through the C ABI with host buffers: every step copies A and B
+from pinned host memory and C back, inside the timed region, double-buffered
+so that the copies of neighbouring steps overlap the product.  L2 is flushed
+(a 512 MiB write) between device-resident steps, outside the timed events.
+
+The same JSON line carries a `sweep` over the rest of the metric: the
+1024^3 p = 256 and 8192^3 p = 53 products, the 64-problem batch in one CUDA
+graph against the plain one-launch-per-modulus form, the binary64 autograd
+step at 4096^2, and the INT8 tensor-core peak of this GPU (the library's
+mma.sync s8 probe and torch._int_mm) with the plane GEMMs' exact-integer
+rate against it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--no-sweep] [--no-e2e] [--no-cpu-baseline]
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of
 the workload (the path needs no exchange); the time is the max over ranks.
 `--impl reference` times the CPU oracle (the slow, exact stage-by-stage
-restatement of the method) on the host cores instead.
+restatement of the method) on the host cores instead, on sampled output
+entries of the same workload.
 """
 from __future__ import annotations
 
@@ -37,10 +47,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "p-bit GEMM 2MNK/s at p=53–2048; INT8 TC util; batched vs plain speedup"
 UNIT = "2MNK/s"
-WORK = {"workload": "gemm_1024_p256", "M": 1024, "N": 1024, "K": 1024, "p": 256,
-        "exp_range": [-32, 32], "seed": 1001}
-PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-CPU_BLOCK = 32          # oracle sample: 32 x 32 output blocks of the workload
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+
+# single-product workloads: M, N, K, p, exponent range, seed
+WORKLOADS = {
+    "gemm_4096_p2048": (4096, 4096, 4096, 2048, (-64, 64), 1004),   # large, p = 2048
+    "gemm_8192_p53": (8192, 8192, 8192, 53, (-8, 8), 1004),         # large, p = 53
+    "gemm_1024_p256": (1024, 1024, 1024, 256, (-32, 32), 1001),     # one product, p = 256
+    "gemm_256_p53": (256, 256, 256, 53, (-8, 8), 1000),             # small, p = 53
+    "gemm_4096_p53": (4096, 4096, 4096, 53, (-8, 8), 1004),
+    "gemm_2048_p512": (2048, 2048, 2048, 512, (-8, 8), 1004),
+    "gemm_1024_p2048": (1024, 1024, 1024, 2048, (-64, 64), 1001),
+    "gemm_1024_p53": (1024, 1024, 1024, 53, (-8, 8), 1001),
+}
+DEFAULT_WORKLOAD = "gemm_4096_p2048"
+# a kernel timed inside a timed region longer than this runs under the power
+# cap: its roofline uses the sustained bf16 peak, otherwise the burst peak
+SUSTAINED_AFTER_S = 1.0
 
 
 # ---------------------------------------------------------------------------
@@ -87,7 +111,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
         self.path = None
@@ -137,40 +161,69 @@ class ClockSampler:
 # CPU oracle timing (the reference arm and the cpu_baseline object)
 # ---------------------------------------------------------------------------
 
-def _oracle_block(args):
-    i0, j0 = args
-    import synth
+def sample_entries(M: int, N: int, count: int, seed: int = 77):
+    """Seeded sample of output entries (i, j) of an M x N product."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [(int(rng.integers(M)), int(rng.integers(N))) for _ in range(count)]
+
+
+def entry_tasks(A: dict, B: dict, pairs):
+    """One oracle task per sampled entry: row i of A and column j of B only
+    (the pool processes receive these slices, not the whole matrices)."""
+    tasks = []
+    for i, j in pairs:
+        a = {"p": A["p"], "limbs": A["limbs"][:, i:i + 1, :].copy(), "exp": A["exp"][i:i + 1, :].copy(),
+             "sign": A["sign"][i:i + 1, :].copy()}
+        b = {"p": B["p"], "limbs": B["limbs"][:, :, j:j + 1].copy(), "exp": B["exp"][:, j:j + 1].copy(),
+             "sign": B["sign"][:, j:j + 1].copy()}
+        tasks.append((a, b))
+    return tasks
+
+
+def _oracle_entry(task):
+    """The oracle's stage-by-stage method on one output entry (full K)."""
     from oracle import ozaki2_oracle as o
-    A, B = synth.gemm_1024_p256(WORK["seed"])
-    rows = slice(i0, i0 + CPU_BLOCK)
-    cols = slice(j0, j0 + CPU_BLOCK)
-    As = {"p": A["p"], "limbs": A["limbs"][:, rows, :].copy(), "exp": A["exp"][rows, :].copy(),
-          "sign": A["sign"][rows, :].copy()}
-    Bs = {"p": B["p"], "limbs": B["limbs"][:, :, cols].copy(), "exp": B["exp"][:, cols].copy(),
-          "sign": B["sign"][:, cols].copy()}
-    t = time.perf_counter()
-    o.ozaki2_full(As, Bs, WORK["p"])
-    return time.perf_counter() - t
+    a, b = task
+    o.ozaki2_entries(a, b, a["p"], [(0, 0)])
+    return 1
 
 
-def cpu_oracle_rate(rounds: int = 2):
-    """Time the CPU oracle (stage-by-stage method, exact integers) on a bounded
-    sample: `cores * rounds` blocks of 32 x 32 outputs (full K) of the
-    workload, one spawn-pool process per host core."""
-    cores = os.cpu_count() or 1
-    nblk = cores * rounds
-    offs = [((b * 97) % (WORK["M"] // CPU_BLOCK) * CPU_BLOCK, (b * 61) % (WORK["N"] // CPU_BLOCK) * CPU_BLOCK)
-            for b in range(nblk)]
-    ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_block, offs, chunksize=1)
-    wall = time.perf_counter() - t0
-    work = nblk * 2 * CPU_BLOCK * CPU_BLOCK * WORK["K"]
-    sample = (f"oracle ozaki2_full on {nblk} blocks of {CPU_BLOCK}x{CPU_BLOCK} outputs (full K=1024) of "
-              f"the 1024^3 p=256 workload, spawn pool of {cores} processes, wall {wall:.1f} s "
-              f"incl. input regeneration")
-    return work / wall, cores, sample
+class OracleTimer:
+    """Times the CPU oracle, as it stands, on sampled output entries of a
+    workload: one spawn-pool process per host core, one entry per task."""
+
+    def __init__(self, A: dict, B: dict, K: int, cores: int | None = None):
+        self.cores = cores or os.cpu_count() or 1
+        self.K = K
+        M, N = A["exp"].shape[0], B["exp"].shape[1]
+        self.pool_tasks = entry_tasks(A, B, sample_entries(M, N, 4 * self.cores))
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.done = 0
+
+    def batch(self, n: int):
+        """Run n entries (cycling through the sample); returns (entries, wall s)."""
+        tasks = [self.pool_tasks[(self.done + q) % len(self.pool_tasks)] for q in range(n)]
+        self.done += n
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_entry, tasks, chunksize=1)
+        return n, time.perf_counter() - t0
+
+    def rate(self, min_s: float = 10.0, max_s: float = 30.0):
+        """Batches of `cores` entries until at least min_s of wall time (and
+        not more batches once max_s is passed): 2K per entry over the wall."""
+        n_tot, wall = 0, 0.0
+        while wall < min_s:
+            n, w = self.batch(self.cores)
+            n_tot += n
+            wall += w
+            if wall > max_s:
+                break
+        return n_tot * 2.0 * self.K / wall, n_tot, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 # ---------------------------------------------------------------------------
@@ -188,14 +241,19 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the committed kernels on the same workload; the source
-# summaries are under profiles/.  A kernel changed since its capture has None.
+# summaries are under profiles/.  A kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_1024_p256": {"residues": 443.90144e6, "gemm": 564.279552e6, "crt_sums": 223.868672e6,
-                       "crt_finish": 123.980288e6},
+    "gemm_1024_p256": {"residues": 443.90144e6, "crt_sums": 223.868672e6, "crt_finish": 123.980288e6},
 }
 
 
-def stage_rooflines(info, M, N, K, p, stages, workload):
+def finish_kernel(crt_digits: int) -> str:
+    """The finish kernel the library runs after the tensor-core CRT sums: the
+    register finish up to 24 accumulator digits, the shared-memory one above."""
+    return "k_crt_fin_short" if crt_digits <= 24 else "k_crt_fin_long"
+
+
+def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False):
     """Achieved vs peak for each stage's kernel, from its algorithmic work.
 
     residues: byte multiply-adds sum_b beta_b (2^(8b) mod m) over the
@@ -204,7 +262,8 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
       two-limb moduli: (M+N) K ceil((t+1)/8) (L1 + 2 L2), against the dp4a
       multiply-add rate.
     gemm: 2 M N K G flops of the G plane products, against the measured bf16
-      tensor peak (the integer planes are exact bf16 operands).
+      tensor peak (the integer planes are exact bf16 operands); the sustained
+      peak where the timed region is seconds long (`sustained`).
     crt (CUDA-core CRT): the 32 x 32 -> 64-bit multiply-adds of
       sum_l v_l M_l, L per output and digit of M_l: M N L ceil(bits(P)/32),
       against the IMAD.WIDE rate.
@@ -219,10 +278,10 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
     Every stage also carries ``hbm``: its algorithmic bytes (what it must read
     and write once) over its time, against the measured HBM copy rate, whatever
     its own bound: residues read the inputs (8 nl + 5 bytes per entry) and
-    write the G bf16 planes; the GEMM reads both plane stacks and writes the L
-    16-bit values v_l; the CRT reads v_l and writes C (8 nl + 5 bytes per
-    output), the tensor-core sums writing the 9-word group sums and the 4-byte
-    estimate in between.
+    write the G planes at `plane_bytes` per entry (2: bf16 planes); the GEMM
+    reads both plane stacks and writes the L 16-bit values v_l; the CRT reads
+    v_l and writes C (8 nl + 5 bytes per output), the tensor-core sums writing
+    the 9-word group sums and the 4-byte estimate in between.
     """
     peaks, src = load_peaks()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
@@ -230,6 +289,9 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
     L2 = L - L1
     md = info["crt_digits"] - 2
     traffic = NCU_TRAFFIC.get(workload, {})
+    tkey = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in peaks else "bf16_tflops"
+    tpk = float(peaks[tkey])
+    tsrc = f"{tkey} ({'sustained, timed region > 1 s' if tkey.endswith('sustained') else 'burst'}), {src}"
     out = {}
 
     def alu(name, kernel, ops, rate, what):
@@ -241,8 +303,15 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
                      "traffic": traffic.get(name)}
 
     res_macs = (M + N) * K * math.ceil((t + 1) / 8) * (L1 + 2 * L2)
-    alu("residues", "k_residue (integerize + byte-table residues + plane writes)", res_macs,
-        SMS * DP4A_MACS_PER_SM_CLK * clk, "byteMAC")
+    if info.get("res_mode") == 2:
+        # the byte products on the tensor cores: 2 flops per byte multiply-add
+        ach = 2.0 * res_macs / (stages["residues"] / 1e3) / 1e12
+        out["residues"] = {"kernel": "k_residue_mm (integerize + residues as an exact bf16 byte GEMM)",
+                           "bound": "tensor", "achieved": round(ach, 1), "peak": tpk, "unit": "TFLOP/s",
+                           "frac": round(ach / tpk, 4), "peak_source": tsrc, "traffic": traffic.get("residues")}
+    else:
+        alu("residues", "k_residue (integerize + byte-table residues + plane writes)", res_macs,
+            SMS * DP4A_MACS_PER_SM_CLK * clk, "byteMAC")
     if "crt" in stages:
         alu("crt", "k_crt1 / k_crt (direct CRT sum + quotient correction + rounding)", M * N * L * md,
             SMS * IMAD_WIDE_PER_SM_CLK * clk, "imad64")
@@ -250,26 +319,24 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
         np_ = info["crt_pieces"]
         fl = 2.0 * M * N * (2 * L) * np_
         ach = fl / (stages["crt_sums"] / 1e3) / 1e12
-        pk = float(peaks["bf16_tflops"])
         out["crt_sums"] = {"kernel": "k_crt_mm (CRT column sums as an exact bf16 GEMM + group carries)",
-                           "bound": "tensor", "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s",
-                           "frac": round(ach / pk, 4), "peak_source": f"bf16_tflops burst, {src}",
+                           "bound": "tensor", "achieved": round(ach, 1), "peak": tpk, "unit": "TFLOP/s",
+                           "frac": round(ach / tpk, 4), "peak_source": tsrc,
                            "traffic": traffic.get("crt_sums")}
         D = info["crt_digits"]
         nl = -(-p // 64)
         fb = M * N * (4 * (D + 2 * -(-D // 7)) + 4 + 8 * nl + 5)
         ach = fb / (stages["crt_finish"] / 1e3) / 1e9
         pk = float(peaks["hbm_gbs"])
-        out["crt_finish"] = {"kernel": "k_crt_fin_long (CRT finish from the group sums + rounding)",
+        out["crt_finish"] = {"kernel": f"{finish_kernel(D)} (CRT finish from the group sums + rounding)",
                              "bound": "hbm", "achieved": round(ach, 1), "peak": pk, "unit": "GB/s",
                              "frac": round(ach / pk, 4), "peak_source": f"hbm_gbs, {src}",
                              "traffic": traffic.get("crt_finish")}
     flops = 2.0 * M * N * K * G
     ach = flops / (stages["gemm"] / 1e3) / 1e12
-    pk = float(peaks["bf16_tflops"])
     out["gemm"] = {"kernel": "k_gemm_tc (plane GEMMs + fused mod-reduce)", "bound": "tensor",
-                   "achieved": round(ach, 1), "peak": pk, "unit": "TFLOP/s", "frac": round(ach / pk, 4),
-                   "peak_source": f"bf16_tflops burst, {src}", "traffic": traffic.get("gemm")}
+                   "achieved": round(ach, 1), "peak": tpk, "unit": "TFLOP/s", "frac": round(ach / tpk, 4),
+                   "peak_source": tsrc, "traffic": traffic.get("gemm")}
     scan_bytes = (M * K + K * N) * (8 + 4)      # top limb + exponent of every entry
     ach = scan_bytes / (stages["scan"] / 1e3) / 1e9
     pk = float(peaks["hbm_gbs"])
@@ -278,12 +345,13 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
                    "peak_source": f"hbm_gbs, {src}", "traffic": traffic.get("scan")}
     nl = -(-p // 64)
     Kp = -(-K // 8) * 8
+    pb = int(info.get("plane_bytes", 2))
     io_in = (M * K + K * N) * (8 * nl + 5)
     c_out = M * N * (8 * nl + 5)
     v_bytes = L * M * N * 2
     nbytes = {"scan": (M * K + K * N) * (8 + 4),
-              "residues": io_in + G * (M + N) * Kp * 2,
-              "gemm": G * (M + N) * Kp * 2 + v_bytes,
+              "residues": io_in + G * (M + N) * Kp * pb,
+              "gemm": G * (M + N) * Kp * pb + v_bytes,
               "crt": v_bytes + c_out}
     if "crt_sums" in stages:
         ngrp = -(-(info["crt_pieces"] + 5) // 32)
@@ -303,90 +371,109 @@ def stage_rooflines(info, M, N, K, p, stages, workload):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def run_ours(args):
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+class Gpu:
+    """Device, launch stream, L2 flush buffer and a CUDA-event timer."""
 
+    def __init__(self, local: int):
+        import torch
+        self.torch = torch
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.flush = torch.empty(512 << 20, dtype=torch.uint8, device=self.dev)
+
+    def timed(self, fn, steps: int, warm: int, each=None):
+        """Mean CUDA-event time (ms) of fn over `steps` calls after `warm`
+        untimed ones; L2 flushed before every timed call, outside the events."""
+        torch = self.torch
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s_, (a, b) in enumerate(ev):
+            self.flush.fill_(s_ & 0xff)
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+            if each is not None:
+                each()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def _plan_stages(plan, samples):
+    med = {k: statistics.median(s_[k] for s_ in samples) for k in samples[0]}
+    info = dict(plan.info)
+    if info["crt_mode"] == 2:        # two kernels: the sums on the tensor cores, then the finish
+        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt_sums", "crt_finish")}
+        Pm = 1
+        for m in plan.moduli():
+            Pm *= m
+        info["crt_pieces"] = (Pm.bit_length() + 6) // 7 + 1
+    else:
+        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
+    return stages, info
+
+
+def measure_single(g: Gpu, ozk, name: str, steps: int, warmup: int, world: int = 1, e2e: bool = True,
+                   barrier=None, host=None, **plan_kw):
+    """Device-resident (and optionally end-to-end) 2MNK/s of one product
+    workload, with the per-stage roofline objects."""
     import synth
-    from paper_2609_27831_gb300 import build
-    build.build()
-    import paper_2609_27831_gb300 as ozk
-
-    world, rank, local = dist_info()
-    if world != args.gpus:
-        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
-    # the CPU baseline's spawn pool runs before the first CUDA call
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(args.cpu_rounds)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    M, N, K, p = WORK["M"], WORK["N"], WORK["K"], WORK["p"]
-    A, B = synth.gemm_1024_p256(WORK["seed"])
-    dA, dB = ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev)
-    dC = ozk.MPMatrix.empty(M, N, p, dev)
-    plan = ozk.Plan((M, N, K, p), timing=1)
-    ws = plan.workspace(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    for _ in range(args.warmup):
-        plan.execute(dA, dB, dC, ws)
-    plan.check()
-    torch.cuda.synchronize()
-
-    # ---- device-resident timing
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage = []
-    props = torch.cuda.get_device_properties(dev)
-    uuid = getattr(props, "uuid", None)
-    clk = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-")
-                       else (str(uuid) if uuid is not None else local))
-    clk.start()
+    M, N, K, p, (lo, hi), seed = WORKLOADS[name]
+    A, B = host if host is not None else synth.workload_single(M, N, K, p, lo, hi, seed)
+    dA, dB = ozk.MPMatrix.from_host(A, g.dev), ozk.MPMatrix.from_host(B, g.dev)
+    dC = ozk.MPMatrix.empty(M, N, p, g.dev)
+    plan = ozk.Plan((M, N, K, p), timing=1, **plan_kw)
+    ws = plan.workspace(g.dev)
+    samples = []
+    barrier = barrier or (lambda: None)
     barrier()
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        flush.fill_(s & 0xff)
-        starts[s].record(stream)
-        plan.execute(dA, dB, dC, ws)
-        ends[s].record(stream)
-        stage.append({**plan.timings(), **plan.crt_split()})
-    torch.cuda.synchronize()
-    barrier()
-    clocks = clk.stop()
+    ms = g.timed(lambda: plan.execute(dA, dB, dC, ws), steps, warmup,
+                 each=lambda: samples.append({**plan.timings(), **plan.crt_split()}))
     plan.check()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    ms = max_over_ranks(sum(step_ms) / len(step_ms), dev)
+    barrier()
+    ms = max_over_ranks(ms, g.dev)
     work = 2.0 * M * N * K
-    value = replica_value(world, work, ms)
+    res = {"M": M, "N": N, "K": K, "p": p, "ms": ms, "value": replica_value(world, work, ms),
+           "plan": plan, "info": dict(plan.info), "samples": samples}
+    if e2e:
+        res["e2e"] = measure_e2e(g, ozk, plan, A, B, (dA, dB, dC), ws, steps, world, barrier)
+    stages, info = _plan_stages(plan, samples)
+    sustained = steps * ms / 1e3 > SUSTAINED_AFTER_S
+    res["stages"] = stages
+    res["kernels"] = stage_rooflines(info, M, N, K, p, stages, name, sustained)
+    res["gemm_tflops"] = 2.0 * M * N * K * info["G"] / (stages["gemm"] / 1e3) / 1e12
+    res["launches"] = plan.launches()
+    del dA, dB, dC, ws
+    return res
 
-    # ---- end to end through the C ABI with host buffers
-    hA = {k: torch.from_numpy(np.ascontiguousarray(A[k]).view(np.int64) if k == "limbs" else
-                              np.ascontiguousarray(A[k])).pin_memory() for k in ("limbs", "exp", "sign")}
-    hB = {k: torch.from_numpy(np.ascontiguousarray(B[k]).view(np.int64) if k == "limbs" else
-                              np.ascontiguousarray(B[k])).pin_memory() for k in ("limbs", "exp", "sign")}
-    hC = {"limbs": torch.empty(dC.limbs.shape, dtype=torch.int64).pin_memory(),
-          "exp": torch.empty(dC.exp.shape, dtype=torch.int32).pin_memory(),
-          "sign": torch.empty(dC.sign.shape, dtype=torch.int8).pin_memory()}
+
+def measure_e2e(g: Gpu, ozk, plan, A, B, bufs, ws, steps, world, barrier):
+    """End to end through the C ABI: pinned host inputs copied in and the
+    result copied out every step, double-buffered on two copy streams so that
+    the copies of step s + 1 and s - 1 overlap the product of step s; the timed
+    region runs from before the first input copy to after the last output copy."""
+    import numpy as np
+    torch = g.torch
+    dev, stream = g.dev, g.stream
+    dA, dB, dC = bufs
+    M, N = dC.shape
+    p = dC.p
+
+    def pinned(m):
+        return {k: torch.from_numpy(np.ascontiguousarray(m[k]).view(np.int64) if k == "limbs" else
+                                    np.ascontiguousarray(m[k])).pin_memory() for k in ("limbs", "exp", "sign")}
+
+    hA, hB = pinned(A), pinned(B)
+    hC = [{"limbs": torch.empty(dC.limbs.shape, dtype=torch.int64).pin_memory(),
+           "exp": torch.empty(dC.exp.shape, dtype=torch.int32).pin_memory(),
+           "sign": torch.empty(dC.sign.shape, dtype=torch.int8).pin_memory()} for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in list(hA.values()) + list(hB.values()))
-    d2h = sum(v.numel() * v.element_size() for v in hC.values())
-    # double-buffered: the host->device copies of step s + 1 (stream s_in) and the
-    # device->host copy of step s - 1 (stream s_out) overlap the product of step s
-    # (the launch stream); every step's copies are inside the timed region, which
-    # runs from before the first input copy to after the last output copy
-    bufA = [dA, ozk.MPMatrix.from_host(A, dev)]
-    bufB = [dB, ozk.MPMatrix.from_host(B, dev)]
+    d2h = sum(v.numel() * v.element_size() for v in hC[0].values())
+    bufA = [dA, ozk.MPMatrix.empty(*dA.shape, dA.p, dev)]
+    bufB = [dB, ozk.MPMatrix.empty(*dB.shape, dB.p, dev)]
     bufC = [dC, ozk.MPMatrix.empty(M, N, p, dev)]
-    hCs = [hC, {k: torch.empty_like(v).pin_memory() for k, v in hC.items()}]
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
@@ -409,16 +496,16 @@ def run_ours(args):
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[b])
             for k in ("limbs", "exp", "sign"):
-                hCs[b][k].copy_(getattr(bufC[b], k), non_blocking=True)
+                hC[b][k].copy_(getattr(bufC[b], k), non_blocking=True)
             ev_out[b].record(s_out)
 
     barrier()
     torch.cuda.synchronize()
     t0.record(s_in)
     copy_in(0)
-    for st in range(args.steps):
+    for st in range(steps):
         b = st & 1
-        if st + 1 < args.steps:
+        if st + 1 < steps:
             copy_in(st + 1)
         stream.wait_event(ev_in[b])
         if st >= 2:
@@ -430,191 +517,293 @@ def run_ours(args):
     t1.record(s_in)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, dev)
+    plan.check()
+    e2e_ms = max_over_ranks(t0.elapsed_time(t1) / steps, dev)
+    work = 2.0 * M * N * dA.shape[1]
+    return {"value": replica_value(world, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "copies": "pinned host buffers, every step, double-buffered on two copy streams"}
 
-    # ---- roofline of the dominant kernel (library stage events on the launch stream)
-    med = {k: statistics.median(s_[k] for s_ in stage) for k in stage[0]}
-    info = dict(plan.info)
-    if info["crt_mode"] == 2:        # two kernels: the sums on the tensor cores, then the finish
-        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt_sums", "crt_finish")}
-        Pm = 1
-        for m in plan.moduli():
-            Pm *= m
-        info["crt_pieces"] = (Pm.bit_length() + 6) // 7 + 1
-    else:
-        stages = {k: med[k] for k in ("scan", "residues", "gemm", "crt")}
-    kernels = stage_rooflines(info, M, N, K, p, stages, WORK["workload"])
+
+def measure_batched(g: Gpu, ozk, steps: int = 5, warmup: int = 3):
+    """64 problems: one CUDA graph of the grouped launches, the grouped
+    executes without the graph, and the plain form (one GEMM launch per
+    modulus per problem) on the same inputs."""
+    import synth
+    probs = synth.batched_problems(64, 1002)
+    shapes = [(M, N, K, p) for (M, N, K, p, _, _) in probs]
+    trip = [(ozk.MPMatrix.from_host(A, g.dev), ozk.MPMatrix.from_host(B, g.dev), ozk.MPMatrix.empty(M, N, p, g.dev))
+            for (M, N, K, p, A, B) in probs]
+    work = sum(2.0 * M * N * K for (M, N, K, p) in shapes)
+    plan_g = ozk.Plan(shapes)
+    ws_g = plan_g.workspace(g.dev)
+    s = g.torch.cuda.Stream(g.dev)
+    with g.torch.cuda.stream(s):
+        graph = plan_g.graph(trip, ws_g, s)
+    ms_graph = g.timed(lambda: graph.launch(g.stream), steps, warmup)
+    ms_grouped = g.timed(lambda: plan_g.execute_batched(trip, ws_g, g.stream), steps, warmup)
+    plan_g.check()
+    del graph, ws_g
+    g.torch.cuda.empty_cache()
+    plan_p = ozk.Plan(shapes, schedule=1)
+    ws_p = plan_p.workspace(g.dev)
+    ms_plain = g.timed(lambda: plan_p.execute_batched(trip, ws_p, g.stream), max(2, steps // 2), warmup)
+    plan_p.check()
+    del ws_p
+    g.torch.cuda.empty_cache()
+    return {"problems": 64, "M_N_K": "log-uniform [128, 2048]", "p": [113, 256, 512],
+            "value": work / (ms_graph / 1e3), "unit": UNIT, "graph_ms": ms_graph, "grouped_ms": ms_grouped,
+            "plain_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_graph,
+            "plain": "one plane-GEMM launch per modulus per problem (other stages grouped)"}
+
+
+def measure_autograd(g: Gpu, steps: int = 5, warmup: int = 3, n: int = 4096):
+    """binary64 forward C = AB and backward dA, dB (three products)."""
+    import synth
+    from paper_2609_27831_gb300 import autograd as ag
+    torch = g.torch
+    X, Y, G = synth.fp64_workload(n, 1003)
+    xa = torch.tensor(X, device=g.dev, requires_grad=True)
+    ya = torch.tensor(Y, device=g.dev, requires_grad=True)
+    gt = torch.tensor(G, device=g.dev)
+
+    def step():
+        xa.grad = None
+        ya.grad = None
+        ag.ozaki_matmul(xa, ya).backward(gt)
+    ms = g.timed(step, steps, warmup)
+    return {"M": n, "N": n, "K": n, "p": 53, "ms_per_step": ms, "value": 3 * 2.0 * n ** 3 / (ms / 1e3),
+            "unit": UNIT, "step": "forward C = AB and backward dA, dB (3 products)"}
+
+
+def measure_int8_peak(g: Gpu, ozk):
+    """INT8 tensor-core peak of this GPU: the library's mma.sync s8 probe and
+    the library INT8 GEMM behind torch._int_mm (cuBLASLt) at 8192^3."""
+    import ctypes as C
+    torch = g.torch
+    sink = torch.zeros(1, dtype=torch.int32, device=g.dev)
+    tops = C.c_double()
+    probe = []
+    for _ in range(3):
+        ozk.check(ozk.lib().ozaki2_probe_mma_s8(SMS * 8, 4096, sink.data_ptr(), C.byref(tops),
+                                                g.stream.cuda_stream), "ozaki2_probe_mma_s8")
+        probe.append(tops.value)
+    out = {"mma_sync_s8_tops": round(max(probe), 1),
+           "mma_sync_s8": "m16n8k32 s8 x s8 -> s32, register operands, 8 warps x 8 blocks per SM"}
+    try:
+        n = 8192
+        a = torch.randint(-127, 128, (n, n), dtype=torch.int8, device=g.dev)
+        b = torch.randint(-127, 128, (n, n), dtype=torch.int8, device=g.dev)
+        ms = g.timed(lambda: torch._int_mm(a, b), 10, 3)
+        out["int_mm_tops"] = round(2.0 * n ** 3 / (ms / 1e3) / 1e12, 1)
+        out["int_mm"] = "torch._int_mm (cuBLASLt INT8, library) 8192^3"
+        del a, b
+    except (RuntimeError, AttributeError) as exc:     # not available on this build
+        out["int_mm_tops"] = None
+        out["int_mm"] = f"unavailable: {str(exc).splitlines()[0][:120]}"
+    cands = [v for v in (out["mma_sync_s8_tops"], out["int_mm_tops"]) if v]
+    out["int8_peak_tops"] = max(cands)
+    return out
+
+
+def _single_summary(r):
+    st = r["stages"]
+    gk = r["kernels"]["gemm"]
+    return {"ms_per_step": r["ms"], "value": r["value"], "unit": UNIT,
+            "config": {"M": r["M"], "N": r["N"], "K": r["K"], "p": r["p"], "t": r["info"]["t"],
+                       "moduli": r["info"]["L"], "gemms": r["info"]["G"],
+                       "plane_groups": r["info"]["plane_groups"], "group_planes": r["info"]["group_planes"],
+                       "workspace_gb": round(r["plan"].workspace_bytes / 1e9, 2)},
+            "stage_ms": {k: round(v, 4) for k, v in st.items()},
+            "plane_gemm_tflops": round(r["gemm_tflops"], 1), "plane_gemm_frac": gk["frac"],
+            "plane_gemm_peak": gk["peak_source"]}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as ozk
+
+    world, rank, local = dist_info()
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    name = args.workload
+    M, N, K, p, (lo, hi), seed = WORKLOADS[name]
+    A, B = synth.workload_single(M, N, K, p, lo, hi, seed)
+    # the CPU baseline's spawn pool: the oracle on sampled entries of the same workload
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ot = OracleTimer(A, B, K)
+        rate, n_ent, wall = ot.rate()
+        ot.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": ot.cores, "kind": "oracle",
+               "sample": f"oracle ozaki2_entries (stage-by-stage method, exact integers) on {n_ent} sampled "
+                         f"output entries of the {M}x{N}x{K} p={p} workload, each a full K={K} inner product; "
+                         f"spawn pool of {ot.cores} processes; wall {wall:.1f} s; rate = 2K per entry / wall"}
+    g = Gpu(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=g.dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    props = torch.cuda.get_device_properties(g.dev)
+    uuid = getattr(props, "uuid", None)
+    clk = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-")
+                       else (str(uuid) if uuid is not None else local))
+    clk.start()
+    r = measure_single(g, ozk, name, args.steps, args.warmup, world, e2e=not args.no_e2e, barrier=barrier,
+                       host=(A, B))
+    clocks = clk.stop()
+    stages, kernels = r["stages"], r["kernels"]
     dom = max(stages, key=stages.get)
     roof = dict(kernels[dom])
     roof["stage_ms"] = {k: round(v, 4) for k, v in stages.items()}
-    gemm_tflops = 2.0 * M * N * K * info["G"] / (stages["gemm"] / 1e3) / 1e12
-
+    info = r["info"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16-int (exact integer planes on tcgen05 kind::f16)",
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": WORK["workload"], "M": M, "N": N, "K": K, "p": p,
-                   "exp_range": WORK["exp_range"], "t": info["t"], "moduli": info["L"], "gemms": info["G"],
-                   "parallelism": f"replicas{world}", "l2": "flushed (512 MiB write between steps)"},
-        "e2e": {"value": replica_value(world, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "copies": "pinned host buffers, every step, double-buffered on two copy streams"},
+        "config": {"workload": name, "M": M, "N": N, "K": K, "p": p, "exp_range": [lo, hi], "seed": seed,
+                   "t": info["t"], "moduli": info["L"], "gemms": info["G"],
+                   "plane_groups": info["plane_groups"], "group_planes": info["group_planes"],
+                   "workspace_gb": round(r["plan"].workspace_bytes / 1e9, 2),
+                   "parallelism": f"replicas{world}",
+                   "l2": "flushed (512 MiB write between steps); inputs larger than L2"},
         "roofline": roof,
         "kernels": {k: v for k, v in kernels.items() if k != dom},
-        "plane_gemm_tflops": round(gemm_tflops, 1),
-        "gpu_launches": plan.launches() * args.steps,
+        "plane_gemm_tflops": round(r["gemm_tflops"], 1),
+        "gpu_launches": r["launches"] * args.steps,
         "clocks": clocks,
     }
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
     if cpu is not None:
-        rate, cores, sample = cpu
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"] = cpu
+    del r
+    torch.cuda.empty_cache()
+    if not args.no_sweep and world == 1:
+        sweep = {}
+        for wl in ("gemm_1024_p256", "gemm_8192_p53", "gemm_256_p53"):
+            if wl == name:
+                continue
+            st_ = {"gemm_1024_p256": 200, "gemm_8192_p53": 5, "gemm_256_p53": 200}[wl]
+            rr = measure_single(g, ozk, wl, st_, 5, e2e=False)
+            sweep[wl] = _single_summary(rr)
+            line["gpu_launches_sweep"] = line.get("gpu_launches_sweep", 0) + rr["launches"] * (st_ + 5)
+            del rr
+            torch.cuda.empty_cache()
+        if info["plane_groups"] > 1:
+            # the same product with every plane resident at once (one group)
+            rr = measure_single(g, ozk, name, 3, 3, e2e=False, host=(A, B), plane_group=-1)
+            sweep[name + "_one_group"] = _single_summary(rr)
+            del rr
+            torch.cuda.empty_cache()
+        sweep["batched64"] = measure_batched(g, ozk)
+        sweep["dgemm4096_autograd"] = measure_autograd(g)
+        i8 = measure_int8_peak(g, ozk)
+        G_ = info["G"]
+        plane_int = 2.0 * M * N * K * G_ / (stages["gemm"] / 1e3) / 1e12
+        i8["plane_gemm_int_tops"] = round(plane_int, 1)
+        i8["plane_gemm_frac_of_int8_peak"] = round(plane_int / i8["int8_peak_tops"], 3)
+        i8["note"] = ("the plane GEMMs run exact integer products on tcgen05 kind::f16 (bf16 operands, "
+                      "fp32 accumulation kept exact by K chunks); their integer-operation rate is stated "
+                      "against this GPU's INT8 tensor peak, which is below the bf16 rate")
+        sweep["int8"] = i8
+        line["sweep"] = sweep
+        line["clocks_sweep_excluded"] = "clocks are sampled over the main workload's timed region"
+    del A, B
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_other(args):
-    """Measurements of the other workloads (one GPU): batched, autograd, large."""
-    import numpy as np
-    import torch
-
-    import synth
-    from paper_2609_27831_gb300 import build
-    build.build()
-    import paper_2609_27831_gb300 as ozk
-    from paper_2609_27831_gb300 import autograd as ag
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    def timed(fn, steps, warm):
-        for _ in range(warm):
-            fn()
-        torch.cuda.synchronize()
-        tot = 0.0
-        for s_ in range(steps):
-            flush.fill_(s_ & 0xff)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            tot += a.elapsed_time(b)
-        return tot / steps
-
-    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": True, "data": "synthetic", "impl": "ours"}
-    if args.workload == "batched64":
-        probs = synth.batched_problems(64, 1002)
-        shapes = [(M, N, K, p) for (M, N, K, p, _, _) in probs]
-        trip = [(ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev), ozk.MPMatrix.empty(M, N, p, dev))
-                for (M, N, K, p, A, B) in probs]
-        work = sum(2.0 * M * N * K for (M, N, K, p) in shapes)
-        plan_g = ozk.Plan(shapes)
-        ws_g = plan_g.workspace(dev)
-        s = torch.cuda.Stream(dev)
-        with torch.cuda.stream(s):
-            g = plan_g.graph(trip, ws_g, s)
-        ms_graph = timed(lambda: g.launch(stream), args.steps, args.warmup)
-        ms_grouped = timed(lambda: plan_g.execute_batched(trip, ws_g, stream), args.steps, args.warmup)
-        del ws_g
-        torch.cuda.empty_cache()
-        plan_p = ozk.Plan(shapes, schedule=1)
-        ws_p = plan_p.workspace(dev)
-        ms_plain = timed(lambda: plan_p.execute_batched(trip, ws_p, stream), args.steps, args.warmup)
-        plan_p.check()
-        out.update({"value": work / (ms_graph / 1e3), "ms_per_step": ms_graph,
-                    "config": {"workload": "batched64", "problems": 64, "M_N_K": "log-uniform [128, 2048]",
-                               "p": [113, 256, 512], "gemms": sum(1 for _ in shapes)},
-                    "batched": {"graph_ms": ms_graph, "grouped_ms": ms_grouped, "plain_ms": ms_plain,
-                                "speedup_vs_plain": ms_plain / ms_graph,
-                                "plain": "one GEMM launch per modulus per problem (other stages grouped)"}})
-    elif args.workload == "dgemm4096_autograd":
-        X, Y, G = synth.fp64_workload(4096, 1003)
-        xa = torch.tensor(X, device=dev, requires_grad=True)
-        ya = torch.tensor(Y, device=dev, requires_grad=True)
-        gt = torch.tensor(G, device=dev)
-
-        def step():
-            xa.grad = None
-            ya.grad = None
-            ag.ozaki_matmul(xa, ya).backward(gt)
-        ms = timed(step, args.steps, args.warmup)
-        n = 4096
-        out.update({"value": 3 * 2.0 * n ** 3 / (ms / 1e3), "ms_per_step": ms,
-                    "config": {"workload": "dgemm4096_autograd", "M": n, "N": n, "K": n, "p": 53,
-                               "step": "forward C = AB and backward dA, dB (3 products)"}})
-    else:
-        M, N, K, p, lo, hi = {"gemm_4096_p2048": (4096, 4096, 4096, 2048, -64, 64),
-                              "gemm_8192_p53": (8192, 8192, 8192, 53, -8, 8),
-                              "gemm_4096_p53": (4096, 4096, 4096, 53, -8, 8),
-                              "gemm_2048_p512": (2048, 2048, 2048, 512, -8, 8)}[args.workload]
-        A, B = synth.workload_single(M, N, K, p, lo, hi, 1004)
-        dA, dB = ozk.MPMatrix.from_host(A, dev), ozk.MPMatrix.from_host(B, dev)
-        del A, B
-        dC = ozk.MPMatrix.empty(M, N, p, dev)
-        plan = ozk.Plan((M, N, K, p), timing=1)
-        ws = plan.workspace(dev)
-        ms = timed(lambda: plan.execute(dA, dB, dC, ws), args.steps, args.warmup)
-        plan.check()
-        st = plan.timings()
-        out.update({"value": 2.0 * M * N * K / (ms / 1e3), "ms_per_step": ms,
-                    "config": {"workload": args.workload, "M": M, "N": N, "K": K, "p": p, "t": plan.info["t"],
-                               "moduli": plan.info["L"], "gemms": plan.info["G"],
-                               "workspace_gb": round(plan.workspace_bytes / 1e9, 2)},
-                    "stage_ms": {k: round(v, 3) for k, v in st.items()},
-                    "plane_gemm_tflops": round(2.0 * M * N * K * plan.info["G"] / (st["gemm"] / 1e3) / 1e12, 1)})
-    print(json.dumps(out), flush=True)
-
-
 def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
         return
+    import synth
+    name = args.workload
+    M, N, K, p, (lo, hi), seed = WORKLOADS[name]
+    A, B = synth.workload_single(M, N, K, p, lo, hi, seed)
+    ot = OracleTimer(A, B, K)
+    del A, B
     for _ in range(args.warmup):
-        _oracle_block((0, 0))
+        ot.batch(1)
     rates = []
+    n_tot, wall_tot = 0, 0.0
     for _ in range(args.steps):
-        rate, cores, sample = cpu_oracle_rate(1)
-        rates.append(rate)
+        n, w = ot.batch(ot.cores)
+        rates.append(n * 2.0 * K / w)
+        n_tot += n
+        wall_tot += w
+    ot.close()
     value = statistics.median(rates)
-    ms = 2.0 * WORK["M"] * WORK["N"] * WORK["K"] / value * 1e3
+    ms = 2.0 * M * N * K / value * 1e3
+    sample = (f"oracle ozaki2_entries on {ot.cores} sampled output entries per step (one per host core, "
+              f"full K={K}) of the {M}x{N}x{K} p={p} workload; {n_tot} entries in {wall_tot:.1f} s")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms,
+        "ms_per_step_kind": "extrapolated: the whole product's 2MNK at the sampled entries' rate",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "exact integers (Python)", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORK["workload"], "M": WORK["M"], "N": WORK["N"], "K": WORK["K"],
-                   "p": WORK["p"], "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": name, "M": M, "N": N, "K": K, "p": p, "exp_range": [lo, hi], "seed": seed,
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ot.cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def run_workload_only(args):
+    """One workload's device-resident timing only (for profilers and quick
+    checks): no end-to-end leg, no sweep, no CPU baseline."""
+    from paper_2609_27831_gb300 import build
+    build.build()
+    import paper_2609_27831_gb300 as ozk
+    g = Gpu(0)
+    if args.workload == "batched64":
+        out = measure_batched(g, ozk, args.steps, args.warmup)
+    elif args.workload == "dgemm4096_autograd":
+        out = measure_autograd(g, args.steps, args.warmup)
+    else:
+        out = _single_summary(measure_single(g, ozk, args.workload, args.steps, args.warmup, e2e=False))
+    out.update({"metric": METRIC, "workload": args.workload, "steps": args.steps, "warmup": args.warmup,
+                "impl": "ours", "only": True})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + ["batched64", "dgemm4096_autograd"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rounds", type=int, default=6)
-    ap.add_argument("--workload", default="gemm_1024_p256",
-                    choices=["gemm_1024_p256", "batched64", "dgemm4096_autograd", "gemm_4096_p2048",
-                             "gemm_8192_p53", "gemm_4096_p53", "gemm_2048_p512"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", action="store_true",
+                    help="time the workload alone (device-resident), e.g. under a profiler")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
+        if args.workload not in WORKLOADS:
+            raise SystemExit("the reference arm times single-product workloads")
         run_reference(args)
-    elif args.workload != "gemm_1024_p256":
-        run_other(args)
+    elif args.only or args.workload not in WORKLOADS:
+        run_workload_only(args)
     else:
         run_ours(args)
 

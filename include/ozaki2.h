@@ -109,6 +109,17 @@ typedef struct {
                      tensor cores where the table has <= 256 rows and <= 256 bytes (CUDA cores
                      otherwise); 2: the same GEMM, warp-specialised (bytes in tensor memory, table
                      streamed), for integers of up to 448 bytes; 3: CUDA cores only */
+  int plane_group; /* residue planes streamed through the workspace in groups of consecutive
+                     moduli (single-product plans with the tensor-core engine and the grouped
+                     schedule; batched plans ignore it): 0 automatic (default): one group while
+                     the bf16 plane stacks of A and B fit in 32 GiB, else groups of at most that
+                     size; -1: never (one group); >= 3: at most this many planes per group.
+                     Each group computes its moduli's residues and plane products before the next
+                     starts; the CRT runs once over all moduli.  Bits are identical either way. */
+  int gemm_tile;  /* output tile of the tensor-core plane GEMMs: 0 automatic (default); 1: 128 x 256
+                     tiles, one SM each; 2: 256 x 256 tiles on CTA pairs (clusters of two SMs,
+                     tcgen05 cta_group::2), each SM holding its 128 rows of A and half of B.  The
+                     SIMT engine uses 1.  Bits are identical either way. */
 } ozaki2_opts;
 
 /* Facts about a plan (all computed on the host at plan creation). */
@@ -125,6 +136,9 @@ typedef struct {
   int crt_mode;     /* CRT path of problem 0: 0 CUDA cores, 1 tensor-core column sums in one
                        kernel, 2 tensor-core sums of any length plus the finish (see crt_engine) */
   int res_mode;     /* residue path of problem 0: 0 CUDA cores, 1 or 2 tensor cores (res_engine) */
+  int plane_groups; /* modulus groups the planes of problem 0 are streamed in (1: not streamed) */
+  int group_planes; /* planes of the largest group (= G when not streamed) */
+  int gemm_tile;    /* plane GEMM tile in use: 1 (128 x 256, one SM) or 2 (256 x 256, CTA pairs) */
 } ozaki2_info;
 
 typedef struct {
@@ -174,7 +188,8 @@ OZ2_API int ozaki2_plan_crt_tables(ozaki2_plan plan, int prob, uint32_t* P_digit
                            uint32_t* Minv);
 
 /* Byte offsets of the workspace regions of problem `prob` (for inspection of
-   intermediates after an execute):
+   intermediates after an execute; when the planes are streamed in groups the
+   plane regions hold the last group's planes, group_planes of them):
      off[0] row exponents e   int32 [M]
      off[1] column exponents f int32 [N]
      off[2] A planes  bf16 [G][M][Kp]   (Kp = K rounded up to 8; K-major)
@@ -197,6 +212,30 @@ OZ2_API int ozaki2_plan_launches(ozaki2_plan plan, int* n);
    |c_hat| as crt_digits little-endian digits), row-major over (i, j). */
 OZ2_API int ozaki2_plan_set_debug_chat(ozaki2_plan plan, int prob, uint32_t* dev_buf);
 
+/* Fault injection and failure detection (debugging aids; the paper has none).
+   Every failure is made on the host; no GPU fault is involved. */
+
+/* The number of polls of every bounded device-side wait (mbarrier waits of
+   the tensor-core kernels) in later executes of this plan; 0 restores the
+   default (2^26).  A wait that runs out sets the device status word
+   (ozaki2_check then returns OZ2_ETIMEOUT), the kernel drains the copies and
+   MMAs it has in flight, frees its tensor memory and returns; the product's
+   output is then undefined.  Host only. */
+OZ2_API int ozaki2_plan_set_wait_limit(ozaki2_plan plan, uint32_t polls);
+
+/* Corrupt problem `prob`'s CRT tables on the host before they are uploaded
+   (OZ2_EINVAL after the plan's first execute): the top 32-bit digit of
+   M_0 = P / m_0 (and its top 7-bit piece in the tensor-core table) has one
+   bit flipped, so the direct CRT's range check (x0 < P, Sec. 4.4) fails on
+   the device and ozaki2_check returns OZ2_EINTERNAL.  Host only. */
+OZ2_API int ozaki2_plan_debug_corrupt_crt(ozaki2_plan plan, int prob);
+
+/* Make the next `count` library allocations (host plan construction, the
+   device tables of a plan's first execute, launch images) fail with
+   OZ2_ENOMEM without allocating; 0 cancels.  Nothing half-made is kept: a
+   later call with the same arguments starts over. */
+OZ2_API int ozaki2_debug_inject_alloc_failure(int count);
+
 /* Run the plan: C = A * B rounded to p bits, via workspace `ws` (device,
    >= info.workspace_bytes, 256-byte aligned, caller-owned, contents need not
    be initialised and are clobbered).  Single-problem plans only. */
@@ -206,6 +245,22 @@ OZ2_API int ozaki2_execute(ozaki2_plan plan, const ozaki2_mat* A, const ozaki2_m
 /* Run a batched plan on `count` problems with the planned shapes. */
 OZ2_API int ozaki2_execute_batched(ozaki2_plan plan, int count, const ozaki2_problem* probs, void* ws,
                            size_t ws_bytes, void* stream);
+
+/* Operand reuse (the paper's Sec. 11 names reusing the residues of one
+   operand across products as future work): C = A X (keep = 0) or C = X B
+   (keep = 1) with the plan's shape, keeping the row exponents and residue
+   planes of A (keep = 0) or the column exponents and planes of B (keep = 1)
+   that the previous execute of this single-problem plan left in the same
+   workspace `ws`; only X is scanned, integerized and reduced.  X has the shape
+   of the replaced operand (K x N for keep = 0, M x K for keep = 1).  The
+   workspace must not have been used by anything else in between (the library
+   checks only that the pointer is the same).  OZ2_EINVAL without a previous
+   execute with this workspace, for batched plans, for plans whose planes are
+   streamed in modulus groups (only the last group's planes stay), and for the
+   binary64 mode's internal plans.  The result is bit-identical to a full
+   execute with the same operands. */
+OZ2_API int ozaki2_execute_reuse(ozaki2_plan plan, int keep, const ozaki2_mat* X, ozaki2_mat* C, void* ws,
+                                 size_t ws_bytes, void* stream);
 
 /* Capture one execute of a (batched or single) plan with fixed pointers into
    a CUDA graph; ozaki2_graph_launch replays it on any stream. */
@@ -233,12 +288,21 @@ OZ2_API int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat
    1024^3 at p = 256) are rejected with OZ2_ERANGE before any device work.
    The first call on a device looks up the arrays' device addresses (once per
    device, with that device current); make that first call before any stream
-   capture.  Every call shares the arrays and rewrites them: calls that
-   overlap on the GPU (different streams, or concurrent host threads) race,
-   so order them on one stream.  Default options; the device status word of
-   this path is not readable through ozaki2_check. */
+   capture.  Each call writes its tables into the array with small kernels on
+   `stream` (their parameters carry the bytes), so it does not wait on the
+   host for earlier work on the stream.  Every call shares the arrays and
+   rewrites them: calls that overlap on the GPU (different streams, or
+   concurrent host threads) race, so order them on one stream.  Default
+   options.  The device status word of the most recent call on the current
+   device (cleared at the start of each call) is read by ozaki2_noalloc_check. */
 OZ2_API int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A,
                                 const ozaki2_mat* B, ozaki2_mat* C, void* stream);
+
+/* Synchronise `stream` and read (then clear) the device status word of the
+   last ozaki2_gemm_noalloc call on the current device: OZ2_OK, OZ2_EINTERNAL
+   (a device-side consistency check failed) or OZ2_ETIMEOUT (a bounded wait
+   gave up).  Allocates nothing. */
+OZ2_API int ozaki2_noalloc_check(void* stream);
 
 /* Convenience batched call (library-owned plan and workspace). */
 OZ2_API int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts,
@@ -286,6 +350,22 @@ OZ2_API int ozaki2_dgemm_bwd(ozaki2_cache cache, const double* dC, int64_t lddc,
                      int64_t ldda, double* dB, int64_t lddb, void* stream);
 
 OZ2_API int ozaki2_cache_destroy(ozaki2_cache cache);
+
+/* ---------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): the throughput of the
+ * warp-level INT8 tensor-core instruction mma.sync m16n8k32 (s8 x s8 -> s32),
+ * the only INT8 tensor path sm_103a exposes (tcgen05.mma kind::i8 is not
+ * available for this target).  It states the INT8 peak against which the
+ * plane GEMMs' exact-integer rate is reported.
+ * ------------------------------------------------------------------------- */
+
+/* Launch `blocks` blocks of 8 warps, each warp issuing 8 x iters independent
+   MMAs on register operands, time the launch with CUDA events on `stream`
+   (after one warm-up launch) and store the rate in tera integer operations
+   per second (2 per multiply-add) in *tops.  `sink` is a device int that is
+   written only in a practically impossible case (it keeps the compiler from
+   removing the MMAs).  Synchronises `stream`. */
+OZ2_API int ozaki2_probe_mma_s8(int blocks, int iters, int* sink, double* tops, void* stream);
 
 /* Library version string (static storage). */
 OZ2_API const char* ozaki2_version(void);

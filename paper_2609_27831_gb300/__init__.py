@@ -153,6 +153,13 @@ class Plan:
         check(lib().ozaki2_execute(self._h, C.byref(a), C.byref(b), C.byref(c), ws.data_ptr(),
                                    ws.numel(), _stream_handle(stream)), "ozaki2_execute")
 
+    def execute_reuse(self, keep: int, X: MPMatrix, Cm: MPMatrix, ws: torch.Tensor, stream=None):
+        """C = A X (keep=0: A's planes from the previous execute with ``ws``) or
+        C = X B (keep=1: B's planes kept)."""
+        x, c = X.desc(), Cm.desc()
+        check(lib().ozaki2_execute_reuse(self._h, keep, C.byref(x), C.byref(c), ws.data_ptr(), ws.numel(),
+                                         _stream_handle(stream)), "ozaki2_execute_reuse")
+
     def _problems(self, triples):
         arr = (L.Problem * len(triples))()
         for i, ((M, N, K, p), (A, B, Cm)) in enumerate(zip(self.shapes, triples)):

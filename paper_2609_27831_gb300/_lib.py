@@ -25,14 +25,16 @@ class Mat(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("guard_bits", C.c_int), ("t_bits", C.c_int), ("engine", C.c_int),
                 ("k_chunk", C.c_int), ("grid", C.c_int), ("schedule", C.c_int),
-                ("timing", C.c_int), ("crt_engine", C.c_int), ("res_engine", C.c_int)]
+                ("timing", C.c_int), ("crt_engine", C.c_int), ("res_engine", C.c_int),
+                ("plane_group", C.c_int), ("gemm_tile", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("count", C.c_int), ("t", C.c_int), ("L", C.c_int), ("L1", C.c_int),
                 ("G", C.c_int), ("crt_digits", C.c_int), ("units", C.c_int),
                 ("jobs", C.c_int), ("workspace_bytes", C.c_size_t), ("crt_mode", C.c_int),
-                ("res_mode", C.c_int)]
+                ("res_mode", C.c_int), ("plane_groups", C.c_int), ("group_planes", C.c_int),
+                ("gemm_tile", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -65,10 +67,15 @@ _SIGS = {
                                       C.POINTER(C.c_int64)]),
     "ozaki2_plan_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "ozaki2_plan_set_debug_chat": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "ozaki2_plan_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "ozaki2_plan_debug_corrupt_crt": (C.c_int, [C.c_void_p, C.c_int]),
+    "ozaki2_debug_inject_alloc_failure": (C.c_int, [C.c_int]),
     "ozaki2_execute": (C.c_int, [C.c_void_p, C.POINTER(Mat), C.POINTER(Mat), C.POINTER(Mat),
                                   C.c_void_p, C.c_size_t, C.c_void_p]),
     "ozaki2_execute_batched": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Problem), C.c_void_p,
                                           C.c_size_t, C.c_void_p]),
+    "ozaki2_execute_reuse": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Mat), C.POINTER(Mat), C.c_void_p,
+                                        C.c_size_t, C.c_void_p]),
     "ozaki2_graph_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Problem), C.c_void_p,
                                        C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p)]),
     "ozaki2_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -78,6 +85,7 @@ _SIGS = {
     "ozaki2_gemm_batched": (C.c_int, [C.c_int, C.POINTER(Problem), C.POINTER(Opts), C.c_void_p]),
     "ozaki2_gemm_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.POINTER(Mat),
                                        C.POINTER(Mat), C.POINTER(Mat), C.c_void_p]),
+    "ozaki2_noalloc_check": (C.c_int, [C.c_void_p]),
     "ozaki2_release_cache": (C.c_int, []),
     "ozaki2_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ozaki2_last_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
@@ -88,6 +96,7 @@ _SIGS = {
     "ozaki2_dgemm_bwd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                     C.c_void_p, C.c_int64, C.c_void_p]),
     "ozaki2_cache_destroy": (C.c_int, [C.c_void_p]),
+    "ozaki2_probe_mma_s8": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
 }
 
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -138,6 +139,17 @@ static int ceil_log2(int64_t k) {
   return c;
 }
 
+// Allocation failures injected on the host by ozaki2_debug_inject_alloc_failure:
+// the next `count` library allocations (host plan construction, device tables,
+// launch images) report OZ2_ENOMEM without allocating.
+static std::atomic<int> g_inject_alloc{0};
+static bool injected_alloc_failure() {
+  int c = g_inject_alloc.load();
+  while (c > 0)
+    if (g_inject_alloc.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
@@ -149,6 +161,15 @@ struct CrtHost {
   // B[j][2l+1] = M_l[j-1], M_l[j] the 7-bit pieces of M_l
   int kpad = 0, npad = 0, np = 0, rows = 0;   // rows: table rows allocated (>= npad)
   std::vector<uint16_t> tc_table;
+};
+
+// One group of consecutive moduli whose residue planes are computed and
+// multiplied together when a product streams its planes through a bounded
+// workspace (the moduli are independent, Sec. 2.3; the paper runs them as
+// separate plane GEMMs, Sec. 5.1).
+struct GroupHost {
+  int l0, L, L1, G;                       // first modulus, moduli, one-limb moduli, planes
+  int res_npad, res_cw, res_nchunk, res_nabuf, res_key;
 };
 
 struct ProbHost {
@@ -165,12 +186,15 @@ struct ProbHost {
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient estimates [upitch] uint32
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_nabuf;           // res_mode 2: chunk width, chunks, byte buffers
+  int nb;                                      // bytes of a (t+1)-bit integer
+  std::vector<GroupHost> groups;               // non-empty: planes streamed in these groups
 };
 
 // Tensor-core residue table [npad][kpad] (bf16 bits): row l (one-limb) =
 // cen(2^(8 b) mod m_l); rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
 // base-128 halves of cen(2^(8 b) mod m_l).
 struct ResTable {
+  int l0 = 0;                // first modulus (index in the list)
   int L, kpad, npad, rows;   // rows: allocated (npad, or whole chunks of the warp-specialised kernel)
   std::vector<uint16_t> bits;
 };
@@ -180,7 +204,16 @@ struct ListRef {
   int n = 0;
   int smem = 0;      // dynamic shared memory of the launch
   int lmax = 0;      // largest modulus count among its problems
+  int na = 0;        // single-problem plans: leading entries of side A (the rest are side B)
 };
+
+// Entries of a block list (int4, side in bit 0 of .y) that belong to side A:
+// the leading run (single-problem lists hold side A's blocks first).
+static int side_a_prefix(const std::vector<int4>& v) {
+  int n = 0;
+  while (n < (int)v.size() && (v[n].y & 1) == 0) ++n;
+  return n;
+}
 
 struct PlainSeg {
   int cta_off, grid;
@@ -217,6 +250,15 @@ struct DevState {
   int rtt_npad = 0;
   std::vector<void*> res_tab;   // per problem: device address of its residue table
   std::vector<void*> crt_tab;   // per problem: device address of its tensor-core CRT table
+  // streamed planes (single problems): per modulus group, the tables of its
+  // launches (modulus constants and digit tables from its first modulus on,
+  // its own GEMM schedule) and the device address of its residue table
+  struct Group {
+    DevTables tab{};
+    int grid = 0;
+    void* res_tab = nullptr;
+  };
+  std::vector<Group> groups;
 };
 
 static void free_launch_block(LaunchBlock& lb) {
@@ -242,7 +284,16 @@ struct ozaki2_plan_s {
   // stage boundaries: scan, residues, GEMM, CRT, end; [5] between the
   // tensor-core CRT sums and the rest of the CRT stage
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> evg;   // streamed planes: before each group's residues and before its GEMM
   bool timed = false;
+  bool no_stream = false;         // internal plans whose planes must all stay resident
+  uint32_t spin_limit = oz2::kDefaultSpinLimit;   // polls of a bounded device-side wait
+  bool tile2 = false;             // plane GEMMs on CTA pairs (256 x 256 tiles)
+  // operand reuse: the last product of a single-problem plan and its workspace,
+  // whose row exponents and planes of A (or column exponents and planes of B)
+  // a later ozaki2_execute_reuse keeps
+  void* last_ws = nullptr;
+  ozaki2_problem last_q{};
 };
 
 struct ozaki2_graph_s {
@@ -255,15 +306,60 @@ namespace oz2 {
 
 cudaError_t init_prep_attributes();
 cudaError_t init_gemm_attributes();
+cudaError_t init_gemm2_attributes();
 cudaError_t init_crt_attributes();
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Tensor-core residue table [rows][kpad] (bf16 bits) of the moduli
+// l0 .. l0 + L - 1 of the list (L1 of them one-limb): row l (one-limb) =
+// cen(2^(8 b) mod m), rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
+// base-128 halves of cen(2^(8 b) mod m).  Shared by problems and modulus
+// groups with the same moduli and geometry; returns its index in pl->rtabs.
+static int res_table_key(ozaki2_plan_s* pl, int l0, int L, int L1, int nb, int kpad, int npad, int rows) {
+  for (size_t i = 0; i < pl->rtabs.size(); ++i) {
+    const ResTable& r = pl->rtabs[i];
+    if (r.l0 == l0 && r.L == L && r.kpad == kpad && r.rows == rows) return (int)i;
+  }
+  ResTable rt;
+  rt.l0 = l0; rt.L = L; rt.kpad = kpad; rt.npad = npad; rt.rows = rows;
+  rt.bits.assign((size_t)rows * kpad, 0);
+  auto bf = [](int x) -> uint16_t {   // exact for |x| <= 256
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+  };
+  const auto& mlist = modulus_list();
+  for (int l = 0; l < L; ++l) {
+    const int m = (int)mlist[l0 + l];
+    int64_t pw = 1 % m;                          // 2^(8 b) mod m
+    for (int b = 0; b < nb; ++b) {
+      int c = (int)pw;
+      if (2 * c > m) c -= m;                     // centered
+      if (l < L1) {
+        rt.bits[(size_t)l * kpad + b] = bf(c);
+      } else {
+        int y = c & 127;
+        const int lo = y > 64 ? y - 128 : y;
+        const int hi = (c - lo) / 128;
+        const int r0 = L1 + 2 * (l - L1);
+        rt.bits[(size_t)r0 * kpad + b] = bf(lo);
+        rt.bits[(size_t)(r0 + 1) * kpad + b] = bf(hi);
+      }
+      pw = (pw << 8) % m;
+    }
+  }
+  pl->rtabs.push_back(std::move(rt));
+  return (int)pl->rtabs.size() - 1;
+}
 
 static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int p,
                          const PlanExtra* ex = nullptr) {
   const ozaki2_opts& o = pl->opts;
   const PlanExtra none{};
   if (!ex) ex = &none;
+  if (injected_alloc_failure()) throw std::bad_alloc();
   if (M <= 0 || N <= 0 || K <= 0 || p < 2) return OZ2_EINVAL;
   if (K > kMaxK || p > kMaxP) return OZ2_ERANGE;
   if (M > 65535LL * kBM || N > 65535LL * kBN) return OZ2_ERANGE;
@@ -299,7 +395,8 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
   if (h.crt_cls < 0) return OZ2_ERANGE;
   h.DS = crt_class_digits(h.crt_cls);
   h.Kp = (int)align_up((size_t)K, 8);
-  h.tiles_m = (int)((M + kBM - 1) / kBM);
+  const int tile_rows = pl->tile2 ? 2 * kBM : kBM;     // rows of a plane GEMM output tile
+  h.tiles_m = (int)((M + tile_rows - 1) / tile_rows);
   h.tiles_n = (int)((N + kBN - 1) / kBN);
   const int kc = o.k_chunk > 0 ? o.k_chunk : kMaxKChunk;
   if (kc % kBK != 0 || kc > kMaxKChunk) return OZ2_EINVAL;
@@ -418,6 +515,7 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
   {
     // tensor-core residues (byte GEMM); opt-in through opts.res_engine
     const int nb = (h.t + 1 + 7) / 8;
+    h.nb = nb;
     const int kpad = (int)align_up((size_t)nb, 64);
     const int npad = (int)align_up((size_t)(h.L1 + 2 * (L - h.L1)), 16);
     h.res_mode = (o.res_engine == 1 && kpad <= 256 && npad <= 256 &&
@@ -438,44 +536,7 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
       h.res_nchunk = (npad + h.res_cw - 1) / h.res_cw;
     }
     const int rows = h.res_mode == 2 ? h.res_cw * h.res_nchunk : npad;
-    h.res_key = -1;
-    if (h.res_mode) {
-      for (size_t i = 0; i < pl->rtabs.size(); ++i)
-        if (pl->rtabs[i].L == L && pl->rtabs[i].kpad == kpad && pl->rtabs[i].rows == rows) h.res_key = (int)i;
-      if (h.res_key < 0) {
-        ResTable rt;
-        rt.L = L; rt.kpad = kpad; rt.npad = npad; rt.rows = rows;
-        rt.bits.assign((size_t)rows * kpad, 0);
-        auto bf = [](int x) -> uint16_t {   // exact for |x| <= 256
-          float f = (float)x;
-          uint32_t u;
-          std::memcpy(&u, &f, 4);
-          return (uint16_t)(u >> 16);
-        };
-        const auto& mlist = modulus_list();
-        for (int l = 0; l < L; ++l) {
-          const int m = (int)mlist[l];
-          int64_t pw = 1 % m;                          // 2^(8 b) mod m
-          for (int b = 0; b < nb; ++b) {
-            int c = (int)pw;
-            if (2 * c > m) c -= m;                     // centered
-            if (l < h.L1) {
-              rt.bits[(size_t)l * kpad + b] = bf(c);
-            } else {
-              int y = c & 127;
-              const int lo = y > 64 ? y - 128 : y;
-              const int hi = (c - lo) / 128;
-              const int r0 = h.L1 + 2 * (l - h.L1);
-              rt.bits[(size_t)r0 * kpad + b] = bf(lo);
-              rt.bits[(size_t)(r0 + 1) * kpad + b] = bf(hi);
-            }
-            pw = (pw << 8) % m;
-          }
-        }
-        pl->rtabs.push_back(std::move(rt));
-        h.res_key = (int)pl->rtabs.size() - 1;
-      }
-    }
+    h.res_key = h.res_mode ? res_table_key(pl, 0, L, h.L1, nb, kpad, npad, rows) : -1;
   }
   pl->probs.push_back(h);
   pl->lmax = std::max(pl->lmax, L);
@@ -485,14 +546,93 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
   return OZ2_OK;
 }
 
+// Bytes of bf16 plane stacks (A and B) above which a single product streams
+// its planes in groups of moduli when opts.plane_group is 0.
+constexpr size_t kAutoPlaneBudget = (size_t)32 << 30;
+
+// Split the moduli of a single-product plan into as few groups of
+// consecutive moduli with at most gmax planes each as the plane counts allow,
+// of about equal size (a group that holds two-limb moduli holds an even number
+// of one-limb ones), so that only one group's residue planes live in the
+// workspace at a time.
+static int plan_groups(ozaki2_plan_s* pl) {
+  if (pl->probs.size() != 1 || pl->no_stream) return OZ2_OK;
+  ProbHost& h = pl->probs[0];
+  h.groups.clear();
+  const ozaki2_opts& o = pl->opts;
+  if (o.plane_group < 0) return OZ2_OK;
+  const size_t per_plane = 2 * (size_t)(h.M + h.N) * (size_t)h.Kp;
+  int gmax = o.plane_group;
+  if (gmax == 0) {
+    if (per_plane * (size_t)h.G <= kAutoPlaneBudget) return OZ2_OK;
+    gmax = (int)std::max<size_t>(3, kAutoPlaneBudget / per_plane);
+  }
+  if (o.engine != OZ2_ENGINE_TC || o.schedule != OZ2_SCHED_GROUPED) {
+    return o.plane_group > 0 ? OZ2_EINVAL : OZ2_OK;   // streaming runs the grouped tensor-core GEMM
+  }
+  if (gmax >= h.G) return OZ2_OK;
+  const int ng = (h.G + gmax - 1) / gmax;
+  const auto& ml = modulus_list();
+  // greedy groups with at most `cap` planes each; the smallest cap from
+  // ceil(G / ng) up to gmax that gives ng groups (the 3-plane two-limb moduli
+  // can leave a small last group at the even split)
+  auto split = [&](int cap, std::vector<GroupHost>& out) {
+    out.clear();
+    int l = 0;
+    while (l < h.L) {
+      GroupHost gr{};
+      gr.l0 = l;
+      while (l < h.L) {
+        const int planes = ml[l] <= 255 ? 1 : 3;
+        if (gr.G > 0 && gr.G + planes > cap) break;
+        // the tensor-core residue epilogue takes two-limb pairs at even table
+        // columns: a group with two-limb moduli holds an even number of one-limb ones
+        if (planes == 3 && (gr.L1 & 1)) break;
+        gr.G += planes;
+        gr.L1 += planes == 1;
+        ++gr.L;
+        ++l;
+      }
+      out.push_back(gr);
+    }
+  };
+  std::vector<GroupHost> groups;
+  for (int cap = (h.G + ng - 1) / ng; cap <= gmax; ++cap) {
+    split(cap, groups);
+    if ((int)groups.size() <= ng) break;
+  }
+  for (GroupHost& gr : groups) {
+    gr.res_npad = (int)align_up((size_t)(gr.L1 + 2 * (gr.L - gr.L1)), 16);
+    gr.res_cw = gr.res_nchunk = gr.res_nabuf = 0;
+    gr.res_key = -1;
+    if (h.res_mode == 2) {
+      residue_mm_geometry(h.res_kpad, gr.res_npad, &gr.res_cw, &gr.res_nabuf);
+      gr.res_nchunk = (gr.res_npad + gr.res_cw - 1) / gr.res_cw;
+    }
+    if (h.res_mode != 0) {
+      const int rows = h.res_mode == 2 ? gr.res_cw * gr.res_nchunk : gr.res_npad;
+      gr.res_key = res_table_key(pl, gr.l0, gr.L, gr.L1, h.nb, h.res_kpad, gr.res_npad, rows);
+    }
+  }
+  if (groups.size() > 1) h.groups = std::move(groups);
+  return OZ2_OK;
+}
+
+static int group_planes_max(const ProbHost& h) {
+  int g = 0;
+  for (const GroupHost& gr : h.groups) g = std::max(g, gr.G);
+  return h.groups.empty() ? h.G : g;
+}
+
 static void layout_workspace(ozaki2_plan_s* pl) {
   size_t off = 0;
   for (auto& h : pl->probs) { h.off_e = off; off += align_up(4 * (size_t)h.M, 256); }
   for (auto& h : pl->probs) { h.off_f = off; off += align_up(4 * (size_t)h.N, 256); }
   pl->ef_bytes = off;
   for (auto& h : pl->probs) {
-    h.off_pa = off; off += align_up(2 * (size_t)h.G * h.M * h.Kp, 256);
-    h.off_pb = off; off += align_up(2 * (size_t)h.G * h.N * h.Kp, 256);
+    const int gp = group_planes_max(h);   // planes resident at a time
+    h.off_pa = off; off += align_up(2 * (size_t)gp * h.M * h.Kp, 256);
+    h.off_pb = off; off += align_up(2 * (size_t)gp * h.N * h.Kp, 256);
     h.off_u = off; off += align_up(2 * (size_t)h.L * align_up((size_t)(h.M * h.N), 8), 256);
     h.off_q = h.off_sig = off;
     if (h.crt_mode == 2) {
@@ -514,10 +654,12 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
       (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
-      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 3)) {
+      (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 3) ||
+      o.plane_group < -1 || (o.plane_group > 0 && o.plane_group < 3) || o.gemm_tile < 0 || o.gemm_tile > 2) {
     delete pl;
     return OZ2_EINVAL;
   }
+  pl->tile2 = o.engine == OZ2_ENGINE_TC && o.gemm_tile == 2;
   *res = pl;
   return OZ2_OK;
 }
@@ -573,6 +715,10 @@ struct TableImage {
   size_t o_rtt = 0;                 // tensor-core residue tile list
   int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
   std::vector<size_t> o_rtab;
+  int na_srows = 0, na_res[6] = {0}, na_rtt = 0;   // side-A prefixes of the lists
+  std::vector<int> na_rmt;
+  size_t o_ctas = 0;                // per-group CTA unit ranges (streamed planes)
+  std::vector<std::array<int, 2>> grp;   // {offset into the range array, grid} per group
 };
 
 // Host side of the device upload: modulus constants, residue digit tables,
@@ -646,7 +792,10 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     }
   }
   const int nunits = (int)units.size();
-  const int grid = std::max(1, std::min(pl->opts.grid > 0 ? pl->opts.grid : d.sms, nunits));
+  // scheduling slots: persistent CTAs, or CTA pairs for the 256 x 256 tiles
+  const int want = pl->opts.grid > 0 ? pl->opts.grid : d.sms;
+  const int slots = pl->tile2 ? std::max(1, want / 2) : want;
+  const int grid = std::max(1, std::min(slots, nunits));
   // greedy list scheduling: every unit, in (problem, modulus, tile) order, goes
   // to the least-loaded CTA; the cost of a unit is its accumulation jobs times
   // (K blocks per job + a fixed epilogue share)
@@ -681,13 +830,48 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   d.plain.clear();
   for (auto& sg : seg) {
     const int first = sg.first, cnt = sg.second;
-    const int g = std::max(1, std::min(cnt, d.sms));
+    const int g = std::max(1, std::min(cnt, pl->tile2 ? d.sms / 2 : d.sms));
     d.plain.push_back(PlainSeg{(int)cta_p.size(), g});
     for (int c = 0; c < g; ++c) {
       cta_p.push_back((int)ordered.size());
       for (int u = c; u < cnt; u += g) ordered.push_back(units[first + u]);
     }
     cta_p.push_back((int)ordered.size());
+  }
+
+  // streamed planes: one grouped GEMM schedule per modulus group of the
+  // (single) problem, with group-local modulus indices, appended to `ordered`
+  std::vector<int32_t> cta_s;
+  ti.grp.clear();
+  if (count == 1) {
+    const ProbHost& h = pl->probs[0];
+    for (const GroupHost& gr : h.groups) {
+      std::vector<Unit> gu;
+      for (int l = 0; l < gr.L; ++l)
+        for (int tm = 0; tm < h.tiles_m; ++tm)
+          for (int tn = 0; tn < h.tiles_n; ++tn)
+            gu.push_back(Unit{0, (uint16_t)l, (uint16_t)tm, (uint16_t)tn});
+      const int gg = std::max(1, std::min(slots, (int)gu.size()));
+      std::vector<std::vector<int>> gl(gg);
+      using Load = std::pair<int64_t, int>;
+      std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+      for (int c = 0; c < gg; ++c) heap.push(Load(0, c));
+      const int64_t kblocks = (std::min<int64_t>(h.K, h.kchunk) + kBK - 1) / kBK;
+      for (int u = 0; u < (int)gu.size(); ++u) {
+        const int planes = gu[u].ell < gr.L1 ? 1 : 3;
+        Load top = heap.top();
+        heap.pop();
+        gl[top.second].push_back(u);
+        top.first += (int64_t)planes * h.nchunks * (kblocks + 4);
+        heap.push(top);
+      }
+      ti.grp.push_back({(int)cta_s.size(), gg});
+      for (int c = 0; c < gg; ++c) {
+        cta_s.push_back((int)ordered.size());
+        for (int u : gl[c]) ordered.push_back(gu[u]);
+      }
+      cta_s.push_back((int)ordered.size());
+    }
   }
 
   // block lists
@@ -781,8 +965,12 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.o_ordered = ti.b.add(ordered.data(), ordered.size() * sizeof(Unit));
   ti.o_ctag = ti.b.add(cta_g.data(), cta_g.size() * 4);
   ti.o_ctap = ti.b.add(cta_p.data(), cta_p.size() * 4);
+  ti.o_ctas = ti.b.add(cta_s.data(), cta_s.size() * 4);
   // one launch scans rows and columns: the column blocks follow the row blocks
   scan_rows.insert(scan_rows.end(), scan_cols.begin(), scan_cols.end());
+  ti.na_srows = side_a_prefix(scan_rows);
+  for (int i = 0; i < 6; ++i) ti.na_res[i] = side_a_prefix(res[i]);
+  ti.na_rtt = side_a_prefix(rtt);
   scan_cols.clear();
   ti.o_srows = ti.b.add(scan_rows.data(), scan_rows.size() * 16);
   ti.o_scols = ti.b.add(scan_cols.data(), scan_cols.size() * 16);
@@ -811,9 +999,11 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     ti.cmt_seg.push_back({(int)cmt.size(), (int)kv.second.size(), kv.first[1]});
     cmt.insert(cmt.end(), kv.second.begin(), kv.second.end());
   }
+  ti.na_rmt.clear();
   for (const auto& kv : rmt_by) {
     if (residue_mm_smem_bytes(kv.first[1], pl->lmax, 512, nullptr) < 0) return OZ2_EINTERNAL;
     ti.rmt_seg.push_back({(int)rmt.size(), (int)kv.second.size(), kv.first[1]});
+    ti.na_rmt.push_back(side_a_prefix(kv.second));
     rmt.insert(rmt.end(), kv.second.begin(), kv.second.end());
   }
   if (!finl.empty() && 3 * ti.finl_dmax * 4 + (ti.finl_dmax + 2 * ti.finl_gmax) * 128 * 4 > 200 * 1024)
@@ -852,6 +1042,7 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   DevState& d = pl->dev;
   const int count = (int)pl->probs.size();
   d.tab = DevTables{};
+  d.tab.spin_limit = pl->spin_limit;
   d.tab.mods = reinterpret_cast<const ModConst*>(base + ti.o_mods);
   d.tab.t16 = reinterpret_cast<const uint32_t*>(base + ti.o_t16);
   d.tab.w16max = pl->w16max;
@@ -865,12 +1056,12 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   d.grid = ti.grid;
   d.cta_grouped = reinterpret_cast<const int32_t*>(base + ti.o_ctag);
   d.cta_plain = reinterpret_cast<const int32_t*>(base + ti.o_ctap);
-  d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_srows), ti.n_srows, 0, 0};
+  d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_srows), ti.n_srows, 0, 0, ti.na_srows};
   d.scan_cols = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_scols), ti.n_scols, 0, 0};
   d.simt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_simt), ti.n_simt, 0, 0};
   for (int i = 0; i < 6; ++i)
     d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_res[i]), ti.n_res[i],
-                       ti.res_l[i] * (residue_class_w16(i) + 4) * 4, ti.res_l[i]};
+                       ti.res_l[i] * (residue_class_w16(i) + 4) * 4, ti.res_l[i], ti.na_res[i]};
   for (int i = 0; i < 9; ++i) {
     d.tct[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_tct[i]), ti.n_tct[i], ti.tct_kpad[i], ti.tct_l[i]};
     d.tct_npad[i] = ti.tct_npad[i];
@@ -880,10 +1071,13 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     d.cmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt) + 4 * sg[0], sg[1], sg[2], 0});
   d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
   for (int c = 0; c < 9; ++c) d.fsh[c] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_fsh[c]), ti.n_fsh[c], 0, 0};
-  d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l};
+  d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l, ti.na_rtt};
   d.rmt.clear();
-  for (const auto& sg : ti.rmt_seg)
-    d.rmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rmt) + 4 * sg[0], sg[1], sg[2], 512});
+  for (size_t i = 0; i < ti.rmt_seg.size(); ++i) {
+    const auto& sg = ti.rmt_seg[i];
+    d.rmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rmt) + 4 * sg[0], sg[1], sg[2], 512,
+                            ti.na_rmt[i]});
+  }
   d.rtt_npad = ti.rtt_npad;
   d.res_tab.assign(pl->probs.size(), nullptr);
   for (size_t i = 0; i < pl->probs.size(); ++i)
@@ -893,6 +1087,23 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
     if (pl->probs[i].crt_mode != 0) d.crt_tab[i] = base + ti.o_tctab[pl->probs[i].crt_key];
   for (int i = 0; i < kCrtClassCount; ++i)
     d.crt[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_crt[i]), ti.n_crt[i], 0, ti.crt_l[i]};
+  d.groups.clear();
+  if (count == 1) {
+    const ProbHost& h = pl->probs[0];
+    for (size_t g = 0; g < h.groups.size(); ++g) {
+      const GroupHost& gr = h.groups[g];
+      DevState::Group dg;
+      dg.tab = d.tab;
+      dg.tab.mods = d.tab.mods + gr.l0;                                // group-local modulus index
+      dg.tab.t16 = d.tab.t16 + (size_t)gr.l0 * pl->w16max;
+      dg.tab.lmax = gr.L;
+      dg.tab.cta_begin = reinterpret_cast<const int32_t*>(base + ti.o_ctas) + ti.grp[g][0];
+      dg.tab.count = 1;
+      dg.grid = ti.grp[g][1];
+      dg.res_tab = gr.res_key >= 0 ? base + ti.o_rtab[gr.res_key] : nullptr;
+      d.groups.push_back(dg);
+    }
+  }
 }
 
 static int upload(ozaki2_plan_s* pl) {
@@ -903,7 +1114,7 @@ static int upload(ozaki2_plan_s* pl) {
   int major = 0;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return OZ2_ENODEV;
   if (major != 10) return OZ2_ENODEV;
-  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
+  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess || init_gemm2_attributes() != cudaSuccess ||
       init_crt_attributes() != cudaSuccess)
     return OZ2_ECUDA;
   if (!get_encode()) return OZ2_ECUDA;
@@ -913,7 +1124,7 @@ static int upload(ozaki2_plan_s* pl) {
   int rc = build_table_image(pl, sms, ti);
   if (rc) return rc;
   void* mem = nullptr;
-  if (cudaMalloc(&mem, ti.b.img.size()) != cudaSuccess) return OZ2_ENOMEM;
+  if (injected_alloc_failure() || cudaMalloc(&mem, ti.b.img.size()) != cudaSuccess) return OZ2_ENOMEM;
   if (cudaMemcpy(mem, ti.b.img.data(), ti.b.img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(mem);
     return OZ2_ECUDA;
@@ -924,18 +1135,37 @@ static int upload(ozaki2_plan_s* pl) {
   if (pl->opts.timing) {
     for (auto& e : pl->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return OZ2_ECUDA;
+    pl->evg.assign(2 * d.groups.size(), nullptr);
+    for (auto& e : pl->evg)
+      if (cudaEventCreate(&e) != cudaSuccess) return OZ2_ECUDA;
   }
   return OZ2_OK;
 }
 
-static int alloc_launch_block(LaunchBlock& lb, int count) {
-  const size_t probs_bytes = align_up(sizeof(ProbDev) * count, 128);
+// Descriptor slots of a launch image: one per problem, then one per modulus
+// group of a single product whose planes are streamed.
+static int launch_slots(const ozaki2_plan_s* pl) {
+  const int count = (int)pl->probs.size();
+  return count + (count == 1 ? (int)pl->probs[0].groups.size() : 0);
+}
+
+static int alloc_launch_block(LaunchBlock& lb, int slots) {
+  const size_t probs_bytes = align_up(sizeof(ProbDev) * slots, 128);
   lb.tmap_off = probs_bytes;
-  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 5 * count;   // A planes, B planes, CRT table, u tiles, residue table
-  if (cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) { lb.d_mem = nullptr; return OZ2_ENOMEM; }
-  if (cudaMallocHost(&lb.h_stage, lb.bytes) != cudaSuccess) { lb.h_stage = nullptr; return OZ2_ENOMEM; }
-  if (cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming) != cudaSuccess) return OZ2_ECUDA;
-  return OZ2_OK;
+  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 5 * slots;   // A planes, B planes, CRT table, u tiles, residue table
+  int rc = OZ2_OK;
+  if (injected_alloc_failure() || cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) {
+    lb.d_mem = nullptr;
+    rc = OZ2_ENOMEM;
+  } else if (cudaMallocHost(&lb.h_stage, lb.bytes) != cudaSuccess) {
+    lb.h_stage = nullptr;
+    rc = OZ2_ENOMEM;
+  } else if (cudaEventCreateWithFlags(&lb.copied, cudaEventDisableTiming) != cudaSuccess) {
+    lb.copied = nullptr;
+    rc = OZ2_ECUDA;
+  }
+  if (rc) free_launch_block(lb);   // nothing half-made is kept: the next execute starts over
+  return rc;
 }
 
 static bool mat_ok(const ozaki2_mat& m, int64_t rows, int64_t cols) {
@@ -1022,7 +1252,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_nvbuf = h.crt_nvbuf;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);
     if (rc) return rc;
-    rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, kBN);
+    rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, pl->tile2 ? kBN / 2 : kBN);
     if (rc) return rc;
     if (h.crt_mode != 0) {
       // mode 1: the whole table in K blocks; mode 2: K block x cw columns of
@@ -1046,6 +1276,38 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
         return OZ2_ECUDA;
     }
   }
+  // streamed planes: one descriptor per modulus group (moduli, planes and
+  // residue geometry of the group; v_l and M_l^{-1} addressed from its first
+  // modulus on), with its own plane and residue-table tensor maps
+  if (count == 1) {
+    const ProbHost& h = pl->probs[0];
+    for (size_t g = 0; g < h.groups.size(); ++g) {
+      const GroupHost& gr = h.groups[g];
+      ProbDev& Q = pd[count + g];
+      Q = pd[0];
+      Q.L = gr.L; Q.L1 = gr.L1; Q.G = gr.G;
+      Q.u = pd[0].u + (int64_t)gr.l0 * pd[0].upitch;
+      Q.crt_off = pd[0].crt_off + gr.l0;
+      Q.res_npad = gr.res_npad; Q.res_cw = gr.res_cw; Q.res_nchunk = gr.res_nchunk; Q.res_nabuf = gr.res_nabuf;
+      Q.dbg_chat = nullptr;
+      CUtensorMap* gm = tm + 5 * count + 5 * g;
+      int rc = encode_planes(&gm[0], Q.pa, h.K, h.M, h.Kp, gr.G, kBM);
+      if (rc) return rc;
+      rc = encode_planes(&gm[1], Q.pb, h.K, h.N, h.Kp, gr.G, pl->tile2 ? kBN / 2 : kBN);
+      if (rc) return rc;
+      if (h.res_mode != 0) {
+        const int rows = pl->rtabs[gr.res_key].rows;
+        const cuuint64_t dims[2] = {(cuuint64_t)h.res_kpad, (cuuint64_t)rows};
+        const cuuint64_t strides[1] = {(cuuint64_t)h.res_kpad * 2};
+        const cuuint32_t box[2] = {64u, (cuuint32_t)(h.res_mode == 1 ? gr.res_npad : gr.res_cw)};
+        const cuuint32_t es[2] = {1u, 1u};
+        if (get_encode()(&gm[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.groups[g].res_tab, dims, strides,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+          return OZ2_ECUDA;
+      }
+    }
+  }
   return OZ2_OK;
 }
 
@@ -1066,38 +1328,75 @@ static int stage_image(LaunchBlock& lb, const std::vector<uint8_t>& img, cudaStr
   } while (0)
 
 // Enqueue the five stages on `s` using launch block `lb` (already staged).
-static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t s, bool timing) {
+// keep = 0 (1): the workspace already holds the row exponents and planes of A
+// (column exponents and planes of B) of this single-problem plan; only the
+// other side is scanned and reduced.
+static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t s, bool timing, int keep = -1) {
   DevState& d = pl->dev;
+  // the part of a block list that runs: every entry, or one side's
+  auto part_ptr = [&](const ListRef& r) { return keep == 0 ? r.ptr + 4 * r.na : r.ptr; };
+  auto part_n = [&](const ListRef& r) { return keep == 0 ? r.n - r.na : (keep == 1 ? r.na : r.n); };
   DevTables tab = d.tab;
+  tab.spin_limit = pl->spin_limit;
   tab.probs = reinterpret_cast<const ProbDev*>(lb.d_mem);
   tab.tmaps = reinterpret_cast<const CUtensorMap*>(static_cast<uint8_t*>(lb.d_mem) + lb.tmap_off);
   const int count = (int)pl->probs.size();
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[0], s));
-  OZ2_CU(cudaMemsetAsync(ws, 0x80, pl->ef_bytes, s));   // exponent sentinel below every valid exponent
+  if (keep < 0) {
+    OZ2_CU(cudaMemsetAsync(ws, 0x80, pl->ef_bytes, s));   // exponent sentinel below every valid exponent
+  } else {
+    const ProbHost& h = pl->probs[0];                     // only the side that is recomputed
+    if (keep == 0) OZ2_CU(cudaMemsetAsync(ws + h.off_f, 0x80, 4 * (size_t)h.N, s));
+    else OZ2_CU(cudaMemsetAsync(ws + h.off_e, 0x80, 4 * (size_t)h.M, s));
+  }
   for (const ProbHost& h : pl->probs) {
     // a side whose planes the caller supplies is used unscaled: exponent 0
     if (h.skip_a) OZ2_CU(cudaMemsetAsync(ws + h.off_e, 0, 4 * (size_t)h.M, s));
     if (h.skip_b) OZ2_CU(cudaMemsetAsync(ws + h.off_f, 0, 4 * (size_t)h.N, s));
   }
-  OZ2_CU(launch_scan(tab, count, d.scan_rows.ptr, d.scan_cols.ptr, d.scan_rows.n, d.scan_cols.n, s));
+  OZ2_CU(launch_scan(tab, count, part_ptr(d.scan_rows), d.scan_cols.ptr, part_n(d.scan_rows), d.scan_cols.n, s));
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[1], s));
-  for (int c = 0; c < 6; ++c)
-    if (d.res[c].n) OZ2_CU(launch_residues(tab, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
-  if (d.rtt.n)
-    OZ2_CU(launch_residues_tc(tab, d.rtt.ptr, d.rtt.n, d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
-  for (const ListRef& r : d.rmt) OZ2_CU(launch_residues_mm(tab, r.ptr, r.n, r.smem, r.lmax, d.sms, s));
-  if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
-  if (pl->opts.engine == OZ2_ENGINE_SIMT) {
-    DevTables t2 = tab;
-    t2.units = d.unsorted;
-    OZ2_CU(launch_gemm_simt(t2, d.simt.ptr, d.simt.n, s));
-  } else if (pl->opts.schedule == OZ2_SCHED_GROUPED) {
-    OZ2_CU(launch_gemm_tc(tab, d.grid, s));
+  if (!d.groups.empty()) {
+    // streamed planes: each modulus group's residues, then its plane GEMMs,
+    // through the same plane regions of the workspace (stream order keeps a
+    // group's planes until its GEMMs have read them)
+    const ProbHost& h = pl->probs[0];
+    auto* pd = reinterpret_cast<const ProbDev*>(lb.d_mem);
+    auto* tmp = reinterpret_cast<const CUtensorMap*>(static_cast<uint8_t*>(lb.d_mem) + lb.tmap_off);
+    for (size_t g = 0; g < d.groups.size(); ++g) {
+      const GroupHost& gr = h.groups[g];
+      DevTables gt = d.groups[g].tab;
+      gt.spin_limit = pl->spin_limit;
+      gt.probs = pd + count + g;
+      gt.tmaps = tmp + 5 * count + 5 * g;
+      if (timing) OZ2_CU(cudaEventRecord(pl->evg[2 * g], s));
+      for (int c = 0; c < 6; ++c)
+        if (d.res[c].n) OZ2_CU(launch_residues(gt, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
+      if (d.rtt.n) OZ2_CU(launch_residues_tc(gt, d.rtt.ptr, d.rtt.n, d.rtt.smem, gr.res_npad, gr.L, d.sms, s));
+      for (const ListRef& r : d.rmt) OZ2_CU(launch_residues_mm(gt, r.ptr, r.n, gr.res_cw, r.lmax, d.sms, s));
+      if (timing) OZ2_CU(cudaEventRecord(pl->evg[2 * g + 1], s));
+      OZ2_CU(pl->tile2 ? launch_gemm_tc2(gt, d.groups[g].grid, s) : launch_gemm_tc(gt, d.groups[g].grid, s));
+    }
   } else {
-    for (const PlainSeg& sg : d.plain) {
+    for (int c = 0; c < 6; ++c)
+      if (part_n(d.res[c])) OZ2_CU(launch_residues(tab, c, part_ptr(d.res[c]), part_n(d.res[c]), d.res[c].smem, s));
+    if (part_n(d.rtt))
+      OZ2_CU(launch_residues_tc(tab, part_ptr(d.rtt), part_n(d.rtt), d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
+    for (const ListRef& r : d.rmt)
+      if (part_n(r)) OZ2_CU(launch_residues_mm(tab, part_ptr(r), part_n(r), r.smem, r.lmax, d.sms, s));
+    if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
+    if (pl->opts.engine == OZ2_ENGINE_SIMT) {
       DevTables t2 = tab;
-      t2.cta_begin = d.cta_plain + sg.cta_off;
-      OZ2_CU(launch_gemm_tc(t2, sg.grid, s));
+      t2.units = d.unsorted;
+      OZ2_CU(launch_gemm_simt(t2, d.simt.ptr, d.simt.n, s));
+    } else if (pl->opts.schedule == OZ2_SCHED_GROUPED) {
+      OZ2_CU(pl->tile2 ? launch_gemm_tc2(tab, d.grid, s) : launch_gemm_tc(tab, d.grid, s));
+    } else {
+      for (const PlainSeg& sg : d.plain) {
+        DevTables t2 = tab;
+        t2.cta_begin = d.cta_plain + sg.cta_off;
+        OZ2_CU(pl->tile2 ? launch_gemm_tc2(t2, sg.grid, s) : launch_gemm_tc(t2, sg.grid, s));
+      }
     }
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
@@ -1117,20 +1416,26 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
 }
 
 static int execute_impl(ozaki2_plan_s* pl, int count, const ozaki2_problem* probs, void* ws,
-                        size_t ws_bytes, cudaStream_t s) {
+                        size_t ws_bytes, cudaStream_t s, int keep = -1) {
   if (!pl || !probs || !ws) return OZ2_EINVAL;
   if (count != (int)pl->probs.size()) return OZ2_EINVAL;
   if (ws_bytes < pl->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZ2_EINVAL;
+  if (keep >= 0 && (count != 1 || !pl->probs[0].groups.empty() || pl->last_ws != ws)) return OZ2_EINVAL;
   int rc = upload(pl);
   if (rc) return rc;
-  if (!pl->lb.d_mem && (rc = alloc_launch_block(pl->lb, count))) return rc;
+  if (!pl->lb.d_mem && (rc = alloc_launch_block(pl->lb, launch_slots(pl)))) return rc;
   std::vector<uint8_t> img;
   rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, pl->lb.tmap_off, pl->lb.bytes);
   if (rc) return rc;
   rc = stage_image(pl->lb, img, s);
   if (rc) return rc;
   pl->timed = pl->opts.timing != 0;
-  return enqueue(pl, pl->lb, static_cast<uint8_t*>(ws), s, pl->timed);
+  rc = enqueue(pl, pl->lb, static_cast<uint8_t*>(ws), s, pl->timed, keep);
+  if (count == 1) {
+    pl->last_ws = rc ? nullptr : ws;
+    pl->last_q = probs[0];
+  }
+  return rc;
 }
 
 int plan_create_ex(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts,
@@ -1140,6 +1445,7 @@ int plan_create_ex(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* op
   ozaki2_plan_s* pl = nullptr;
   int rc = new_plan(opts, &pl);
   if (rc) return rc;
+  pl->no_stream = true;                          // the binary64 mode keeps every plane for the backward
   try {
     rc = build_problem(pl, M, N, K, p, &ex);
   } catch (const std::bad_alloc&) {
@@ -1213,6 +1519,7 @@ int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts
   if (rc) return rc;
   try {
     rc = build_problem(pl, M, N, K, p);
+    if (!rc) rc = plan_groups(pl);
   } catch (const std::bad_alloc&) {
     rc = OZ2_ENOMEM;
   }
@@ -1246,6 +1553,8 @@ int ozaki2_plan_destroy(ozaki2_plan pl) {
   if (pl->dev.mem) cudaFree(pl->dev.mem);
   for (auto& e : pl->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : pl->evg)
+    if (e) cudaEventDestroy(e);
   delete pl;
   return OZ2_OK;
 }
@@ -1264,6 +1573,9 @@ int ozaki2_plan_info(ozaki2_plan pl, ozaki2_info* out) {
   out->workspace_bytes = pl->ws_bytes;
   out->crt_mode = h.crt_mode;
   out->res_mode = h.res_mode;
+  out->plane_groups = std::max<int>(1, (int)h.groups.size());
+  out->group_planes = group_planes_max(h);
+  out->gemm_tile = pl->tile2 ? 2 : 1;
   return OZ2_OK;
 }
 
@@ -1309,12 +1621,14 @@ int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
   if (!d.mem) return OZ2_EINVAL;                 // counted once the plan has run
   int c = 0;
   c += (d.scan_rows.n || d.scan_cols.n) ? 1 : 0;
-  for (int i = 0; i < 6; ++i) c += d.res[i].n ? 1 : 0;
-  c += d.rtt.n ? 1 : 0;
-  c += (int)d.rmt.size();
-  if (pl->opts.engine == OZ2_ENGINE_SIMT) c += 1;
-  else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += 1;
-  else c += (int)d.plain.size();
+  int res = 0;
+  for (int i = 0; i < 6; ++i) res += d.res[i].n ? 1 : 0;
+  res += d.rtt.n ? 1 : 0;
+  res += (int)d.rmt.size();
+  if (!d.groups.empty()) c += (int)d.groups.size() * (res + 1);   // per group: residues + one GEMM
+  else if (pl->opts.engine == OZ2_ENGINE_SIMT) c += res + 1;
+  else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += res + 1;
+  else c += res + (int)d.plain.size();
   c += (int)d.cmt.size();
   c += d.finl.n ? 1 : 0;
   for (int i = 0; i < 9; ++i) c += d.fsh[i].n ? 1 : 0;
@@ -1328,6 +1642,45 @@ int ozaki2_plan_set_debug_chat(ozaki2_plan pl, int prob, uint32_t* dev_buf) {
   if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
   if (pl->dbg_chat.empty()) pl->dbg_chat.assign(pl->probs.size(), nullptr);
   pl->dbg_chat[prob] = dev_buf;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_set_wait_limit(ozaki2_plan pl, uint32_t polls) {
+  if (!pl) return OZ2_EINVAL;
+  pl->spin_limit = polls ? polls : kDefaultSpinLimit;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_debug_corrupt_crt(ozaki2_plan pl, int prob) {
+  if (!pl || prob < 0 || prob >= (int)pl->probs.size() || pl->dev.mem) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[prob];
+  CrtHost& c = pl->crts[h.crt_key];
+  // the top 32-bit digit of M_0 = P / m_0 in the digit table, with its high bit flipped
+  Big M0;
+  big_divmod_small(c.P, modulus_list()[0], &M0);
+  const int top = (int)M0.size() - 1;
+  c.words[3 * c.DS + c.L + top] ^= 0x80000000u;
+  if (!c.tc_table.empty()) {
+    // the top 7-bit piece of M_0 in the tensor-core table (both places it occurs)
+    const int jt = (big_bitlen(M0) - 1) / 7;
+    auto flip = [&](size_t idx) {
+      float f;
+      uint32_t u = (uint32_t)c.tc_table[idx] << 16;
+      std::memcpy(&f, &u, 4);
+      const uint32_t x = (uint32_t)f ^ 64u;
+      f = (float)x;
+      std::memcpy(&u, &f, 4);
+      c.tc_table[idx] = (uint16_t)(u >> 16);
+    };
+    flip((size_t)jt * c.kpad + 0);
+    if (jt + 1 < c.rows) flip((size_t)(jt + 1) * c.kpad + 1);
+  }
+  return OZ2_OK;
+}
+
+int ozaki2_debug_inject_alloc_failure(int count) {
+  if (count < 0) return OZ2_EINVAL;
+  g_inject_alloc.store(count);
   return OZ2_OK;
 }
 
@@ -1352,6 +1705,21 @@ int ozaki2_execute_batched(ozaki2_plan pl, int count, const ozaki2_problem* prob
   }
 }
 
+int ozaki2_execute_reuse(ozaki2_plan pl, int keep, const ozaki2_mat* X, ozaki2_mat* C, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!pl || !X || !C || (keep != 0 && keep != 1) || pl->probs.size() != 1 || !pl->last_ws) return OZ2_EINVAL;
+  if (pl->probs[0].skip_a || pl->probs[0].skip_b) return OZ2_EINVAL;
+  ozaki2_problem q = pl->last_q;
+  if (keep == 0) q.B = *X;
+  else q.A = *X;
+  q.C = *C;
+  try {
+    return execute_impl(pl, 1, &q, ws, ws_bytes, static_cast<cudaStream_t>(stream), keep);
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
 int ozaki2_graph_create(ozaki2_plan pl, int count, const ozaki2_problem* probs, void* ws,
                         size_t ws_bytes, void* stream, ozaki2_graph* out) {
   if (!pl || !probs || !ws || !out || !stream) return OZ2_EINVAL;
@@ -1361,7 +1729,7 @@ int ozaki2_graph_create(ozaki2_plan pl, int count, const ozaki2_problem* probs, 
   if (rc) return rc;
   auto* g = new (std::nothrow) ozaki2_graph_s();
   if (!g) return OZ2_ENOMEM;
-  rc = alloc_launch_block(g->lb, count);
+  rc = alloc_launch_block(g->lb, launch_slots(pl));
   std::vector<uint8_t> img;
   if (!rc) rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, g->lb.tmap_off, g->lb.bytes);
   if (!rc && cudaMemcpy(g->lb.d_mem, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) rc = OZ2_ECUDA;
@@ -1416,8 +1784,25 @@ int ozaki2_check(ozaki2_plan pl, void* stream) {
 int ozaki2_last_timings(ozaki2_plan pl, float ms[5]) {
   if (!pl || !ms || !pl->timed || !pl->ev[0]) return OZ2_EINVAL;
   if (cudaEventSynchronize(pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
-  for (int i = 0; i < 4; ++i)
-    if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return OZ2_ECUDA;
+  if (!pl->evg.empty() && !pl->dev.groups.empty()) {
+    // streamed planes: residues and GEMMs summed over the groups
+    const size_t ng = pl->evg.size() / 2;
+    float r = 0.f, gm = 0.f, x = 0.f;
+    for (size_t g = 0; g < ng; ++g) {
+      if (cudaEventElapsedTime(&x, pl->evg[2 * g], pl->evg[2 * g + 1]) != cudaSuccess) return OZ2_ECUDA;
+      r += x;
+      cudaEvent_t end = g + 1 < ng ? pl->evg[2 * g + 2] : pl->ev[3];
+      if (cudaEventElapsedTime(&x, pl->evg[2 * g + 1], end) != cudaSuccess) return OZ2_ECUDA;
+      gm += x;
+    }
+    if (cudaEventElapsedTime(&ms[0], pl->ev[0], pl->ev[1]) != cudaSuccess) return OZ2_ECUDA;
+    ms[1] = r;
+    ms[2] = gm;
+    if (cudaEventElapsedTime(&ms[3], pl->ev[3], pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
+  } else {
+    for (int i = 0; i < 4; ++i)
+      if (cudaEventElapsedTime(&ms[i], pl->ev[i], pl->ev[i + 1]) != cudaSuccess) return OZ2_ECUDA;
+  }
   if (cudaEventElapsedTime(&ms[4], pl->ev[0], pl->ev[4]) != cudaSuccess) return OZ2_ECUDA;
   return OZ2_OK;
 }
@@ -1445,7 +1830,7 @@ std::vector<int64_t> cache_key(int count, const ozaki2_problem* probs, const oza
   int dev = -1;
   cudaGetDevice(&dev);
   std::vector<int64_t> k{dev, o.guard_bits, o.t_bits, o.engine, o.k_chunk, o.grid, o.schedule, o.timing,
-                         o.crt_engine, o.res_engine, count};
+                         o.crt_engine, o.res_engine, o.plane_group, o.gemm_tile, count};
   for (int i = 0; i < count; ++i) {
     k.push_back(probs[i].M);
     k.push_back(probs[i].N);
@@ -1524,6 +1909,27 @@ static __device__ __align__(256) uint8_t ozaki2_noalloc_tables[4u << 20];     //
 
 namespace {
 
+// The last 256 bytes of the table array hold this path's device status word;
+// the table image of a call never reaches them.
+constexpr size_t kNoAllocStatusOff = (4u << 20) - 256;
+
+// The table image reaches the static array through kernel parameters, in
+// pieces of kNoAllocPiece bytes: no host buffer has to outlive the call and
+// no pageable host-to-device copy (which would wait for the stream) is made.
+constexpr int kNoAllocPiece = 30720;
+struct alignas(16) NoAllocPiece {
+  uint32_t off;       // byte offset in the table array (a multiple of 16)
+  uint32_t n;         // bytes in this piece (a multiple of 16)
+  uint32_t pad[2];
+  uint8_t bytes[kNoAllocPiece];
+};
+
+__global__ void __launch_bounds__(256) k_noalloc_put(const __grid_constant__ NoAllocPiece c) {
+  const uint4* src = reinterpret_cast<const uint4*>(c.bytes);
+  uint4* dst = reinterpret_cast<uint4*>(ozaki2_noalloc_tables + c.off);
+  for (uint32_t i = threadIdx.x; i < c.n / 16; i += blockDim.x) dst[i] = src[i];
+}
+
 struct NoAllocDevice {
   uint8_t* scratch = nullptr;
   uint8_t* tables = nullptr;
@@ -1555,16 +1961,22 @@ int noalloc_setup(int dev, NoAllocDevice** out) {
   return d.state == 1 ? OZ2_OK : OZ2_ECUDA;
 }
 
-int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
-                ozaki2_mat* C, cudaStream_t s) {
+int noalloc_device(NoAllocDevice** nd) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return OZ2_ENODEV;
   int major = 0;
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major != 10)
     return OZ2_ENODEV;
+  return noalloc_setup(dev, nd);
+}
+
+int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, const ozaki2_mat* B,
+                ozaki2_mat* C, cudaStream_t s) {
   NoAllocDevice* nd = nullptr;
-  int rc = noalloc_setup(dev, &nd);
+  int rc = noalloc_device(&nd);
   if (rc) return rc;
+  int dev = 0;
+  cudaGetDevice(&dev);
   // host-side plan with the default options (no device memory is touched)
   ozaki2_opts o;
   ozaki2_opts_default(&o);
@@ -1579,7 +1991,7 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   if (rc) return rc;
   layout_workspace(pl);
   if (pl->ws_bytes > sizeof(ozaki2_noalloc_scratch)) return OZ2_ERANGE;
-  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess ||
+  if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess || init_gemm2_attributes() != cudaSuccess ||
       init_crt_attributes() != cudaSuccess || !get_encode())
     return OZ2_ECUDA;
   int sms = 0;
@@ -1590,19 +2002,28 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   const size_t lb_off = align_up(ti.b.img.size(), 256);
   const size_t probs_bytes = align_up(sizeof(ProbDev), 128);
   const size_t lb_bytes = probs_bytes + 5 * sizeof(CUtensorMap);
-  if (lb_off + lb_bytes > sizeof(ozaki2_noalloc_tables)) return OZ2_ERANGE;
+  if (lb_off + lb_bytes > kNoAllocStatusOff) return OZ2_ERANGE;
   install_table_image(pl, ti, nd->tables);
+  pl->dev.tab.status = reinterpret_cast<int32_t*>(nd->tables + kNoAllocStatusOff);
   const ozaki2_problem q{M, N, K, p, *A, *B, *C};
   std::vector<uint8_t> lbimg;
   rc = build_image(pl, &q, nd->scratch, lbimg, probs_bytes, lb_bytes);
   if (rc) return rc;
-  // one image: tables (status word zeroed) + problem descriptor + tensor maps;
-  // copied from pageable host memory, stream-ordered behind earlier calls
+  // one image: tables + problem descriptor + tensor maps, put in place by
+  // kernels on the stream (ordered behind earlier calls), then the status
+  // word of this call cleared
   std::vector<uint8_t>& img = ti.b.img;
-  img.resize(lb_off + lb_bytes, 0);
+  img.resize(align_up(lb_off + lb_bytes, 16), 0);
   std::memcpy(img.data() + lb_off, lbimg.data(), lb_bytes);
-  if (cudaMemcpyAsync(nd->tables, img.data(), img.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return OZ2_ECUDA;
+  NoAllocPiece piece{};
+  for (size_t off = 0; off < img.size(); off += kNoAllocPiece) {
+    piece.off = (uint32_t)off;
+    piece.n = (uint32_t)std::min<size_t>(kNoAllocPiece, img.size() - off);
+    std::memcpy(piece.bytes, img.data() + off, piece.n);
+    k_noalloc_put<<<1, 256, 0, s>>>(piece);
+    if (cudaGetLastError() != cudaSuccess) return OZ2_ECUDA;
+  }
+  if (cudaMemsetAsync(nd->tables + kNoAllocStatusOff, 0, 4, s) != cudaSuccess) return OZ2_ECUDA;
   LaunchBlock lb;                       // not allocated: points into the static table array
   lb.d_mem = nd->tables + lb_off;
   lb.tmap_off = probs_bytes;
@@ -1622,4 +2043,17 @@ extern "C" int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const
   } catch (const std::bad_alloc&) {
     return OZ2_ENOMEM;
   }
+}
+
+extern "C" int ozaki2_noalloc_check(void* stream) {
+  NoAllocDevice* nd = nullptr;
+  int rc = noalloc_device(&nd);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return OZ2_ECUDA;
+  int32_t st = 0;
+  if (cudaMemcpy(&st, nd->tables + kNoAllocStatusOff, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OZ2_ECUDA;
+  if (st && cudaMemset(nd->tables + kNoAllocStatusOff, 0, 4) != cudaSuccess) return OZ2_ECUDA;
+  if (st & kStatusTimeout) return OZ2_ETIMEOUT;
+  if (st) return OZ2_EINTERNAL;
+  return OZ2_OK;
 }

@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
   auto epilogue = [&](int4 tp, int s) {
     const ProbDev& P = T.probs[tp.x];
     const int D = P.D32, np = P.crt_np;
-    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status);
+    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status, T.spin_limit);
     ++mcnt[s];
     ok = __syncthreads_and(ok);                   // keep every thread on the same path
     tc_fence_after();
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
         const int i2 = i + gridDim.x;
         if (i2 < ntiles && tiles[i2].x == tl.x) issue_u(i2, (k + 1) & 1);
       }
-      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status);
+      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status, T.spin_limit);
       ok = __syncthreads_and(ok);
       ++bcnt;
       cur = tl.x;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
     const int L = P.L;
     const int b = k & 1;
     // ---- V for this tile (two threads per output, half of the moduli each)
-    if (ok) ok = mbar_wait(u_bar + b, ucnt[b] & 1u, &abort_flag, T.status);
+    if (ok) ok = mbar_wait(u_bar + b, ucnt[b] & 1u, &abort_flag, T.status, T.spin_limit);
     ++ucnt[b];
     ok = __syncthreads_and(ok);
     if (!ok) break;
@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk;
         for (int c = 0; ok && c < nchunk; ++c) {
           for (int q = 0; q < nkb; ++q) {
-            if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
+            if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
             mbar_expect_tx(full + st, (uint32_t)cw * 128u);
             tma_load_2d(sRing + st * stage_bytes, mt, smem_u32(full + st), q * 64, c * cw);
             issued_phase[st] = (int)ph;
@@ -1147,13 +1147,13 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
         const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
         vnext = nvbuf == 2 ? vnext ^ 1 : 0;
-        if (!mbar_wait(v_full + vb, (uint32_t)(vuse & 1), abort_flag, T.status)) { ok = false; break; }
+        if (!mbar_wait(v_full + vb, (uint32_t)(vuse & 1), abort_flag, T.status, T.spin_limit)) { ok = false; break; }
         tc_fence_after();
         const uint32_t vbase = tmem + (uint32_t)vb * vcols;
         for (int c = 0; ok && c < nchunk; ++c) {
           const int s = nslot == 2 ? next : 0, use = uses[s]++;
           next = nslot == 2 ? next ^ 1 : 0;
-          if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
+          if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status, T.spin_limit)) {
             ok = false;
             break;
           }
@@ -1162,7 +1162,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           const uint32_t idesc = idesc_bf16(128, ncol);
           const uint32_t d = tmem + (uint32_t)nvbuf * vcols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
-            if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
+            if (!mbar_wait(full + st, ph, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
             tc_fence_after();
             const uint64_t db = desc_sw128(sRing + st * stage_bytes);
 #pragma unroll
@@ -1197,7 +1197,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int L = P.L;
         for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
           const int s = uc % kCmUSlots, use = uc / kCmUSlots;
-          if (use > 0 && !mbar_wait(u_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
+          if (use > 0 && !mbar_wait(u_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status, T.spin_limit)) {
             ok = false;
             break;
           }
@@ -1233,7 +1233,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
       vnext = nvbuf == 2 ? vnext ^ 1 : 0;
       // the buffer may be rewritten once every MMA of its previous tile is done
-      if (vuse > 0 && ok) ok = mbar_wait(v_free + vb, (uint32_t)((vuse - 1) & 1), abort_flag, T.status);
+      if (vuse > 0 && ok) ok = mbar_wait(v_free + vb, (uint32_t)((vuse - 1) & 1), abort_flag, T.status, T.spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) return;
       tc_fence_after();
@@ -1241,7 +1241,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       for (int l0 = 0; l0 < L; l0 += kCmUMods, ++uc) {
         if ((uc & 3) != half) continue;             // another group's copy
         const int s = uc % kCmUSlots, use = uc / kCmUSlots;
-        if (ok) ok = mbar_wait(u_full + s, (uint32_t)(use & 1), abort_flag, T.status);
+        if (ok) ok = mbar_wait(u_full + s, (uint32_t)(use & 1), abort_flag, T.status, T.spin_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
         const uint16_t* su = s_u + s * (kCmUMods * 128);
@@ -1284,7 +1284,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       for (int c = 0; c < nchunk; ++c) {
         const int s = nslot == 2 ? next : 0, use = uses[s]++;
         next = nslot == 2 ? next ^ 1 : 0;
-        if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
+        if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status, T.spin_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
         tc_fence_after();

@@ -23,6 +23,7 @@
 #include <climits>
 
 #include "oz2_internal.h"
+#include "plane_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace oz2 {
@@ -30,6 +31,7 @@ namespace oz2 {
 namespace {
 
 using namespace tc;
+using namespace plane;
 
 constexpr int kTileABytes = kBM * kBK * 2;            // 16 KB
 constexpr int kTileBBytes = kBN * kBK * 2;            // 32 KB
@@ -44,90 +46,6 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
   tc::umma_bf16(d_tmem, a, b, kIdesc, acc);
 }
-__device__ __forceinline__ uint32_t barrett32(uint32_t x, uint32_t m, uint32_t mu) {
-  uint32_t q = __umulhi(x, mu);
-  uint32_t r = x - q * m;
-  return r >= m ? r - m : r;
-}
-
-// x: exact integer held in fp32 with |x| < 2^25.  Returns x mod m in [0, m).
-// q = rint(x * rcp) is within 0.52 of x/m, so r = x - q m lies in
-// (-0.52 m, 0.52 m) and is computed exactly by the fma; one correction
-// brings it into [0, m).
-__device__ __forceinline__ uint32_t fmod_small(float x, float mf, float rcp) {
-  const float q = rintf(x * rcp);
-  float r = fmaf(-q, mf, x);
-  r = r < 0.f ? r + mf : r;
-  // exact float -> int of 0 <= r < 2^23 without a conversion instruction
-  return __float_as_uint(r + 8388608.0f) - 0x4B000000u;
-}
-
-// exact int -> float of 0 <= x < 2^23 without a conversion instruction
-__device__ __forceinline__ float small_u2f(uint32_t x) {
-  return __uint_as_float(0x4B000000u + x) - 8388608.0f;
-}
-
-// One accumulation job: plane `plane` of unit `u` over K chunk `chunk`.
-struct Job {
-  Unit u;
-  int slot;
-  int plane;
-  int chunk;
-  bool first;       // first job of the unit: the MMA overwrites the slot
-  bool last;        // last job of the unit: the epilogue writes u_l
-  uint32_t kmul;    // write-back multiplier (not last)
-};
-
-// Deterministic job order shared by the producer, MMA and epilogue roles:
-// units s, s+2, s+4, ... of the CTA's list go to TMEM slot s, and the jobs of
-// the two slot streams alternate.
-struct JobIter {
-  const DevTables* T;
-  int ubeg, n;
-  int uidx[2], job[2], turn;
-
-  __device__ void init(const DevTables* t, int b, int e) {
-    T = t; ubeg = b; n = e - b;
-    uidx[0] = 0; uidx[1] = 1; job[0] = job[1] = 0; turn = 0;
-  }
-  __device__ bool next(Job& j) {
-    int s = turn;
-    if (uidx[s] >= n) {
-      s ^= 1;
-      if (uidx[s] >= n) return false;
-    }
-    const Unit u = T->units[ubeg + uidx[s]];
-    const ProbDev& P = T->probs[u.prob];
-    const bool two = u.ell >= P.L1;
-    const int nch = P.nchunks;
-    const int njobs = (two ? 3 : 1) * nch;
-    const int jj = job[s];
-    const int pi = jj / nch;
-    j.u = u;
-    j.slot = s;
-    j.chunk = jj - pi * nch;
-    if (two) {
-      const int g0 = P.L1 + 3 * (u.ell - P.L1);
-      j.plane = g0 + (pi == 0 ? 0 : (pi == 1 ? 2 : 1));   // P0, Ps, P2
-    } else {
-      j.plane = u.ell;
-    }
-    j.first = jj == 0;
-    j.last = jj == njobs - 1;
-    j.kmul = 1u;
-    if (!j.last && j.chunk == nch - 1) {
-      const ModConst& mc = T->mods[u.ell];
-      j.kmul = pi == 0 ? mc.kmul01 : mc.kmul12;
-    }
-    if (++job[s] == njobs) {
-      job[s] = 0;
-      uidx[s] += 2;
-    }
-    turn = s ^ 1;
-    return true;
-  }
-};
-
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ DevTables T) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -187,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       const int k0 = j.chunk * P.kchunk;
       const int k1 = min(P.K, k0 + P.kchunk);
       for (int k = k0; k < k1; k += kBK) {
-        if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
+        if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
         mbar_expect_tx(full + st, kStageBytes);
         const uint32_t sa = base + st * kStageBytes;
         tma_load_3d(sa, ma, smem_u32(full + st), k, j.u.tm * kBM, j.plane);
@@ -220,14 +138,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       const int k0 = j.chunk * P.kchunk;
       const int k1 = min(P.K, k0 + P.kchunk);
       if (uses[s] > 0) {
-        if (!mbar_wait(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status)) { ok = false; break; }
+        if (!mbar_wait(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status, T.spin_limit)) { ok = false; break; }
       }
       ++uses[s];
       tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(s * kBN);
       bool acc = !j.first;
       for (int k = k0; k < k1; k += kBK) {
-        if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
+        if (!mbar_wait(full + st, ph, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
         tc_fence_after();
         const uint32_t sa = base + st * kStageBytes;
         const uint64_t da = desc_sw128(sa);
@@ -276,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
       // the stored value is the CRT's v_l = (c mod m_l) M_l^{-1} mod m_l (Sec. 4.4)
       uint32_t fin = mc.kfin;
       if (j.last) fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
-      if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status)) break;
+      if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status, T.spin_limit)) break;
       ++uses[s];
       tc_fence_after();
 #pragma unroll 1

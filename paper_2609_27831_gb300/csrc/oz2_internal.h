@@ -20,6 +20,10 @@ constexpr int kBK = 64;
 constexpr int kStages = 4;
 constexpr int kMaxKChunk = 1024;   // 127^2 * 1024 + 16191 < 2^24: fp32 accumulation stays exact
 
+// Polls of a bounded mbarrier wait before it gives up (the launch's
+// DevTables::spin_limit; a plan may lower it to test the timeout path).
+constexpr uint32_t kDefaultSpinLimit = 1u << 26;
+
 constexpr int kMaxP = 2048;
 constexpr int kMaxK = 133000;      // Sec. 4.3(a) implementation cap
 
@@ -136,7 +140,7 @@ struct DevTables {
   const CUtensorMap* tmaps;  // [2 * count]: A planes, B planes
   int32_t* status;           // device status word
   int32_t count;
-  int32_t pad;
+  uint32_t spin_limit;       // iterations of a bounded mbarrier wait before it gives up
 };
 
 // Status bits of the device status word.
@@ -151,6 +155,9 @@ cudaError_t launch_scan(const DevTables& t, int count, const int32_t* blk_prefix
 cudaError_t launch_residues(const DevTables& t, int w16_class, const int32_t* blk_list,
                             int nblk, int smem_bytes, cudaStream_t s);
 cudaError_t launch_gemm_tc(const DevTables& t, int grid, cudaStream_t s);
+// CTA-pair plane GEMM (256 x 256 tiles): `pairs` clusters of two CTAs,
+// t.cta_begin holding pairs + 1 unit ranges.
+cudaError_t launch_gemm_tc2(const DevTables& t, int pairs, cudaStream_t s);
 cudaError_t launch_gemm_simt(const DevTables& t, const int32_t* unit_list, int nunits,
                              cudaStream_t s);
 cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int nblk, int lmax,

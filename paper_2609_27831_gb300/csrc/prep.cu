@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 
   auto epilogue = [&](int4 tp, int s) {
     const ProbDev& P = T.probs[tp.x];
-    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status);
+    if (ok) ok = mbar_wait(m_bar + s, mcnt[s] & 1u, &abort_flag, T.status, T.spin_limit);
     ++mcnt[s];
     ok = __syncthreads_and(ok);
     tc_fence_after();
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kRtThreads, 2)
         for (int q = 0; q < kb; ++q)
           tma_load_2d(sB + q * tb, T.tmaps + 4 * T.count + tl.x, smem_u32(b_bar), q * 64, 0);
       }
-      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status);
+      ok = mbar_wait(b_bar, bcnt & 1u, &abort_flag, T.status, T.spin_limit);
       ok = __syncthreads_and(ok);
       ++bcnt;
       cur = tl.x;
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         const int nkb = P.res_kpad / 64, cw = P.res_cw, nchunk = P.res_nchunk;
         for (int c = 0; ok && c < nchunk; ++c) {
           for (int q = 0; q < nkb; ++q) {
-            if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status)) { ok = false; break; }
+            if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
             mbar_expect_tx(full + st, (uint32_t)cw * 128u);
             tma_load_2d(sRing + st * stage_bytes, mt, smem_u32(full + st), q * 64, c * cw);
             issued_phase[st] = (int)ph;
@@ -846,12 +846,12 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         const uint32_t acols = (uint32_t)P.res_kpad / 2;
         const int nabuf = P.res_nabuf;
         const int ab = tcount % nabuf, ause = tcount / nabuf;
-        if (!mbar_wait(a_full + ab, (uint32_t)(ause & 1), abort_flag, T.status)) { ok = false; break; }
+        if (!mbar_wait(a_full + ab, (uint32_t)(ause & 1), abort_flag, T.status, T.spin_limit)) { ok = false; break; }
         tc_fence_after();
         const uint32_t abase = tmem + (uint32_t)ab * acols;
         for (int c = 0; ok && c < nchunk; ++c, ++ck) {
           const int s = ck & 1, use = ck >> 1;
-          if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status)) {
+          if (use > 0 && !mbar_wait(acc_free + s, (uint32_t)((use - 1) & 1), abort_flag, T.status, T.spin_limit)) {
             ok = false;
             break;
           }
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           const uint32_t idesc = idesc_bf16(128, ncol);
           const uint32_t d = tmem + (uint32_t)nabuf * acols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
-            if (!mbar_wait(full + st, ph, abort_flag, T.status)) { ok = false; break; }
+            if (!mbar_wait(full + st, ph, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
             tc_fence_after();
             const uint64_t db = desc_sw128(sRing + st * stage_bytes);
 #pragma unroll
@@ -939,7 +939,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       for (int j = lq - 3; j >= 1 && !sticky; --j) sticky |= S(j);
       uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(lm0[2] >> (Bb & 63)) & 1u))) : 0u;
       const uint32_t sgn = neg ? 0x80008000u : 0u;
-      if (ause > 0 && ok) ok = mbar_wait(a_free + ab, (uint32_t)((ause - 1) & 1), abort_flag, T.status);
+      if (ause > 0 && ok) ok = mbar_wait(a_free + ab, (uint32_t)((ause - 1) & 1), abort_flag, T.status, T.spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       uint16_t* dst0 = planes + (int64_t)(valid ? line : 0) * P.Kp + (valid ? k : 0);
       for (int c = 0; c < nchunk; ++c, ++ck) {
         const int s = ck & 1, use = ck >> 1;
-        if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status);
+        if (ok) ok = mbar_wait(acc_full + s, (uint32_t)(use & 1), abort_flag, T.status, T.spin_limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();

@@ -11,7 +11,7 @@
 namespace oz2 {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint32_t kSpinLimit = kDefaultSpinLimit;   // drains of copies and MMAs in flight
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -38,11 +38,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait.  On timeout the CTA-wide abort flag and the device status word
-// are set and false is returned; every other waiter then leaves its loop.
+// Bounded wait of at most `limit` polls (the launch's DevTables::spin_limit,
+// kSpinLimit unless a test lowers it).  On timeout the CTA-wide abort flag and
+// the device status word are set and false is returned; every other waiter
+// then leaves its loop.
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                          int32_t* status) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+                          int32_t* status, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (it > 1024) __nanosleep(32);

@@ -57,3 +57,16 @@ def test_every_stage_reports_its_hbm_rate():
     cpu = bench.stage_rooflines(_info(), M, N, K, 256, {"scan": 0.02, "residues": 0.2, "gemm": 0.18, "crt": 0.25},
                                 "none")
     assert cpu["crt"]["hbm"]["bytes"] == 70 * M * N * 2 + M * N * (8 * 4 + 5)
+
+
+def test_tensor_core_residues_against_the_tensor_peak():
+    """res_mode 2 runs the residue byte products on the tensor cores: 2 flops
+    per byte multiply-add against the bf16 peak, not the dp4a rate."""
+    M = N = K = 1024
+    info = _info(res_mode=2, crt_pieces=83)
+    st = {"scan": 0.02, "residues": 0.5, "gemm": 0.18, "crt_sums": 0.15, "crt_finish": 0.09}
+    out = bench.stage_rooflines(info, M, N, K, 256, st, "none")
+    r = out["residues"]
+    macs = (M + N) * K * -(-283 // 8) * (54 + 2 * 16)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(2.0 * macs / 0.5e-3 / 1e12, abs=0.05)

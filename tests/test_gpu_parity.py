@@ -58,7 +58,7 @@ def run_gpu(ozk, A, B, p, debug=True, **kw):
     plan.check()
     torch.cuda.synchronize()
     off, kp = plan.layout()
-    G, L = plan.info["G"], plan.info["L"]
+    G, L = plan.info["group_planes"], plan.info["L"]     # streamed: the last group's planes
     upitch = -(-(M * N) // 8) * 8
     w = ws.cpu().numpy()
 
@@ -432,3 +432,159 @@ def test_convenience_gemm_call(ozk):
     torch.cuda.synchronize()
     ref = o.ozaki2_full(A, B, 160)["C"]
     assert np.array_equal(Cd.to_host()["limbs"], ref["limbs"])
+
+
+def _groups(moduli, req):
+    """Planes per modulus group: as few groups of consecutive moduli with at
+    most req planes each (one per one-limb modulus, three per two-limb) as
+    the plane counts allow, of about equal size (the smallest cap from the
+    even split up that reaches that count); a group with two-limb moduli
+    holds an even number of one-limb ones."""
+    planes = [1 if m <= 255 else 3 for m in moduli]
+    G = sum(planes)
+    ng = -(-G // req)
+
+    def split(cap):
+        out, cur, ones = [], 0, 0
+        for pl_ in planes:
+            if cur and (cur + pl_ > cap or (pl_ == 3 and ones % 2)):
+                out.append(cur)
+                cur, ones = 0, 0
+            cur += pl_
+            ones += pl_ == 1
+        out.append(cur)
+        return out
+
+    for cap in range(-(-G // ng), req + 1):
+        out = split(cap)
+        if len(out) <= ng:
+            break
+    return out
+
+
+@pytest.mark.parametrize("p,shape,req,kw", [
+    (256, (150, 130, 200), 20, {}),                 # CUDA-core residues, groups across the one/two-limb border
+    (256, (150, 130, 200), 7, {"res_engine": 2}),   # tensor-core residues, small groups
+    (1024, (70, 60, 90), 40, {}),                   # tensor-core residues (automatic), an odd one-limb border
+    (1024, (70, 60, 90), 40, {"res_engine": 3}),    # the same groups on the CUDA cores
+    (113, (40, 300, 70), 3, {"crt_engine": 3}),     # one or three planes per group
+])
+def test_planes_streamed_in_modulus_groups(ozk, p, shape, req, kw):
+    """Planes streamed through the workspace group by group give the same
+    reduced products, CRT integers and outputs as the oracle (and as one
+    group); the plane region holds the last group's planes."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(5200 + p + req))
+    A = synth.mp_matrix(rng, M, K, p, -8, 8)
+    B = synth.mp_matrix(rng, K, N, p, -8, 8)
+    got = run_gpu(ozk, A, B, p, plane_group=req, **kw)
+    info = got["plan"].info
+    ref = o.ozaki2_full(A, B, p)
+    sizes = _groups(ref["par"].moduli, req)
+    assert info["plane_groups"] == len(sizes) > 1 and info["group_planes"] == max(sizes)
+    last = sizes[-1]
+    assert np.array_equal(bf16_to_int(got["pa"][:last]), ref["planes_a"][-last:])
+    assert np.array_equal(bf16_to_int(got["pb"][:last]), ref["planes_b"][-last:])
+    assert np.array_equal(got["u"].astype(np.int64), crt_v(ref["u"], ref["par"].moduli))
+    assert all(got["chat"][i, j] == ref["chat"][i, j] for i in range(M) for j in range(N))
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got["C"][key], ref["C"][key]), key
+    whole = run_gpu(ozk, A, B, p, debug=False, plane_group=-1, **kw)
+    assert whole["plan"].info["plane_groups"] == 1
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got["C"][key], whole["C"][key]), key
+    # timings: residues and GEMMs summed over the groups
+    plan = ozk.Plan((M, N, K, p), plane_group=req, timing=1, **kw)
+    ws = plan.workspace()
+    dC = ozk.MPMatrix.empty(M, N, p)
+    plan.execute(ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), dC, ws)
+    tm = plan.timings()
+    assert all(tm[k] > 0 for k in ("scan", "residues", "gemm", "crt"))
+    assert tm["scan"] + tm["residues"] + tm["gemm"] + tm["crt"] <= tm["total"] * 1.001 + 1e-3
+    assert plan.launches() >= 1 + len(sizes) * 2
+
+
+@pytest.mark.parametrize("shape,p,kw", [
+    ((40, 30, 50), 53, {}),                           # one pair tile, the peer's rows all outside M
+    ((130, 260, 70), 113, {}),                        # ragged rows inside the peer, two column tiles
+    ((300, 520, 200), 256, {"k_chunk": 128}),         # K chunks with write-back, two-limb moduli
+    ((257, 129, 1100), 53, {}),                       # K above one 1024 chunk, rows one past a pair tile
+])
+def test_pair_tiles_bit_exact(ozk, shape, p, kw):
+    """The CTA-pair plane GEMM (256 x 256 tiles, tcgen05 cta_group::2) gives the
+    oracle's planes products bit for bit: every v_l, CRT integer and output."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(7100 + M + p))
+    A = synth.mp_matrix(rng, M, K, p, -8, 8)
+    B = synth.mp_matrix(rng, K, N, p, -8, 8)
+    got, _ = assert_full_parity(ozk, A, B, p, truth=False, gemm_tile=2, **kw)
+    assert got["plan"].info["gemm_tile"] == 2
+
+
+def test_pair_tiles_streamed_and_batched(ozk):
+    """Pair tiles through modulus groups and in a batched plan agree with the
+    one-SM tiles bit for bit."""
+    rng = np.random.Generator(np.random.PCG64(7200))
+    A = synth.mp_matrix(rng, 180, 200, 256, -8, 8)
+    B = synth.mp_matrix(rng, 200, 300, 256, -8, 8)
+    one = run_gpu(ozk, A, B, 256, debug=False, gemm_tile=1)
+    two = run_gpu(ozk, A, B, 256, debug=False, gemm_tile=2, plane_group=20)
+    assert two["plan"].info["plane_groups"] > 1
+    assert np.array_equal(one["u"], two["u"])
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(one["C"][key], two["C"][key]), key
+    shapes = [(70, 300, 90, 113), (260, 40, 64, 256), (33, 33, 33, 53)]
+    trip, ins = [], []
+    for (M, N, K, p) in shapes:
+        a = synth.mp_matrix(rng, M, K, p, -8, 8)
+        b = synth.mp_matrix(rng, K, N, p, -8, 8)
+        ins.append((a, b, p))
+        trip.append((ozk.MPMatrix.from_host(a), ozk.MPMatrix.from_host(b), ozk.MPMatrix.empty(M, N, p)))
+    for sched in (0, 1):                               # grouped, and one launch per modulus
+        plan = ozk.Plan(shapes, gemm_tile=2, schedule=sched)
+        plan.execute_batched(trip, plan.workspace())
+        plan.check()
+        torch.cuda.synchronize()
+        for (a, b, p), (_, _, c) in zip(ins, trip):
+            ref = o.ozaki2_full(a, b, p)["C"]
+            h = c.to_host()
+            for key in ("limbs", "exp", "sign"):
+                assert np.array_equal(h[key], ref[key]), key
+
+
+@pytest.mark.parametrize("p,shape,kw", [(113, (90, 70, 130), {}), (256, (64, 300, 200), {"res_engine": 2}),
+                                        (1024, (40, 50, 60), {})])
+def test_operand_reuse(ozk, p, shape, kw):
+    """ozaki2_execute_reuse: a second right-hand side with A's planes kept, and
+    a second left-hand side with B's planes kept, each bit-identical to the
+    oracle; a workspace that did not run the previous product is refused."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(7300 + p))
+    A = synth.mp_matrix(rng, M, K, p, -8, 8)
+    B1 = synth.mp_matrix(rng, K, N, p, -8, 8)
+    B2 = synth.mp_matrix(rng, K, N, p, -20, 3)
+    A2 = synth.mp_matrix(rng, M, K, p, -2, 9)
+    plan = ozk.Plan((M, N, K, p), **kw)
+    ws = plan.workspace()
+    dA, dB1 = ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B1)
+    C1 = ozk.MPMatrix.empty(M, N, p)
+    plan.execute(dA, dB1, C1, ws)
+    C2 = ozk.MPMatrix.empty(M, N, p)
+    plan.execute_reuse(0, ozk.MPMatrix.from_host(B2), C2, ws)      # A kept
+    C3 = ozk.MPMatrix.empty(M, N, p)
+    plan.execute_reuse(1, ozk.MPMatrix.from_host(A2), C3, ws)      # B2 kept
+    plan.check()
+    torch.cuda.synchronize()
+    for got, (x, y) in ((C1, (A, B1)), (C2, (A, B2)), (C3, (A2, B2))):
+        ref = o.ozaki2_full(x, y, p)["C"]
+        h = got.to_host()
+        for key in ("limbs", "exp", "sign"):
+            assert np.array_equal(h[key], ref[key]), key
+    with pytest.raises(ozk.OzakiError):
+        plan.execute_reuse(0, ozk.MPMatrix.from_host(B2), C2, plan.workspace())
+    streamed = ozk.Plan((M, N, K, p), plane_group=3, **kw)
+    if streamed.info["plane_groups"] > 1:
+        w2 = streamed.workspace()
+        streamed.execute(dA, dB1, C1, w2)
+        with pytest.raises(ozk.OzakiError):
+            streamed.execute_reuse(0, ozk.MPMatrix.from_host(B2), C2, w2)

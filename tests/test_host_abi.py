@@ -173,3 +173,92 @@ def test_residue_engine_choice(ozk):
     assert ozk.Plan((64, 64, 64, 512)).info["res_mode"] == 0
     assert ozk.Plan((64, 64, 64, 2048), res_engine=3).info["res_mode"] == 0
     assert ozk.Plan((64, 64, 64, 256), res_engine=2).info["res_mode"] == 2
+
+
+def test_planes_streamed_in_modulus_groups(ozk):
+    """Large products stream their residue planes through the workspace in
+    groups of consecutive moduli: one group's bf16 plane stacks at a time
+    (at most 32 GiB automatically, or opts.plane_group planes), the reduced
+    products and the CRT of every modulus kept whole."""
+    big = (4096, 4096, 4096, 2048)
+    whole = ozk.Plan(big, plane_group=-1).info
+    auto = ozk.Plan(big).info
+    G, L = whole["G"], whole["L"]
+    assert whole["plane_groups"] == 1 and whole["group_planes"] == G == 879
+    per_plane = 2 * (4096 + 4096) * 4096
+    assert auto["plane_groups"] == 2 and auto["group_planes"] * per_plane <= 32 << 30
+    # the workspace shrinks by the planes no longer resident
+    assert whole["workspace_bytes"] - auto["workspace_bytes"] == (G - auto["group_planes"]) * per_plane
+    # explicit group sizes: about equal groups, each at most the request
+    for req in (3, 64, 300, 878):
+        inf = ozk.Plan(big, plane_group=req).info
+        assert inf["group_planes"] <= req
+        assert inf["plane_groups"] in (-(-G // req), -(-G // req) + 1)
+        assert inf["t"] == whole["t"] and inf["L"] == L and inf["crt_digits"] == whole["crt_digits"]
+    assert ozk.Plan(big, plane_group=879).info["plane_groups"] == 1
+    # small products stay in one group unless asked
+    assert ozk.Plan((1024, 1024, 1024, 256)).info["plane_groups"] == 1
+    assert ozk.Plan((200, 150, 300, 256), plane_group=20).info["plane_groups"] > 1
+    # batched plans and the binary64 mode never stream
+    assert ozk.Plan([(200, 150, 300, 256), (64, 64, 64, 53)], plane_group=20).info["plane_groups"] == 1
+
+
+def test_plane_group_option_errors(ozk):
+    for bad in (-2, 1, 2):
+        with pytest.raises(ozk.OzakiError) as ei:
+            ozk.Plan((200, 150, 300, 256), plane_group=bad)
+        assert ei.value.status == ozk._lib.OZ2_EINVAL
+    # streaming runs the grouped tensor-core GEMM: other engines or schedules refuse an explicit group size
+    for kw in ({"engine": 1}, {"schedule": 1}):
+        with pytest.raises(ozk.OzakiError):
+            ozk.Plan((200, 150, 300, 256), plane_group=20, **kw)
+        assert ozk.Plan((200, 150, 300, 256), **kw).info["plane_groups"] == 1
+
+
+def test_injected_host_allocation_failure(ozk):
+    """A host allocation failure while a plan is built is reported as
+    OZ2_ENOMEM (nothing aborts, nothing half-made is kept); the next call
+    succeeds."""
+    lib = ozk.lib()
+    h = C.c_void_p()
+    assert lib.ozaki2_debug_inject_alloc_failure(1) == 0
+    assert lib.ozaki2_plan_create(64, 64, 64, 53, None, C.byref(h)) == ozk._lib.OZ2_ENOMEM
+    assert not h.value
+    assert lib.ozaki2_plan_create(64, 64, 64, 53, None, C.byref(h)) == 0 and h.value
+    lib.ozaki2_plan_destroy(h)
+    # batched plans take the same path
+    arr = (ozk._lib.Problem * 2)()
+    for i, (M, N, K, p) in enumerate([(64, 64, 64, 53), (32, 16, 8, 113)]):
+        arr[i].M, arr[i].N, arr[i].K, arr[i].p = M, N, K, p
+    assert lib.ozaki2_debug_inject_alloc_failure(2) == 0
+    assert lib.ozaki2_plan_create_batched(2, arr, None, C.byref(h)) == ozk._lib.OZ2_ENOMEM
+    assert lib.ozaki2_plan_create_batched(2, arr, None, C.byref(h)) == ozk._lib.OZ2_ENOMEM
+    assert lib.ozaki2_plan_create_batched(2, arr, None, C.byref(h)) == 0
+    lib.ozaki2_plan_destroy(h)
+    assert lib.ozaki2_debug_inject_alloc_failure(-1) == ozk._lib.OZ2_EINVAL
+    assert lib.ozaki2_debug_inject_alloc_failure(0) == 0
+
+
+def test_fault_injection_setters(ozk):
+    lib = ozk.lib()
+    assert lib.ozaki2_plan_set_wait_limit(None, 5) == ozk._lib.OZ2_EINVAL
+    assert lib.ozaki2_plan_debug_corrupt_crt(None, 0) == ozk._lib.OZ2_EINVAL
+    plan = ozk.Plan((64, 64, 64, 256))
+    assert lib.ozaki2_plan_set_wait_limit(plan._h, 1) == 0
+    assert lib.ozaki2_plan_set_wait_limit(plan._h, 0) == 0
+    assert lib.ozaki2_plan_debug_corrupt_crt(plan._h, 1) == ozk._lib.OZ2_EINVAL
+    assert lib.ozaki2_plan_debug_corrupt_crt(plan._h, 0) == 0
+
+
+def test_operand_reuse_needs_a_previous_execute(ozk):
+    """ozaki2_execute_reuse keeps one operand's planes from the previous
+    execute with the same workspace: without one it refuses (host check)."""
+    lib = ozk.lib()
+    plan = ozk.Plan((64, 64, 64, 113))
+    m = ozk._lib.Mat(1, 1, 1, 64, 64 * 64)
+    c = ozk._lib.Mat(1, 1, 1, 64, 64 * 64)
+    for keep in (0, 1):
+        assert lib.ozaki2_execute_reuse(plan._h, keep, C.byref(m), C.byref(c), 256, 1 << 30, None) == \
+            ozk._lib.OZ2_EINVAL
+    assert lib.ozaki2_execute_reuse(plan._h, 2, C.byref(m), C.byref(c), 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
+    assert lib.ozaki2_execute_reuse(None, 0, C.byref(m), C.byref(c), 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
