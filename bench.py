@@ -525,7 +525,7 @@ def measure_e2e(g: Gpu, ozk, plan, A, B, bufs, ws, steps, world, barrier):
             "copies": "pinned host buffers, every step, double-buffered on two copy streams"}
 
 
-def measure_batched(g: Gpu, ozk, steps: int = 5, warmup: int = 3):
+def measure_batched(g: Gpu, ozk, steps: int = 5, warmup: int = 3, tune: bool = True):
     """64 problems: one CUDA graph of the grouped launches, the grouped
     executes without the graph, and the plain form (one GEMM launch per
     modulus per problem) on the same inputs."""
@@ -551,10 +551,33 @@ def measure_batched(g: Gpu, ozk, steps: int = 5, warmup: int = 3):
     plan_p.check()
     del ws_p
     g.torch.cuda.empty_cache()
-    return {"problems": 64, "M_N_K": "log-uniform [128, 2048]", "p": [113, 256, 512],
-            "value": work / (ms_graph / 1e3), "unit": UNIT, "graph_ms": ms_graph, "grouped_ms": ms_grouped,
-            "plain_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_graph,
-            "plain": "one plane-GEMM launch per modulus per problem (other stages grouped)"}
+    out = {"problems": 64, "M_N_K": "log-uniform [128, 2048]", "p": [113, 256, 512],
+           "value": work / (ms_graph / 1e3), "unit": UNIT, "graph_ms": ms_graph, "grouped_ms": ms_grouped,
+           "plain_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_graph,
+           "plain": "one plane-GEMM launch per modulus per problem (other stages grouped)"}
+    if tune:
+        # autotuned: per-problem K chunk and engines per class, the launch-wide
+        # tile measured on the batch; then one CUDA graph of the tuned plan
+        import tempfile
+        from paper_2609_27831_gb300 import autotune as at
+        t0 = time.perf_counter()
+        with tempfile.TemporaryDirectory() as td:
+            tuned = at.tune_batched(shapes, os.path.join(td, "tune.json"), reps=1)
+        tune_s = time.perf_counter() - t0
+        plan_t = ozk.Plan(shapes, per_problem=tuned["per_problem"], **tuned["opts"])
+        ws_t = plan_t.workspace(g.dev)
+        with g.torch.cuda.stream(s):
+            graph_t = plan_t.graph(trip, ws_t, s)
+        ms_tuned = g.timed(lambda: graph_t.launch(g.stream), steps, warmup)
+        plan_t.check()
+        del graph_t, ws_t
+        g.torch.cuda.empty_cache()
+        out.update({"tuned_graph_ms": ms_tuned, "tuned_value": work / (ms_tuned / 1e3),
+                    "tuned_speedup_vs_plain": ms_plain / ms_tuned, "tuned_opts": tuned["opts"],
+                    "tuned_per_problem_distinct": sorted({json.dumps(d, sort_keys=True)
+                                                          for d in tuned["per_problem"]}),
+                    "tuning_s": round(tune_s, 1)})
+    return out
 
 
 def measure_autograd(g: Gpu, steps: int = 5, warmup: int = 3, n: int = 4096):

@@ -173,6 +173,14 @@ OZ2_API int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const oza
 OZ2_API int ozaki2_plan_create_batched(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
                                ozaki2_plan* out);
 
+/* The same with per-problem choices (an autotuner's per-class table):
+   per_problem[i] supplies problem i's guard_bits, t_bits, k_chunk,
+   crt_engine and res_engine (its other fields are ignored); the launch-wide
+   options (engine, grid, schedule, timing, plane GEMM tile) come from opts.
+   per_problem may be NULL (= ozaki2_plan_create_batched). */
+OZ2_API int ozaki2_plan_create_batched_ex(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
+                                          const ozaki2_opts* per_problem, ozaki2_plan* out);
+
 OZ2_API int ozaki2_plan_destroy(ozaki2_plan plan);
 
 /* Host-side facts; see ozaki2_info. */

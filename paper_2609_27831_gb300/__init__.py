@@ -83,8 +83,10 @@ class Graph:
 class Plan:
     """A plan for one product or for a batch of independent products."""
 
-    def __init__(self, shapes, **kw):
-        """``shapes``: (M, N, K, p) or a list of such tuples (batched)."""
+    def __init__(self, shapes, per_problem=None, **kw):
+        """``shapes``: (M, N, K, p) or a list of such tuples (batched);
+        ``per_problem`` (batched): one dict of per-problem options each
+        (guard_bits, t_bits, k_chunk, crt_engine, res_engine)."""
         self._o = opts(**kw)
         h = C.c_void_p()
         if isinstance(shapes, tuple):
@@ -96,7 +98,13 @@ class Plan:
             arr = (L.Problem * len(shapes))()
             for i, (M, N, K, p) in enumerate(shapes):
                 arr[i].M, arr[i].N, arr[i].K, arr[i].p = M, N, K, p
-            st = lib().ozaki2_plan_create_batched(len(shapes), arr, C.byref(self._o), C.byref(h))
+            if per_problem is not None:
+                po = (L.Opts * len(shapes))()
+                for i, d in enumerate(per_problem):
+                    po[i] = opts(**d)
+                st = lib().ozaki2_plan_create_batched_ex(len(shapes), arr, C.byref(self._o), po, C.byref(h))
+            else:
+                st = lib().ozaki2_plan_create_batched(len(shapes), arr, C.byref(self._o), C.byref(h))
             self.shapes = list(shapes)
             self.batched = True
         check(st, "ozaki2_plan_create")

@@ -58,6 +58,8 @@ _SIGS = {
                                       C.POINTER(C.c_void_p)]),
     "ozaki2_plan_create_batched": (C.c_int, [C.c_int, C.POINTER(Problem), C.POINTER(Opts),
                                               C.POINTER(C.c_void_p)]),
+    "ozaki2_plan_create_batched_ex": (C.c_int, [C.c_int, C.POINTER(Problem), C.POINTER(Opts), C.POINTER(Opts),
+                                                 C.POINTER(C.c_void_p)]),
     "ozaki2_plan_destroy": (C.c_int, [C.c_void_p]),
     "ozaki2_plan_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "ozaki2_plan_moduli": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int32), C.c_int]),

@@ -311,6 +311,23 @@ cudaError_t init_crt_attributes();
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The shortest prefix of the modulus list with P > inner 2^(2t + 2) (Eq.
+// crtcond with the implementation's +2 margin, Sec. 4.3), or exactly force_L
+// moduli when force_L > 0 (which must still meet the bound); its length, or
+// -1 when the list cannot reach the bound.  *P receives the product.
+static int modulus_prefix(int64_t inner, int t, int force_L, Big* P) {
+  const Big bound = big_shifted((uint64_t)inner, 2 * t + 2);
+  const auto& ml = modulus_list();
+  *P = Big{1u};
+  int L = 0;
+  while (force_L > 0 ? L < force_L : big_cmp(*P, bound) <= 0) {
+    if (L >= (int)ml.size()) return -1;
+    big_mul_small(*P, ml[L]);
+    ++L;
+  }
+  return big_cmp(*P, bound) <= 0 ? -1 : L;
+}
+
 // Tensor-core residue table [rows][kpad] (bf16 bits) of the moduli
 // l0 .. l0 + L - 1 of the list (L1 of them one-limb): row l (one-limb) =
 // cen(2^(8 b) mod m), rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
@@ -354,9 +371,12 @@ static int res_table_key(ozaki2_plan_s* pl, int l0, int L, int L1, int nb, int k
   return (int)pl->rtabs.size() - 1;
 }
 
+// One problem of a plan.  `po` (batched plans) supplies this problem's own
+// guard bits, t, K chunk and residue and CRT engines; the plan's options
+// otherwise.
 static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int p,
-                         const PlanExtra* ex = nullptr) {
-  const ozaki2_opts& o = pl->opts;
+                         const PlanExtra* ex = nullptr, const ozaki2_opts* po = nullptr) {
+  const ozaki2_opts& o = po ? *po : pl->opts;
   const PlanExtra none{};
   if (!ex) ex = &none;
   if (injected_alloc_failure()) throw std::bad_alloc();
@@ -370,17 +390,10 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
   h.t = ex->force_t > 0 ? ex->force_t
                         : (o.t_bits > 0 ? o.t_bits : p + o.guard_bits + ceil_log2(inner));   // Eq. 3
   if (h.t > kMaxP + 64) return OZ2_ERANGE;
-  // shortest modulus prefix with P > inner 2^(2t + 2)   (Eq. crtcond, +2 margin)
-  const Big bound = big_shifted((uint64_t)inner, 2 * h.t + 2);
+  Big P;
+  const int L = modulus_prefix(inner, h.t, ex->force_L, &P);
+  if (L < 0) return OZ2_ERANGE;
   const auto& ml = modulus_list();
-  Big P{1u};
-  int L = 0;
-  while (ex->force_L > 0 ? L < ex->force_L : big_cmp(P, bound) <= 0) {
-    if (L >= (int)ml.size()) return OZ2_ERANGE;
-    big_mul_small(P, ml[L]);
-    ++L;
-  }
-  if (big_cmp(P, bound) <= 0) return OZ2_ERANGE;
   h.kind = ex->kind;
   h.skip_a = ex->skip_a;
   h.skip_b = ex->skip_b;
@@ -471,9 +484,26 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     h.crt_nvbuf = (mm_ok && kpad + h.crt_nslot * h.crt_cw <= 512) ? 2 : 1;
     h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
     const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
-    if (h.crt_mode != 0 && !c.tc_table.empty() && (c.rows != rows || c.npad != h.crt_npad))
-      return OZ2_EINTERNAL;                      // one table per modulus set and CRT engine
-    if (h.crt_mode != 0 && c.tc_table.empty()) {
+    CrtHost* cp = &c;
+    if (h.crt_mode != 0 && !c.tc_table.empty() && (c.rows != rows || c.npad != h.crt_npad)) {
+      // another problem of this modulus set runs the other tensor-core CRT
+      // form: a table of this form exists already, or this problem gets a copy
+      // of the digit tables with its own
+      int other = -1;
+      for (size_t i = 0; i < pl->crts.size(); ++i)
+        if (pl->crts[i].L == L && pl->crts[i].rows == rows && pl->crts[i].npad == h.crt_npad) other = (int)i;
+      if (other < 0) {
+        CrtHost cc;
+        cc.L = c.L; cc.D32 = c.D32; cc.DS = c.DS; cc.cls = c.cls; cc.P = c.P; cc.words = c.words;
+        pl->crts.push_back(std::move(cc));
+        other = (int)pl->crts.size() - 1;
+      }
+      h.crt_key = other;
+      cp = &pl->crts[other];
+    }
+    CrtHost& c2 = *cp;
+    if (h.crt_mode != 0 && c2.tc_table.empty()) {
+      CrtHost& c = c2;
       c.kpad = kpad; c.npad = h.crt_npad; c.np = np; c.rows = rows;
       c.tc_table.assign((size_t)rows * kpad, 0);
       const auto& mlist = modulus_list();
@@ -645,6 +675,25 @@ static void layout_workspace(ozaki2_plan_s* pl) {
   pl->ws_bytes = off;
 }
 
+// Automatic plane GEMM tile of a single product: CTA pairs (256 x 256) where
+// both output dimensions exceed one 128-row tile and the plane products are
+// below 1e13 flop; one SM per 128 x 256 tile for larger products, where the
+// pairs measured slower on one GB300 (1024^3 at p = 256: 0.180 vs 0.188 ms,
+// 4096^3 at p = 53: 2.07 vs 2.16 ms; 8192^3 at p = 53: 17.3 vs 17.0 ms,
+// 4096^3 at p = 2048: 82.2 vs 77.7 ms).
+static bool auto_pair_tiles(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int p) {
+  if (M <= 128 || N <= 128 || p < 2 || K <= 0 || K > kMaxK || p > kMaxP) return false;
+  // planes G from the modulus rule (Eq. 3 and Eq. crtcond), without building the plan
+  const ozaki2_opts& o = pl->opts;
+  const int t = o.t_bits > 0 ? o.t_bits : p + o.guard_bits + ceil_log2(K);
+  Big P;
+  const int L = modulus_prefix(K, t, 0, &P);
+  if (L < 0) return false;
+  const int L1 = std::min(L, one_limb_count());
+  const double G = L1 + 3.0 * (L - L1);
+  return 2.0 * (double)M * (double)N * (double)K * G < 1e13;
+}
+
 static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   auto* pl = new (std::nothrow) ozaki2_plan_s();
   if (!pl) return OZ2_ENOMEM;
@@ -659,7 +708,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
     delete pl;
     return OZ2_EINVAL;
   }
-  pl->tile2 = o.engine == OZ2_ENGINE_TC && o.gemm_tile == 2;
+  pl->tile2 = o.engine == OZ2_ENGINE_TC && o.gemm_tile == 2;   // automatic: decided per plan (plan_tile)
   *res = pl;
   return OZ2_OK;
 }
@@ -1517,6 +1566,7 @@ int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts
   ozaki2_plan_s* pl = nullptr;
   int rc = new_plan(opts, &pl);
   if (rc) return rc;
+  if (pl->opts.gemm_tile == 0 && pl->opts.engine == OZ2_ENGINE_TC) pl->tile2 = auto_pair_tiles(pl, M, N, K, p);
   try {
     rc = build_problem(pl, M, N, K, p);
     if (!rc) rc = plan_groups(pl);
@@ -1531,13 +1581,36 @@ int ozaki2_plan_create(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts
 
 int ozaki2_plan_create_batched(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
                                ozaki2_plan* out) {
+  return ozaki2_plan_create_batched_ex(count, shapes, opts, nullptr, out);
+}
+
+int ozaki2_plan_create_batched_ex(int count, const ozaki2_problem* shapes, const ozaki2_opts* opts,
+                                  const ozaki2_opts* per_problem, ozaki2_plan* out) {
   if (!out || !shapes || count <= 0 || count > 65535) return OZ2_EINVAL;
   *out = nullptr;
   ozaki2_plan_s* pl = nullptr;
   int rc = new_plan(opts, &pl);
   if (rc) return rc;
+  std::vector<ozaki2_opts> po;
+  if (per_problem) {
+    po.assign(count, pl->opts);
+    for (int i = 0; i < count; ++i) {
+      const ozaki2_opts& q = per_problem[i];
+      if (q.guard_bits < 0 || q.t_bits < 0 || q.k_chunk < 0 || q.crt_engine < 0 || q.crt_engine > 3 ||
+          q.res_engine < 0 || q.res_engine > 3) {
+        delete pl;
+        return OZ2_EINVAL;
+      }
+      po[i].guard_bits = q.guard_bits;
+      po[i].t_bits = q.t_bits;
+      po[i].k_chunk = q.k_chunk;
+      po[i].crt_engine = q.crt_engine;
+      po[i].res_engine = q.res_engine;
+    }
+  }
   try {
-    for (int i = 0; i < count && !rc; ++i) rc = build_problem(pl, shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].p);
+    for (int i = 0; i < count && !rc; ++i)
+      rc = build_problem(pl, shapes[i].M, shapes[i].N, shapes[i].K, shapes[i].p, nullptr, po.empty() ? nullptr : &po[i]);
   } catch (const std::bad_alloc&) {
     rc = OZ2_ENOMEM;
   }

@@ -87,30 +87,12 @@ __device__ __forceinline__ void commit_pair(uint64_t* bar) {
       "h"((uint16_t)3)
       : "memory");
 }
+// arrive on a barrier that may live in the peer CTA (default .release.cta
+// semantics: the slot's TMEM reads are ordered by tcgen05.wait::ld and the
+// tcgen05 fences around the arrive and the leader's wait, not by the memory
+// model, so no cluster-scope fence is needed)
 __device__ __forceinline__ void arrive_cluster(uint32_t bar_cluster) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
-}
-__device__ __forceinline__ bool try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait on a barrier that other CTAs of the cluster arrive on
-__device__ __forceinline__ bool wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                             int32_t* status, uint32_t limit) {
-  for (uint32_t it = 0; it < limit; ++it) {
-    if (try_wait_cluster(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (it > 1024) __nanosleep(32);
-  }
-  *abort_flag = 1;
-  atomicOr(status, kStatusTimeout);
-  return false;
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
 __global__ void __launch_bounds__(kThreads2, 1) k_gemm_tc2(const __grid_constant__ DevTables T) {
@@ -216,7 +198,7 @@ __global__ void __launch_bounds__(kThreads2, 1) k_gemm_tc2(const __grid_constant
       const int k0 = j.chunk * P.kchunk;
       const int k1 = min(P.K, k0 + P.kchunk);
       if (uses[s] > 0) {
-        if (!wait_cluster(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status, T.spin_limit)) {
+        if (!mbar_wait(slot_free + s, (uint32_t)((uses[s] - 1) & 1), abort_flag, T.status, T.spin_limit)) {
           ok = false;
           break;
         }
