@@ -239,11 +239,16 @@ SMS = 152
 IMAD_WIDE_PER_SM_CLK = 32
 DP4A_MACS_PER_SM_CLK = 64 * 4
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu capture of the committed kernels on the same workload; the source
-# summaries are under profiles/.  A kernel changed since its capture is absent.
+# DRAM traffic of each stage per execute (dram__bytes_read.sum +
+# dram__bytes_write.sum over the stage's launches, averaged over the four
+# executes of one ncu capture of the committed kernels on the same workload,
+# one pass, the full size); the source summaries are under profiles/.  A
+# kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_1024_p256": {"residues": 443.90144e6, "crt_sums": 223.868672e6, "crt_finish": 123.980288e6},
+    "gemm_4096_p2048": {"scan": 403938240, "residues": 83432203520, "gemm": 157047812288,
+                        "crt_sums": 23148799872, "crt_finish": 16030045888},
+    "gemm_1024_p256": {"scan": 25206464, "residues": 440552128, "gemm": 569037696, "crt_sums": 222713088,
+                       "crt_finish": 121899328},
 }
 
 
@@ -738,6 +743,20 @@ def run_ours(args):
         i8["note"] = ("the plane GEMMs run exact integer products on tcgen05 kind::f16 (bf16 operands, "
                       "fp32 accumulation kept exact by K chunks); their integer-operation rate is stated "
                       "against this GPU's INT8 tensor peak, which is below the bf16 rate")
+        # the second plane GEMM engine (INT8 x INT8 -> INT32 on mma.sync) against the default,
+        # same product, same bits
+        ab = {}
+        for eng, label in ((0, "tcgen05_bf16"), (2, "mma_sync_s8")):
+            rr = measure_single(g, ozk, "gemm_1024_p256", 20 if eng == 0 else 5, 3, e2e=False, engine=eng)
+            gm = rr["stages"]["gemm"]
+            ops = 2.0 * 1024 ** 3 * rr["info"]["G"]
+            ab[label] = {"gemm_ms": round(gm, 4), "int_tops": round(ops / (gm / 1e3) / 1e12, 1),
+                         "frac_of_int8_peak": round(ops / (gm / 1e3) / 1e12 / i8["int8_peak_tops"], 3),
+                         "ms_per_step": round(rr["ms"], 4)}
+            del rr
+            torch.cuda.empty_cache()
+        ab["workload"] = "gemm_1024_p256"
+        i8["engines"] = ab
         sweep["int8"] = i8
         line["sweep"] = sweep
         line["clocks_sweep_excluded"] = "clocks are sampled over the main workload's timed region"
@@ -799,7 +818,8 @@ def run_workload_only(args):
     elif args.workload == "dgemm4096_autograd":
         out = measure_autograd(g, args.steps, args.warmup)
     else:
-        out = _single_summary(measure_single(g, ozk, args.workload, args.steps, args.warmup, e2e=False))
+        kw = {"gemm_tile": args.gemm_tile} if args.gemm_tile else {}
+        out = _single_summary(measure_single(g, ozk, args.workload, args.steps, args.warmup, e2e=False, **kw))
     out.update({"metric": METRIC, "workload": args.workload, "steps": args.steps, "warmup": args.warmup,
                 "impl": "ours", "only": True})
     print(json.dumps(out), flush=True)
@@ -818,6 +838,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", action="store_true",
                     help="time the workload alone (device-resident), e.g. under a profiler")
+    ap.add_argument("--gemm-tile", type=int, default=0, choices=[0, 1, 2],
+                    help="with --only: plane GEMM tile (0 automatic, 1 one SM, 2 CTA pairs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

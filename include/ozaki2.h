@@ -69,7 +69,11 @@ enum {
 /* GEMM engines for the per-plane products. */
 enum {
   OZ2_ENGINE_TC = 0,   /* tcgen05 kind::f16 tensor-core kernel (TMA + TMEM), default */
-  OZ2_ENGINE_SIMT = 1  /* CUDA-core int32 kernel: slow cross-check engine */
+  OZ2_ENGINE_SIMT = 1, /* CUDA-core int32 kernel: slow cross-check engine */
+  OZ2_ENGINE_S8 = 2    /* INT8 x INT8 -> INT32 on the warp-level tensor-core instruction
+                          mma.sync m16n8k32 (sm_103a has no tcgen05 INT8 form): the second
+                          engine, for comparison at equal accuracy; bf16 planes converted to
+                          int8 while staged in shared memory */
 };
 
 /* Plane schedules. */
@@ -243,6 +247,14 @@ OZ2_API int ozaki2_plan_debug_corrupt_crt(ozaki2_plan plan, int prob);
    OZ2_ENOMEM without allocating; 0 cancels.  Nothing half-made is kept: a
    later call with the same arguments starts over. */
 OZ2_API int ozaki2_debug_inject_alloc_failure(int count);
+
+/* Debugging aid: when dev_buf is not NULL, later executes of the tensor-core
+   engine also write the exact sum of every plane product before any
+   reduction, C_g[i][j] = sum_k r_a[g][i][k] r_b[g][k][j] (Sec. 2.4: the
+   integer GEMM output of plane g), to dev_buf (device, int32 [G][M][N],
+   plane order as in ozaki2_plan_layout).  Only for problems whose K fits in
+   one exact accumulation chunk (K <= k_chunk); OZ2_EINVAL otherwise. */
+OZ2_API int ozaki2_plan_set_debug_prods(ozaki2_plan plan, int prob, int32_t* dev_buf);
 
 /* Run the plan: C = A * B rounded to p bits, via workspace `ws` (device,
    >= info.workspace_bytes, 256-byte aligned, caller-owned, contents need not

@@ -152,6 +152,11 @@ class Plan:
         check(lib().ozaki2_plan_launches(self._h, C.byref(n)), "ozaki2_plan_launches")
         return n.value
 
+    def set_debug_prods(self, prob: int, buf: torch.Tensor | None):
+        """Exact plane sums before reduction, int32 [G][M][N] (K within one chunk)."""
+        check(lib().ozaki2_plan_set_debug_prods(self._h, prob, None if buf is None else buf.data_ptr()),
+              "ozaki2_plan_set_debug_prods")
+
     def set_debug_chat(self, prob: int, buf: torch.Tensor | None):
         check(lib().ozaki2_plan_set_debug_chat(self._h, prob, None if buf is None else buf.data_ptr()),
               "ozaki2_plan_set_debug_chat")

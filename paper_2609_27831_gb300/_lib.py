@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libozaki2_gb300.so")
 
 OZ2_OK, OZ2_EINVAL, OZ2_ERANGE, OZ2_ENOMEM, OZ2_ECUDA, OZ2_EINTERNAL, OZ2_ETIMEOUT, OZ2_ENODEV = range(8)
-ENGINE_TC, ENGINE_SIMT = 0, 1
+ENGINE_TC, ENGINE_SIMT, ENGINE_S8 = 0, 1, 2
 SCHED_GROUPED, SCHED_PLAIN = 0, 1
 
 
@@ -70,6 +70,7 @@ _SIGS = {
     "ozaki2_plan_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "ozaki2_plan_set_debug_chat": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "ozaki2_plan_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "ozaki2_plan_set_debug_prods": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "ozaki2_plan_debug_corrupt_crt": (C.c_int, [C.c_void_p, C.c_int]),
     "ozaki2_debug_inject_alloc_failure": (C.c_int, [C.c_int]),
     "ozaki2_execute": (C.c_int, [C.c_void_p, C.POINTER(Mat), C.POINTER(Mat), C.POINTER(Mat),

@@ -233,7 +233,7 @@ struct DevState {
   void* mem = nullptr;
   DevTables tab{};
   const Unit* unsorted = nullptr;
-  ListRef scan_rows, scan_cols, simt;
+  ListRef scan_rows, scan_cols, simt, s8;
   ListRef res[6], crt[kCrtClassCount];
   const int32_t* cta_grouped = nullptr;
   int grid = 0;
@@ -281,6 +281,7 @@ struct ozaki2_plan_s {
   oz2::DevState dev;
   oz2::LaunchBlock lb;
   std::vector<uint32_t*> dbg_chat;
+  std::vector<int32_t*> dbg_prods;
   // stage boundaries: scan, residues, GEMM, CRT, end; [5] between the
   // tensor-core CRT sums and the rest of the CRT stage
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -701,7 +702,7 @@ static int new_plan(const ozaki2_opts* opts, ozaki2_plan_s** res) {
   else ozaki2_opts_default(&pl->opts);
   const ozaki2_opts& o = pl->opts;
   if (o.guard_bits < 0 || o.t_bits < 0 || o.grid < 0 || o.k_chunk < 0 ||
-      (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT) ||
+      (o.engine != OZ2_ENGINE_TC && o.engine != OZ2_ENGINE_SIMT && o.engine != OZ2_ENGINE_S8) ||
       (o.schedule != OZ2_SCHED_GROUPED && o.schedule != OZ2_SCHED_PLAIN) ||
       (o.crt_engine < 0 || o.crt_engine > 3) || (o.res_engine < 0 || o.res_engine > 3) ||
       o.plane_group < -1 || (o.plane_group > 0 && o.plane_group < 3) || o.gemm_tile < 0 || o.gemm_tile > 2) {
@@ -744,9 +745,9 @@ struct Builder {
 struct TableImage {
   Builder b;
   size_t o_mods = 0, o_t16 = 0, o_pool = 0, o_units = 0, o_ordered = 0, o_ctag = 0, o_ctap = 0,
-         o_srows = 0, o_scols = 0, o_simt = 0, o_status = 0;
+         o_srows = 0, o_scols = 0, o_simt = 0, o_s8 = 0, o_status = 0;
   size_t o_res[6] = {0}, o_crt[kCrtClassCount] = {0};
-  int n_srows = 0, n_scols = 0, n_simt = 0, n_res[6] = {0}, n_crt[kCrtClassCount] = {0};
+  int n_srows = 0, n_scols = 0, n_simt = 0, n_s8 = 0, n_res[6] = {0}, n_crt[kCrtClassCount] = {0};
   int res_l[6] = {0}, crt_l[kCrtClassCount] = {0};
   int grid = 0;
   // tensor-core CRT: tile lists per one-lane class, table offsets per CRT key
@@ -999,12 +1000,18 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.crt_l[h.crt_cls] = std::max(ti.crt_l[h.crt_cls], h.L);
     }
   }
+  std::vector<int4> s8;
   for (int u = 0; u < nunits; ++u) {
     const ProbHost& h = pl->probs[units[u].prob];
     const int64_t r0 = (int64_t)units[u].tm * kBM, c0 = (int64_t)units[u].tn * kBN;
-    for (int sy = 0; sy < kBM / 32; ++sy)
-      for (int sx = 0; sx < kBN / 32; ++sx)
-        if (r0 + 32 * sy < h.M && c0 + 32 * sx < h.N) simt.push_back(make_int4(u, sy, sx, 0));
+    if (pl->opts.engine == OZ2_ENGINE_SIMT) {
+      for (int sy = 0; sy < kBM / 32; ++sy)
+        for (int sx = 0; sx < kBN / 32; ++sx)
+          if (r0 + 32 * sy < h.M && c0 + 32 * sx < h.N) simt.push_back(make_int4(u, sy, sx, 0));
+    }
+    if (pl->opts.engine == OZ2_ENGINE_S8)
+      for (int half = 0; half < 2; ++half)
+        if (c0 + 128 * half < h.N) s8.push_back(make_int4(u, half, 0, 0));
   }
 
   ti.o_mods = ti.b.add(mods.data(), mods.size() * sizeof(ModConst));
@@ -1024,6 +1031,8 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   ti.o_srows = ti.b.add(scan_rows.data(), scan_rows.size() * 16);
   ti.o_scols = ti.b.add(scan_cols.data(), scan_cols.size() * 16);
   ti.o_simt = ti.b.add(simt.data(), simt.size() * 16);
+  ti.o_s8 = ti.b.add(s8.data(), s8.size() * 16);
+  ti.n_s8 = (int)s8.size();
   for (int i = 0; i < 6; ++i) ti.o_res[i] = ti.b.add(res[i].data(), res[i].size() * 16);
   for (int i = 0; i < kCrtClassCount; ++i) ti.o_crt[i] = ti.b.add(crt[i].data(), crt[i].size() * 16);
   ti.o_status = ti.b.add(nullptr, 256);
@@ -1108,6 +1117,7 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   d.scan_rows = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_srows), ti.n_srows, 0, 0, ti.na_srows};
   d.scan_cols = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_scols), ti.n_scols, 0, 0};
   d.simt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_simt), ti.n_simt, 0, 0};
+  d.s8 = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_s8), ti.n_s8, 0, 0};
   for (int i = 0; i < 6; ++i)
     d.res[i] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_res[i]), ti.n_res[i],
                        ti.res_l[i] * (residue_class_w16(i) + 4) * 4, ti.res_l[i], ti.na_res[i]};
@@ -1269,6 +1279,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     }
     P.DS = h.DS;
     P.dbg_chat = pl->dbg_chat.empty() ? nullptr : pl->dbg_chat[i];
+    P.dbg_prods = pl->dbg_prods.empty() ? nullptr : pl->dbg_prods[i];
     P.upitch = (int64_t)align_up((size_t)(h.M * h.N), 8);
     P.res_mode = h.res_mode;
     P.res_kpad = h.res_kpad;
@@ -1339,6 +1350,9 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
       Q.crt_off = pd[0].crt_off + gr.l0;
       Q.res_npad = gr.res_npad; Q.res_cw = gr.res_cw; Q.res_nchunk = gr.res_nchunk; Q.res_nabuf = gr.res_nabuf;
       Q.dbg_chat = nullptr;
+      int gfirst = 0;                                    // planes of the groups before this one
+      for (size_t q = 0; q < g; ++q) gfirst += h.groups[q].G;
+      if (Q.dbg_prods) Q.dbg_prods += (int64_t)gfirst * h.M * h.N;
       CUtensorMap* gm = tm + 5 * count + 5 * g;
       int rc = encode_planes(&gm[0], Q.pa, h.K, h.M, h.Kp, gr.G, kBM);
       if (rc) return rc;
@@ -1438,6 +1452,10 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
       DevTables t2 = tab;
       t2.units = d.unsorted;
       OZ2_CU(launch_gemm_simt(t2, d.simt.ptr, d.simt.n, s));
+    } else if (pl->opts.engine == OZ2_ENGINE_S8) {
+      DevTables t2 = tab;
+      t2.units = d.unsorted;
+      OZ2_CU(launch_gemm_s8(t2, d.s8.ptr, d.s8.n, s));
     } else if (pl->opts.schedule == OZ2_SCHED_GROUPED) {
       OZ2_CU(pl->tile2 ? launch_gemm_tc2(tab, d.grid, s) : launch_gemm_tc(tab, d.grid, s));
     } else {
@@ -1699,7 +1717,7 @@ int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
   res += d.rtt.n ? 1 : 0;
   res += (int)d.rmt.size();
   if (!d.groups.empty()) c += (int)d.groups.size() * (res + 1);   // per group: residues + one GEMM
-  else if (pl->opts.engine == OZ2_ENGINE_SIMT) c += res + 1;
+  else if (pl->opts.engine == OZ2_ENGINE_SIMT || pl->opts.engine == OZ2_ENGINE_S8) c += res + 1;
   else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += res + 1;
   else c += res + (int)d.plain.size();
   c += (int)d.cmt.size();
@@ -1715,6 +1733,14 @@ int ozaki2_plan_set_debug_chat(ozaki2_plan pl, int prob, uint32_t* dev_buf) {
   if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
   if (pl->dbg_chat.empty()) pl->dbg_chat.assign(pl->probs.size(), nullptr);
   pl->dbg_chat[prob] = dev_buf;
+  return OZ2_OK;
+}
+
+int ozaki2_plan_set_debug_prods(ozaki2_plan pl, int prob, int32_t* dev_buf) {
+  if (!pl || prob < 0 || prob >= (int)pl->probs.size()) return OZ2_EINVAL;
+  if (dev_buf && (pl->probs[prob].nchunks != 1 || pl->opts.engine != OZ2_ENGINE_TC)) return OZ2_EINVAL;
+  if (pl->dbg_prods.empty()) pl->dbg_prods.assign(pl->probs.size(), nullptr);
+  pl->dbg_prods[prob] = dev_buf;
   return OZ2_OK;
 }
 

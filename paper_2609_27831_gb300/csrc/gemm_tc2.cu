@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(kThreads2, 1) k_gemm_tc2(const __grid_constant
       for (int c = 0; c < 4; ++c) {
         uint32_t v[32];
         tmem_ld32(tbase + (uint32_t)(c * 32), v);
+        if (P.dbg_prods != nullptr)
+          dbg_plane_sums(P.dbg_prods, j.plane, j.first, PM, PN, row, col_base + c * 32, tbase + (uint32_t)(c * 32));
         if (!j.last) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
@@ -273,6 +275,9 @@ __global__ void __launch_bounds__(kThreads2, 1) k_gemm_tc2(const __grid_constant
             v[i] = __float_as_uint(small_u2f(r));
           }
           tmem_st32(tbase + (uint32_t)(c * 32), v);
+          if (P.dbg_prods != nullptr)
+            dbg_write_back(P.dbg_prods, j.plane, j.u.ell, P.L1, PM, PN, row, col_base + c * 32,
+                           tbase + (uint32_t)(c * 32));
         } else {
 #pragma unroll
           for (int i = 0; i < 32; ++i) {

@@ -94,6 +94,7 @@ struct ProbDev {
   int32_t crt_nslot;     // crt_mode 2: TMEM accumulator slots (1 or 2)
   int32_t res_nabuf;     // res_mode 2: byte buffers (A) in TMEM (2 or 4)
   int32_t pad9;
+  int32_t* dbg_prods;    // optional (K within one chunk): [G][M][N] exact plane sums before reduction
 };
 
 // CRT tables of one modulus prefix, laid out in a uint32 pool at crt_off,
@@ -160,6 +161,8 @@ cudaError_t launch_gemm_tc(const DevTables& t, int grid, cudaStream_t s);
 cudaError_t launch_gemm_tc2(const DevTables& t, int pairs, cudaStream_t s);
 cudaError_t launch_gemm_simt(const DevTables& t, const int32_t* unit_list, int nunits,
                              cudaStream_t s);
+// INT8 mma.sync engine: blocks {unit index (units in problem order), half of the 256 columns}.
+cudaError_t launch_gemm_s8(const DevTables& t, const int32_t* list, int n, cudaStream_t s);
 cudaError_t launch_crt(const DevTables& t, int cls, const int32_t* blk_list, int nblk, int lmax,
                        cudaStream_t s);
 // Tensor-core CRT for one-lane class `cls` (0..8): tiles of 128 outputs.

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "oz2_internal.h"
+#include "tc_ptx.cuh"
 
 namespace oz2 {
 namespace plane {
@@ -93,6 +94,38 @@ struct JobIter {
     return true;
   }
 };
+
+// Debugging aid: the exact sum of each plane product before any reduction,
+// when K fits in one accumulation chunk.  A job's accumulator holds its
+// plane's sum plus the value the unit's previous job wrote back; that job
+// leaves the written-back value in this plane's debug slot, so
+// dbg_plane_sums subtracts it, and dbg_write_back leaves the current job's
+// for the next plane (Karatsuba order P0, Ps, P2 = planes g0, g0 + 2, g0 + 1).
+// Both read the 32 columns at taddr from tensor memory themselves (whole warp)
+// and are kept out of line, so that the epilogue's registers and code stay as
+// they are when no dump is asked for.
+static __device__ __noinline__ void dbg_plane_sums(int32_t* dbg, int plane, bool first, int M, int N, int row,
+                                                   int col0, uint32_t taddr) {
+  uint32_t v[32];
+  tc::tmem_ld32(taddr, v);
+  if (row >= M) return;
+  int32_t* d = dbg + ((int64_t)plane * M + row) * N + col0;
+  for (int i = 0; i < 32 && col0 + i < N; ++i) {
+    const int32_t acc = __float2int_rn(__uint_as_float(v[i]));
+    d[i] = first ? acc : acc - d[i];
+  }
+}
+static __device__ __noinline__ void dbg_write_back(int32_t* dbg, int plane, int ell, int L1, int M, int N,
+                                                   int row, int col0, uint32_t taddr) {
+  uint32_t v[32];
+  tc::tmem_wait_st();
+  tc::tmem_ld32(taddr, v);
+  if (row >= M || ell < L1) return;
+  const int g0 = L1 + 3 * (ell - L1);
+  const int next = plane == g0 ? g0 + 2 : g0 + 1;
+  int32_t* d = dbg + ((int64_t)next * M + row) * N + col0;
+  for (int i = 0; i < 32 && col0 + i < N; ++i) d[i] = __float2int_rn(__uint_as_float(v[i]));
+}
 
 }  // namespace plane
 }  // namespace oz2

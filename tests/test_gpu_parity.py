@@ -13,6 +13,7 @@ import pytest
 
 import synth
 from oracle import ozaki2_oracle as o
+from ties_cases import final_rounding_ties, integerization_ties, mat_from_values
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -144,7 +145,7 @@ def test_engines_and_schedules_agree(ozk):
     A = synth.mp_matrix(rng, 200, 96, 300, -10, 10)
     B = synth.mp_matrix(rng, 96, 300, 300, -10, 10)
     base = run_gpu(ozk, A, B, 300, debug=False)
-    for kw in ({"engine": 1}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}, {"crt_engine": 1},
+    for kw in ({"engine": 1}, {"engine": 2}, {"schedule": 1}, {"grid": 7}, {"k_chunk": 128}, {"crt_engine": 1},
                {"res_engine": 1}):
         other = run_gpu(ozk, A, B, 300, debug=False, **kw)
         assert np.array_equal(other["u"], base["u"]), kw
@@ -588,3 +589,80 @@ def test_operand_reuse(ozk, p, shape, kw):
         streamed.execute(dA, dB1, C1, w2)
         with pytest.raises(ozk.OzakiError):
             streamed.execute_reuse(0, ozk.MPMatrix.from_host(B2), C2, w2)
+
+
+@pytest.mark.parametrize("p", [53, 113, 256])
+@pytest.mark.parametrize("res_engine", [2, 3])
+def test_integerization_ties(ozk, p, res_engine):
+    """Entries whose integerization drops exactly half a step (even and odd
+    kept bits, both signs) or just off it: planes, CRT integers and outputs
+    bit-exact against the oracle (whose rounding is pinned to round(Fraction))
+    on both residue engines."""
+    K = 3
+    rows, t, d = integerization_ties(p, K)
+    A = mat_from_values(rows, p)
+    rng = np.random.Generator(np.random.PCG64(7400 + p))
+    B = synth.mp_matrix(rng, K, 5, p, -3, 3)
+    got, ref = assert_full_parity(ozk, A, B, p, truth=False, res_engine=res_engine)
+    assert got["plan"].info["t"] == t
+
+
+@pytest.mark.parametrize("p", [53, 256])
+def test_final_rounding_ties(ozk, p):
+    """Products whose exact value is a tie at p bits (or just off one, or
+    carries into a new bit): outputs equal to the values fixed by hand."""
+    cases = final_rounding_ties(p)
+    A = mat_from_values([c[0] for c in cases], p)
+    B = mat_from_values([[(1, 0)] for _ in range(3)], p)
+    got, _ = assert_full_parity(ozk, A, B, p)
+    for i, (_, want) in enumerate(cases):
+        assert o.to_fraction(*o.matrix_entry(got["C"], i, 0)) == Fraction(want, 1 << 10), i
+
+
+@pytest.mark.parametrize("shape,p,kw", [
+    ((100, 130, 200), 53, {}),                                  # one-limb planes only
+    ((90, 300, 257), 256, {"gemm_tile": 1}),                    # two-limb Karatsuba planes, one-SM tiles
+    ((300, 90, 128), 256, {"gemm_tile": 2}),                    # CTA-pair tiles
+    ((150, 120, 100), 256, {"plane_group": 20}),                # planes streamed in groups
+])
+def test_plane_sums_before_reduction(ozk, shape, p, kw):
+    """The exact integer GEMM output of every plane, C_g = sum_k r_a r_b
+    before any reduction (dumped by the tensor-core epilogue), equals the
+    oracle's plane products bit for bit."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(7500 + M + p))
+    A = synth.mp_matrix(rng, M, K, p, -8, 8)
+    B = synth.mp_matrix(rng, K, N, p, -8, 8)
+    plan = ozk.Plan((M, N, K, p), **kw)
+    G = plan.info["G"]
+    buf = torch.full((G, M, N), -7, dtype=torch.int32, device="cuda")
+    plan.set_debug_prods(0, buf)
+    dC = ozk.MPMatrix.empty(M, N, p)
+    plan.execute(ozk.MPMatrix.from_host(A), ozk.MPMatrix.from_host(B), dC, plan.workspace())
+    plan.check()
+    torch.cuda.synchronize()
+    ref = o.ozaki2_full(A, B, p)
+    assert np.array_equal(buf.cpu().numpy().astype(np.int64), ref["prods"])
+    h = dC.to_host()
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(h[key], ref["C"][key]), key
+
+
+def test_plane_sums_need_one_chunk(ozk):
+    plan = ozk.Plan((64, 64, 2000, 113))             # K above one 1024 chunk
+    buf = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ozk.OzakiError):
+        plan.set_debug_prods(0, buf)
+
+
+@pytest.mark.parametrize("shape,p", [((130, 300, 77), 256),      # two-limb moduli, ragged tiles, K tail
+                                     ((40, 20, 2100), 53),       # K above one accumulation chunk
+                                     ((257, 129, 33), 113)])     # a column tile with one 128-half
+def test_int8_mma_engine_bit_exact(ozk, shape, p):
+    """The second plane GEMM engine (INT8 x INT8 -> INT32 on mma.sync) gives
+    the oracle's v_l, CRT integers and outputs bit for bit."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(7600 + M + p))
+    A = synth.mp_matrix(rng, M, K, p, -8, 8)
+    B = synth.mp_matrix(rng, K, N, p, -8, 8)
+    assert_full_parity(ozk, A, B, p, truth=False, engine=2)
