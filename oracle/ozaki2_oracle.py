@@ -656,3 +656,138 @@ def dgemm_dB_entry(X, dC, k, j, par: Params, e=None) -> float:
 def exact_dot_double(xs, ys) -> float:
     """Correctly rounded binary64 value of sum x*y (exact rational sum)."""
     return float(sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(xs, ys)))
+
+
+# ---------------------------------------------------------------------------
+# Complex products, 3M form in the residue domain (the paper's Sec. 11 names
+# complex 3M/4M products as future work; this is the reading used here).
+# C = (Ar + i Ai)(Br + i Bi).  Rows of Ar and Ai share one exponent e_i (the
+# largest over both), columns of Br and Bi one f_j, so that all four integer
+# matrices carry the same scale and Cr_hat = sum ar br - ai bi and
+# Ci_hat = sum ar bi + ai br are exact integers with |C_hat| <= 2K 2^(2t); t
+# and the modulus set are chosen for inner length 2K.  Per modulus, three
+# plane products T1 = ar br, T2 = ai bi, T3 = (ar + ai)(br + bi) of centered
+# residues (the sums' residues are those of the integer sums), then
+# u_r = T1 - T2 and u_i = T3 - T1 - T2 mod m, the direct CRT of each, and
+# one rounding of each part to p bits.
+# ---------------------------------------------------------------------------
+
+def complex_params(K: int, p: int, g: int = GUARD_BITS) -> Params:
+    """t and the modulus set of a complex product: inner length 2K."""
+    return Params(K, p, g, inner=2 * K)
+
+
+def joint_exponent(mats, r: int, axis: int) -> int:
+    """Largest MPFR exponent over the nonzero entries of row r (axis=0) or
+    column r (axis=1) of every matrix in mats; 0 when all of them are zero."""
+    best = None
+    for mat in mats:
+        R, C = mat["exp"].shape
+        n = C if axis == 0 else R
+        for k in range(n):
+            rr, cc = (r, k) if axis == 0 else (k, r)
+            ssig, e, _ = decode(mat, rr, cc)
+            if ssig != 0 and (best is None or e > best):
+                best = e
+    return 0 if best is None else best
+
+
+def joint_lines(mats, r: int, axis: int, t: int):
+    """The integerized lines of each matrix with their joint shared exponent."""
+    e = joint_exponent(mats, r, axis)
+    out = []
+    for mat in mats:
+        R, C = mat["exp"].shape
+        n = C if axis == 0 else R
+        line = []
+        for k in range(n):
+            rr, cc = (r, k) if axis == 0 else (k, r)
+            ssig, ex, nl = decode(mat, rr, cc)
+            line.append(integerize(ssig, ex, nl, e, t))
+        out.append(line)
+    return out, e
+
+
+def complex_entry(ar, ai, e_i, br, bi, f_j, par: Params) -> dict:
+    """All stages of one complex output entry (3M in the residue domain)."""
+    def planes(xs):
+        return [plane_values(x, par.moduli) for x in xs]
+    pa_r, pa_i = planes(ar), planes(ai)
+    pa_s = planes([x + y for x, y in zip(ar, ai)])
+    pb_r, pb_i = planes(br), planes(bi)
+    pb_s = planes([x + y for x, y in zip(br, bi)])
+    K = len(ar)
+
+    def prods(pa, pb):
+        out = [sum(pa[k][g] * pb[k][g] for k in range(K)) for g in range(par.G)]
+        assert all(abs(c) < 2 ** 31 for c in out)
+        return out
+    T1, T2, T3 = prods(pa_r, pb_r), prods(pa_i, pb_i), prods(pa_s, pb_s)
+    u1, u2, u3 = (reduce_planes(T, par.moduli) for T in (T1, T2, T3))
+    u_r = [(a - b) % m for a, b, m in zip(u1, u2, par.moduli)]
+    u_i = [(c - a - b) % m for a, b, c, m in zip(u1, u2, u3, par.moduli)]
+    chat_r, chat_i = crt_signed(u_r, par.tab), crt_signed(u_i, par.tab)
+    out = {"T1": T1, "T2": T2, "T3": T3, "u_r": u_r, "u_i": u_i, "chat_r": chat_r, "chat_i": chat_i}
+    for part, chat in (("r", chat_r), ("i", chat_i)):
+        sg, S, e = round_to_p(chat, e_i + f_j - 2 * par.t, par.p)
+        out["C" + part] = encode_rounded(sg, S, e, par.p)
+    return out
+
+
+def complex_entries(Ar, Ai, Br, Bi, p: int, pairs, g: int = GUARD_BITS) -> list[dict]:
+    """The complex method at the listed (i, j) output entries."""
+    K = Ar["exp"].shape[1]
+    par = complex_params(K, p, g)
+    rows = {i: joint_lines([Ar, Ai], i, 0, par.t) for i in sorted({i for i, _ in pairs})}
+    cols = {j: joint_lines([Br, Bi], j, 1, par.t) for j in sorted({j for _, j in pairs})}
+    out = []
+    for i, j in pairs:
+        (ar, ai), e_i = rows[i]
+        (br, bi), f_j = cols[j]
+        out.append(complex_entry(ar, ai, e_i, br, bi, f_j, par))
+    return out
+
+
+def complex_full(Ar, Ai, Br, Bi, p: int, g: int = GUARD_BITS) -> dict:
+    """The complex method for every entry of a small product: Cr and Ci in the
+    storage format, with the CRT integers and the reduced values."""
+    M, K = Ar["exp"].shape
+    N = Br["exp"].shape[1]
+    nl = (p + 63) // 64
+    ents = complex_entries(Ar, Ai, Br, Bi, p, [(i, j) for i in range(M) for j in range(N)], g)
+    res = {"par": complex_params(K, p, g)}
+    for part in ("r", "i"):
+        limbs = np.zeros((nl, M, N), dtype=np.uint64)
+        exp = np.zeros((M, N), dtype=np.int32)
+        sign = np.zeros((M, N), dtype=np.int8)
+        chat = np.empty((M, N), dtype=object)
+        u = np.zeros((len(res["par"].moduli), M, N), dtype=np.int64)
+        for n, e in enumerate(ents):
+            i, j = divmod(n, N)
+            lb, ex, sg = e["C" + part]
+            for q in range(nl):
+                limbs[q, i, j] = lb[q]
+            exp[i, j], sign[i, j] = ex, sg
+            chat[i, j] = e["chat_" + part]
+            u[:, i, j] = e["u_" + part]
+        res["C" + part] = {"p": p, "limbs": limbs, "exp": exp, "sign": sign}
+        res["chat_" + part] = chat
+        res["u_" + part] = u
+    return res
+
+
+def complex_truth_entry(Ar, Ai, Br, Bi, i: int, j: int, p: int):
+    """Exact real and imaginary parts of entry (i, j), each rounded once."""
+    K = Ar["exp"].shape[1]
+    re = sum(value(Ar, i, k) * value(Br, k, j) - value(Ai, i, k) * value(Bi, k, j) for k in range(K))
+    im = sum(value(Ar, i, k) * value(Bi, k, j) + value(Ai, i, k) * value(Br, k, j) for k in range(K))
+    out = []
+    for x in (re, im):
+        if x == 0:
+            out.append(encode_rounded(0, 0, 0, p))
+            continue
+        lo = x.denominator.bit_length() - 1               # dyadic: denominator 2^lo
+        num = x.numerator                                  # x = num 2^-lo
+        sg, S, e = round_to_p(num, -lo, p)
+        out.append(encode_rounded(sg, S, e, p))
+    return out
