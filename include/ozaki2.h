@@ -324,6 +324,34 @@ OZ2_API int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const oz
    gave up).  Allocates nothing. */
 OZ2_API int ozaki2_noalloc_check(void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Complex products in 3M form in the residue domain (the paper names complex
+ * 3M/4M products as future work, Sec. 11): C = (Ar + i Ai)(Br + i Bi) for
+ * p-bit parts.  Rows of Ar and Ai share one exponent, columns of Br and Bi
+ * one, so that Cr_hat = sum ar br - ai bi and Ci_hat = sum ar bi + ai br are
+ * exact integers below 2K 2^(2t) (t and the moduli chosen for inner length
+ * 2K); per modulus three plane products, T1 = ar br, T2 = ai bi and
+ * T3 = (ar + ai)(br + bi) (the sums' residue planes formed from the parts'),
+ * then u_r = T1 - T2 and u_i = T3 - T1 - T2 mod m, the direct CRT of each and
+ * one rounding of each part to p bits.
+ * ------------------------------------------------------------------------- */
+
+/* A plan of three real products (Ar Br, Ai Bi and the sums' product) sharing
+   the exponents; ozaki2_plan_info reports count 3.  Host only. */
+OZ2_API int ozaki2_plan_create_complex(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts,
+                                       ozaki2_plan* out);
+
+/* Run a complex plan (workspace as for ozaki2_execute).  Cr and Ci are M x N
+   p-bit matrices written with the real and imaginary parts. */
+OZ2_API int ozaki2_execute_complex(ozaki2_plan plan, const ozaki2_mat* Ar, const ozaki2_mat* Ai,
+                                   const ozaki2_mat* Br, const ozaki2_mat* Bi, ozaki2_mat* Cr, ozaki2_mat* Ci,
+                                   void* ws, size_t ws_bytes, void* stream);
+
+/* Convenience call with a library-owned plan and workspace (as ozaki2_gemm). */
+OZ2_API int ozaki2_zgemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* Ar, const ozaki2_mat* Ai,
+                         const ozaki2_mat* Br, const ozaki2_mat* Bi, ozaki2_mat* Cr, ozaki2_mat* Ci,
+                         const ozaki2_opts* opts, void* stream);
+
 /* Convenience batched call (library-owned plan and workspace). */
 OZ2_API int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts,
                         void* stream);

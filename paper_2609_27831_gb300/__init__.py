@@ -16,7 +16,8 @@ import torch
 from . import _lib as L
 from ._lib import OzakiError, check, lib, opts  # noqa: F401
 
-__all__ = ["MPMatrix", "Plan", "Graph", "gemm", "gemm_batched", "OzakiError", "lib", "opts"]
+__all__ = ["MPMatrix", "Plan", "ComplexPlan", "Graph", "gemm", "gemm_batched", "zgemm", "OzakiError", "lib",
+           "opts"]
 
 
 def _stream_handle(stream) -> int:
@@ -206,6 +207,44 @@ class Plan:
         ms = (C.c_float * 2)()
         check(lib().ozaki2_last_crt_split(self._h, ms), "ozaki2_last_crt_split")
         return {"crt_sums": ms[0], "crt_finish": ms[1]}
+
+
+class ComplexPlan(Plan):
+    """A plan for one complex product (Ar + i Ai)(Br + i Bi), 3M form."""
+
+    def __init__(self, shape, **kw):
+        self._o = opts(**kw)
+        h = C.c_void_p()
+        M, N, K, p = shape
+        check(lib().ozaki2_plan_create_complex(M, N, K, p, C.byref(self._o), C.byref(h)),
+              "ozaki2_plan_create_complex")
+        self.shapes = [shape]
+        self.batched = False
+        self._h = h
+        inf = L.Info()
+        check(lib().ozaki2_plan_info(h, C.byref(inf)), "ozaki2_plan_info")
+        self.info = {f: getattr(inf, f) for f, _ in L.Info._fields_}
+        self.workspace_bytes = inf.workspace_bytes
+
+    def execute_complex(self, Ar: MPMatrix, Ai: MPMatrix, Br: MPMatrix, Bi: MPMatrix, Cr: MPMatrix, Ci: MPMatrix,
+                        ws: torch.Tensor, stream=None):
+        d = [x.desc() for x in (Ar, Ai, Br, Bi, Cr, Ci)]
+        check(lib().ozaki2_execute_complex(self._h, *[C.byref(x) for x in d], ws.data_ptr(), ws.numel(),
+                                           _stream_handle(stream)), "ozaki2_execute_complex")
+
+
+def zgemm(Ar: MPMatrix, Ai: MPMatrix, Br: MPMatrix, Bi: MPMatrix, p: int | None = None, stream=None, **kw):
+    """(Cr, Ci) = (Ar + i Ai)(Br + i Bi) rounded to p bits per part (cached plan)."""
+    p = p or Ar.p
+    M, K = Ar.shape
+    N = Br.shape[1]
+    Cr = MPMatrix.empty(M, N, p, device=Ar.limbs.device)
+    Ci = MPMatrix.empty(M, N, p, device=Ar.limbs.device)
+    o = opts(**kw)
+    d = [x.desc() for x in (Ar, Ai, Br, Bi, Cr, Ci)]
+    check(lib().ozaki2_zgemm(M, N, K, p, *[C.byref(x) for x in d], C.byref(o), _stream_handle(stream)),
+          "ozaki2_zgemm")
+    return Cr, Ci
 
 
 def gemm(A: MPMatrix, B: MPMatrix, p: int | None = None, stream=None, **kw) -> MPMatrix:

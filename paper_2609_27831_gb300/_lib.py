@@ -89,6 +89,12 @@ _SIGS = {
     "ozaki2_gemm_noalloc": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.POINTER(Mat),
                                        C.POINTER(Mat), C.POINTER(Mat), C.c_void_p]),
     "ozaki2_noalloc_check": (C.c_int, [C.c_void_p]),
+    "ozaki2_plan_create_complex": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int, C.POINTER(Opts),
+                                              C.POINTER(C.c_void_p)]),
+    "ozaki2_execute_complex": (C.c_int, [C.c_void_p] + [C.POINTER(Mat)] * 6 + [C.c_void_p, C.c_size_t,
+                                                                               C.c_void_p]),
+    "ozaki2_zgemm": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int] + [C.POINTER(Mat)] * 6 +
+                     [C.POINTER(Opts), C.c_void_p]),
     "ozaki2_release_cache": (C.c_int, []),
     "ozaki2_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ozaki2_last_timings": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libozaki2_gb300.so")
-SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "gemm_tc2.cu", "gemm_s8.cu", "crt.cu", "fp64.cu", "probe.cu"]
+SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "gemm_tc2.cu", "gemm_s8.cu", "complex.cu", "crt.cu", "fp64.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

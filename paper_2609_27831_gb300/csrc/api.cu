@@ -188,6 +188,8 @@ struct ProbHost {
   int res_cw, res_nchunk, res_nabuf;           // res_mode 2: chunk width, chunks, byte buffers
   int nb;                                      // bytes of a (t+1)-bit integer
   std::vector<GroupHost> groups;               // non-empty: planes streamed in these groups
+  bool sum_of = false;                         // complex plan: planes are the sums of problems 0 and 1's
+  bool no_crt = false;                         // complex plan: no CRT (its v_l feed the combination)
 };
 
 // Tensor-core residue table [npad][kpad] (bf16 bits): row l (one-limb) =
@@ -279,7 +281,13 @@ struct ozaki2_plan_s {
   size_t ws_bytes = 0, ef_bytes = 0;
   int64_t total_units = 0, total_jobs = 0;
   oz2::DevState dev;
-  oz2::LaunchBlock lb;
+  // launch images (problem descriptors + tensor maps) in a small ring: an
+  // execute whose image one of them already holds (for example two buffer sets
+  // used in turn) reuses it without a copy or a host wait
+  static constexpr int kLaunchRing = 4;
+  oz2::LaunchBlock lbs[kLaunchRing];
+  uint64_t lb_used[kLaunchRing] = {0, 0, 0, 0};
+  uint64_t lb_clock = 0;
   std::vector<uint32_t*> dbg_chat;
   std::vector<int32_t*> dbg_prods;
   // stage boundaries: scan, residues, GEMM, CRT, end; [5] between the
@@ -290,6 +298,7 @@ struct ozaki2_plan_s {
   bool no_stream = false;         // internal plans whose planes must all stay resident
   uint32_t spin_limit = oz2::kDefaultSpinLimit;   // polls of a bounded device-side wait
   bool tile2 = false;             // plane GEMMs on CTA pairs (256 x 256 tiles)
+  bool complex3m = false;         // complex product: problems Ar Br, Ai Bi, (Ar + Ai)(Br + Bi)
   // operand reuse: the last product of a single-problem plan and its workspace,
   // whose row exponents and planes of A (or column exponents and planes of B)
   // a later ozaki2_execute_reuse keeps
@@ -308,6 +317,9 @@ namespace oz2 {
 cudaError_t init_prep_attributes();
 cudaError_t init_gemm_attributes();
 cudaError_t init_gemm2_attributes();
+cudaError_t init_gemm_s8_attributes();
+cudaError_t launch_plane_sum(const DevTables& t, int64_t items_a, int64_t items_b, cudaStream_t s);
+cudaError_t launch_combine_complex(const DevTables& t, int64_t items, cudaStream_t s);
 cudaError_t init_crt_attributes();
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -933,7 +945,8 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   std::map<std::array<int, 3>, std::vector<int4>> cmt_by, rmt_by;
   for (int pi = 0; pi < count; ++pi) {
     const ProbHost& h = pl->probs[pi];
-    if (!h.skip_a) {
+    const bool own_planes = !h.sum_of;             // planes made by the scan and residue kernels
+    if (!h.skip_a && own_planes) {
       // rows of A: 8 rows per block, K split into parts of >= 256 (maxima combined by atomicMax)
       const int rparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 256));
       for (int64_t r = 0; r < h.M; r += 8)
@@ -941,17 +954,17 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     }
     // columns of B: 32 columns per block, K split into parts of >= 64
     const int kparts = (int)std::max<int64_t>(1, std::min<int64_t>(64, h.K / 64));
-    if (!h.skip_b)
+    if (!h.skip_b && own_planes)
       for (int64_t c = 0; c < h.N; c += 32)
         for (int kp = 0; kp < kparts; ++kp) scan_cols.push_back(make_int4(pi, 1 | (kp << 8), (int)c, kparts));
-    for (int side = 0; h.res_mode == 2 && side < 2; ++side) {
+    for (int side = 0; h.res_mode == 2 && side < 2 && own_planes; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       std::vector<int4>& rl = rmt_by[{h.res_kpad, h.res_cw, h.res_nabuf}];
       for (int64_t r = 0; r < R; r += 4)
         for (int64_t k = 0; k < h.K; k += 32) rl.push_back(make_int4(pi, side, (int)r, (int)k));
     }
-    for (int side = 0; h.res_mode == 1 && side < 2; ++side) {
+    for (int side = 0; h.res_mode == 1 && side < 2 && own_planes; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       for (int64_t r = 0; r < R; r += 4)
@@ -960,15 +973,17 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.rtt_npad = std::max(ti.rtt_npad, h.res_npad);
       ti.rtt_l = std::max(ti.rtt_l, h.L);
     }
-    for (int side = 0; h.res_mode == 0 && side < 2; ++side) {
+    for (int side = 0; h.res_mode == 0 && side < 2 && own_planes; ++side) {
       if (side == 0 ? h.skip_a : h.skip_b) continue;
       const int64_t R = side ? h.N : h.M;
       for (int64_t r = 0; r < R; r += 8)
         for (int64_t k = 0; k < h.K; k += 32 * residue_class_ept(h.res_cls))
           res[h.res_cls].push_back(make_int4(pi, side, (int)r, (int)k));
     }
-    if (h.res_mode == 0) ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
-    if (h.crt_mode == 1) {
+    if (h.res_mode == 0 && own_planes) ti.res_l[h.res_cls] = std::max(ti.res_l[h.res_cls], h.L);
+    if (h.no_crt) {
+      // no CRT for this problem
+    } else if (h.crt_mode == 1) {
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
       for (int64_t tt = 0; tt < nt; ++tt) tct[h.crt_cls].push_back(make_int4(pi, (int)tt, 0, 0));
@@ -1042,6 +1057,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   }
   // consistency of the launch sizes with the problems they serve
   for (const ProbHost& h : pl->probs) {
+    if (h.sum_of || h.no_crt) continue;
     if (h.res_mode == 0 && !(h.skip_a && h.skip_b) && ti.res_l[h.res_cls] < h.L) return OZ2_EINTERNAL;
     if (h.res_mode == 1 && (ti.rtt_l < h.L || ti.rtt_kpad < h.res_kpad || ti.rtt_npad < h.res_npad))
       return OZ2_EINTERNAL;
@@ -1174,6 +1190,7 @@ static int upload(ozaki2_plan_s* pl) {
   if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return OZ2_ENODEV;
   if (major != 10) return OZ2_ENODEV;
   if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess || init_gemm2_attributes() != cudaSuccess ||
+      init_gemm_s8_attributes() != cudaSuccess ||
       init_crt_attributes() != cudaSuccess)
     return OZ2_ECUDA;
   if (!get_encode()) return OZ2_ECUDA;
@@ -1447,6 +1464,12 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
       OZ2_CU(launch_residues_tc(tab, part_ptr(d.rtt), part_n(d.rtt), d.rtt.smem, d.rtt_npad, d.rtt.lmax, d.sms, s));
     for (const ListRef& r : d.rmt)
       if (part_n(r)) OZ2_CU(launch_residues_mm(tab, part_ptr(r), part_n(r), r.smem, r.lmax, d.sms, s));
+    if (pl->complex3m) {
+      // the residue planes of Ar + Ai and Br + Bi, from those of the real and imaginary parts
+      const ProbHost& h = pl->probs[0];
+      const int64_t kc = h.Kp / 8;
+      OZ2_CU(launch_plane_sum(tab, (int64_t)h.L * h.M * kc, (int64_t)h.L * h.N * kc, s));
+    }
     if (timing) OZ2_CU(cudaEventRecord(pl->ev[2], s));
     if (pl->opts.engine == OZ2_ENGINE_SIMT) {
       DevTables t2 = tab;
@@ -1465,6 +1488,11 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
         OZ2_CU(pl->tile2 ? launch_gemm_tc2(t2, sg.grid, s) : launch_gemm_tc(t2, sg.grid, s));
       }
     }
+  }
+  if (pl->complex3m) {
+    // v_r = v(Ar Br) - v(Ai Bi), v_i = v((Ar + Ai)(Br + Bi)) - v(Ar Br) - v(Ai Bi) mod m_l
+    const ProbHost& h = pl->probs[0];
+    OZ2_CU(launch_combine_complex(tab, (int64_t)h.L * (int64_t)(align_up((size_t)(h.M * h.N), 8) / 8), s));
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
   for (const ListRef& r : d.cmt) OZ2_CU(launch_crt_mm(tab, r.ptr, r.n, r.smem, d.sms, s));
@@ -1490,14 +1518,28 @@ static int execute_impl(ozaki2_plan_s* pl, int count, const ozaki2_problem* prob
   if (keep >= 0 && (count != 1 || !pl->probs[0].groups.empty() || pl->last_ws != ws)) return OZ2_EINVAL;
   int rc = upload(pl);
   if (rc) return rc;
-  if (!pl->lb.d_mem && (rc = alloc_launch_block(pl->lb, launch_slots(pl)))) return rc;
+  const int slots = launch_slots(pl);
+  const size_t tmap_off = align_up(sizeof(ProbDev) * slots, 128);
+  const size_t lb_bytes = tmap_off + sizeof(CUtensorMap) * 5 * slots;
   std::vector<uint8_t> img;
-  rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, pl->lb.tmap_off, pl->lb.bytes);
+  rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, tmap_off, lb_bytes);
   if (rc) return rc;
-  rc = stage_image(pl->lb, img, s);
-  if (rc) return rc;
+  // the ring entry holding this image, else the least recently used one
+  int pick = -1;
+  for (int i = 0; i < ozaki2_plan_s::kLaunchRing && pick < 0; ++i)
+    if (pl->lbs[i].d_mem && pl->lbs[i].last == img) pick = i;
+  if (pick < 0) {
+    pick = 0;
+    for (int i = 1; i < ozaki2_plan_s::kLaunchRing; ++i)
+      if (pl->lb_used[i] < pl->lb_used[pick]) pick = i;
+    if (!pl->lbs[pick].d_mem && (rc = alloc_launch_block(pl->lbs[pick], slots))) return rc;
+    rc = stage_image(pl->lbs[pick], img, s);
+    if (rc) return rc;
+  }
+  pl->lb_used[pick] = ++pl->lb_clock;
+  LaunchBlock& lb = pl->lbs[pick];
   pl->timed = pl->opts.timing != 0;
-  rc = enqueue(pl, pl->lb, static_cast<uint8_t*>(ws), s, pl->timed, keep);
+  rc = enqueue(pl, lb, static_cast<uint8_t*>(ws), s, pl->timed, keep);
   if (count == 1) {
     pl->last_ws = rc ? nullptr : ws;
     pl->last_q = probs[0];
@@ -1638,9 +1680,52 @@ int ozaki2_plan_create_batched_ex(int count, const ozaki2_problem* shapes, const
   return OZ2_OK;
 }
 
+int ozaki2_plan_create_complex(int64_t M, int64_t N, int64_t K, int p, const ozaki2_opts* opts, ozaki2_plan* out) {
+  if (!out) return OZ2_EINVAL;
+  *out = nullptr;
+  ozaki2_plan_s* pl = nullptr;
+  int rc = new_plan(opts, &pl);
+  if (rc) return rc;
+  if (pl->opts.gemm_tile == 0 && pl->opts.engine == OZ2_ENGINE_TC) pl->tile2 = auto_pair_tiles(pl, M, N, K, p);
+  pl->complex3m = true;
+  PlanExtra ex;
+  ex.inner = 2 * K;                              // |Cr_hat|, |Ci_hat| <= 2K 2^(2t)
+  try {
+    for (int i = 0; i < 3 && !rc; ++i) rc = build_problem(pl, M, N, K, p, &ex);
+  } catch (const std::bad_alloc&) {
+    rc = OZ2_ENOMEM;
+  }
+  if (rc) { delete pl; return rc; }
+  pl->probs[2].sum_of = true;
+  pl->probs[2].no_crt = true;
+  layout_workspace(pl);
+  // one row exponent over Ar and Ai, one column exponent over Br and Bi
+  for (int i = 1; i < 3; ++i) {
+    pl->probs[i].off_e = pl->probs[0].off_e;
+    pl->probs[i].off_f = pl->probs[0].off_f;
+  }
+  *out = pl;
+  return OZ2_OK;
+}
+
+int ozaki2_execute_complex(ozaki2_plan pl, const ozaki2_mat* Ar, const ozaki2_mat* Ai, const ozaki2_mat* Br,
+                           const ozaki2_mat* Bi, ozaki2_mat* Cr, ozaki2_mat* Ci, void* ws, size_t ws_bytes,
+                           void* stream) {
+  if (!pl || !pl->complex3m || !Ar || !Ai || !Br || !Bi || !Cr || !Ci) return OZ2_EINVAL;
+  const ProbHost& h = pl->probs[0];
+  const ozaki2_problem q[3] = {{h.M, h.N, h.K, h.p, *Ar, *Br, *Cr},
+                               {h.M, h.N, h.K, h.p, *Ai, *Bi, *Ci},
+                               {h.M, h.N, h.K, h.p, *Ar, *Br, *Cr}};   // planes from the sums; no output
+  try {
+    return execute_impl(pl, 3, q, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
 int ozaki2_plan_destroy(ozaki2_plan pl) {
   if (!pl) return OZ2_EINVAL;
-  free_launch_block(pl->lb);
+  for (auto& lb : pl->lbs) free_launch_block(lb);
   if (pl->dev.mem) cudaFree(pl->dev.mem);
   for (auto& e : pl->ev)
     if (e) cudaEventDestroy(e);
@@ -1716,6 +1801,7 @@ int ozaki2_plan_launches(ozaki2_plan pl, int* n) {
   for (int i = 0; i < 6; ++i) res += d.res[i].n ? 1 : 0;
   res += d.rtt.n ? 1 : 0;
   res += (int)d.rmt.size();
+  if (pl->complex3m) c += 2;                      // plane sums, combination
   if (!d.groups.empty()) c += (int)d.groups.size() * (res + 1);   // per group: residues + one GEMM
   else if (pl->opts.engine == OZ2_ENGINE_SIMT || pl->opts.engine == OZ2_ENGINE_S8) c += res + 1;
   else if (pl->opts.schedule == OZ2_SCHED_GROUPED) c += res + 1;
@@ -1797,6 +1883,7 @@ int ozaki2_execute(ozaki2_plan pl, const ozaki2_mat* A, const ozaki2_mat* B, oza
 
 int ozaki2_execute_batched(ozaki2_plan pl, int count, const ozaki2_problem* probs, void* ws,
                            size_t ws_bytes, void* stream) {
+  if (pl && pl->complex3m) return OZ2_EINVAL;   // ozaki2_execute_complex
   try {
     return execute_impl(pl, count, probs, ws, ws_bytes, static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc&) {
@@ -1972,6 +2059,36 @@ int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   }
 }
 
+int ozaki2_zgemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* Ar, const ozaki2_mat* Ai,
+                 const ozaki2_mat* Br, const ozaki2_mat* Bi, ozaki2_mat* Cr, ozaki2_mat* Ci, const ozaki2_opts* opts,
+                 void* stream) {
+  if (!Ar || !Ai || !Br || !Bi || !Cr || !Ci) return OZ2_EINVAL;
+  ozaki2_opts o;
+  if (opts) o = *opts;
+  else ozaki2_opts_default(&o);
+  try {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    const ozaki2_problem q{M, N, K, p, *Ar, *Br, *Cr};
+    auto key = cache_key(1, &q, o);
+    key.push_back(-3);                             // complex plans are cached apart
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) {
+      Cached c;
+      int rc = ozaki2_plan_create_complex(M, N, K, p, &o, &c.plan);
+      if (rc) return rc;
+      if (injected_alloc_failure() || cudaMalloc(&c.ws, c.plan->ws_bytes) != cudaSuccess) {
+        ozaki2_plan_destroy(c.plan);
+        return OZ2_ENOMEM;
+      }
+      it = g_cache.emplace(key, c).first;
+    }
+    return ozaki2_execute_complex(it->second.plan, Ar, Ai, Br, Bi, Cr, Ci, it->second.ws, it->second.plan->ws_bytes,
+                                  stream);
+  } catch (const std::bad_alloc&) {
+    return OZ2_ENOMEM;
+  }
+}
+
 int ozaki2_gemm_batched(int count, const ozaki2_problem* probs, const ozaki2_opts* opts, void* stream) {
   if (!probs || count <= 0) return OZ2_EINVAL;
   try {
@@ -2091,6 +2208,7 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   layout_workspace(pl);
   if (pl->ws_bytes > sizeof(ozaki2_noalloc_scratch)) return OZ2_ERANGE;
   if (init_prep_attributes() != cudaSuccess || init_gemm_attributes() != cudaSuccess || init_gemm2_attributes() != cudaSuccess ||
+      init_gemm_s8_attributes() != cudaSuccess ||
       init_crt_attributes() != cudaSuccess || !get_encode())
     return OZ2_ECUDA;
   int sms = 0;

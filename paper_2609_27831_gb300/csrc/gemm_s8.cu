@@ -5,14 +5,15 @@
 // mma.sync.m16n8k32.s8.s8.s32; its INT32 accumulators are exact for
 // K * 127^2 < 2^31 (every K this library accepts), so no K chunking is needed.
 //
-// Block = one 128 x 128 half of a (modulus, 128 x 256 output tile) unit.  The
-// residue planes are bf16 in HBM (as the tcgen05 engines read them); each
-// block converts its K-slices to int8 while staging them in shared memory
-// (double-buffered through registers), and 8 warps (2 x 4) each own a 64 x 32
-// piece of the tile: 4 x 4 MMAs per K step of 32.  A unit's planes run one
-// after the other; each plane's exact sum is reduced mod m and added, times its
-// Karatsuba coefficient (one-limb: 1; two-limb: -127 P0 + 128 Ps + 16256 P2,
-// Eq. 4), to a running residue; the result times M_l^{-1} mod m_l is the CRT's
+// Block = one 128 x 128 half of a (modulus, 128 x 256 output tile) unit, two
+// blocks per SM.  The residue planes are bf16 in HBM (as the tcgen05 engines
+// read them); each block converts its K-slices to int8 while staging them in
+// shared memory (double-buffered through registers), and 8 warps (2 x 4) each
+// own a 64 x 32 piece of the tile: 4 x 4 MMAs per K step of 32.  A unit's
+// planes run one after the other; each plane's exact sum is reduced mod m and
+// added, times its Karatsuba coefficient (one-limb: 1; two-limb:
+// -127 P0 + 128 Ps + 16256 P2, Eq. 4), to a running residue kept in shared
+// memory (16 bits per output); the result times M_l^{-1} mod m_l is the CRT's
 // v_l (Sec. 4.4), stored as the tcgen05 engines store it.
 // Entry: {unit index (units in (problem, modulus, tile) order), half, 0, 0}.
 #include "oz2_internal.h"
@@ -94,10 +95,12 @@ __device__ __forceinline__ void store_slice(uint8_t* s, const uint4 (&v)[2]) {
   }
 }
 
-__global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant__ DevTables T,
+__global__ void __launch_bounds__(kS8Threads, 2) k_gemm_s8(const __grid_constant__ DevTables T,
                                                           const int4* __restrict__ list) {
-  __shared__ __align__(16) uint8_t sA[2][kS8Rows * kS8Stride];
-  __shared__ __align__(16) uint8_t sB[2][kS8Rows * kS8Stride];
+  extern __shared__ __align__(16) uint8_t s8_smem[];
+  uint8_t (*sA)[kS8Rows * kS8Stride] = reinterpret_cast<uint8_t (*)[kS8Rows * kS8Stride]>(s8_smem);
+  uint8_t (*sB)[kS8Rows * kS8Stride] = sA + 2;
+  uint16_t* sRes = reinterpret_cast<uint16_t*>(s8_smem + 4 * kS8Rows * kS8Stride);   // thread t's 64 at t + 256 i
   const int4 e = list[blockIdx.x];
   const Unit u = T.units[e.x];
   const ProbDev& P = T.probs[u.prob];
@@ -112,22 +115,14 @@ __global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant
   const int gid = lane >> 2, tig = lane & 3;
   const int64_t psA = (int64_t)P.M * P.Kp, psB = (int64_t)P.N * P.Kp;
 
-  uint32_t res[4][4][4];                           // running residue per output (mod m)
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) res[a][b][c] = 0u;
-
   const int nplanes = two ? 3 : 1;
+  int acc[4][4][4];                                // a plane's exact sums; after the last plane, u_l
   for (int pi = 0; pi < nplanes; ++pi) {
     // planes r0 r0', r1 r1', (r0 + r1)(r0' + r1') with coefficients -127, 16256, 128 (Eq. 4)
     const int g = g0 + pi;
     const uint32_t coef = !two ? 1u : (pi == 0 ? (m - 127u % m) % m : (pi == 1 ? 16256u % m : 128u % m));
     const uint16_t* pa = P.pa + (int64_t)g * psA;
     const uint16_t* pb = P.pb + (int64_t)g * psB;
-    int acc[4][4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -175,6 +170,7 @@ __global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant
       buf ^= 1;
     }
     // the plane's exact sums, reduced and weighted into the running residue
+    // (each thread reads and writes only its own 64 entries of sRes)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -183,7 +179,10 @@ __global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant
         for (int c = 0; c < 4; ++c) {
           uint32_t r = mod_s32(acc[a][b][c], m, mu, off);
           if (coef != 1u) r = mod_u32(r * coef, m, mu);
-          res[a][b][c] = mod_u32(res[a][b][c] + r, m, mu);
+          uint16_t& slot = sRes[threadIdx.x + kS8Threads * (16 * a + 4 * b + c)];
+          if (pi > 0) r = mod_u32(r + slot, m, mu);
+          if (pi + 1 < nplanes) slot = (uint16_t)r;
+          else acc[a][b][c] = (int)r;                // the unit's u_l, kept for the store
         }
   }
   // v_l = u_l M_l^{-1} mod m_l, stored as the tcgen05 engines store it
@@ -198,8 +197,8 @@ __global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant
         const int row = row0 + wm * 64 + mt * 16 + gid + 8 * h;
         const int col = col0 + wn * 32 + nt * 8 + 2 * tig;
         if (row >= P.M) continue;
-        const uint32_t v0 = mod_u32(res[mt][nt][2 * h] * minv, m, mu);
-        const uint32_t v1 = mod_u32(res[mt][nt][2 * h + 1] * minv, m, mu);
+        const uint32_t v0 = mod_u32((uint32_t)acc[mt][nt][2 * h] * minv, m, mu);
+        const uint32_t v1 = mod_u32((uint32_t)acc[mt][nt][2 * h + 1] * minv, m, mu);
         if (col < P.N) ub[(int64_t)row * P.N + col] = (uint16_t)v0;
         if (col + 1 < P.N) ub[(int64_t)row * P.N + col + 1] = (uint16_t)v1;
       }
@@ -207,9 +206,15 @@ __global__ void __launch_bounds__(kS8Threads, 1) k_gemm_s8(const __grid_constant
 
 }  // namespace
 
+constexpr int kS8Smem = 4 * kS8Rows * kS8Stride + kS8Threads * 64 * 2;   // two double-buffered slices, residues
+
+cudaError_t init_gemm_s8_attributes() {
+  return cudaFuncSetAttribute(k_gemm_s8, cudaFuncAttributeMaxDynamicSharedMemorySize, kS8Smem);
+}
+
 cudaError_t launch_gemm_s8(const DevTables& t, const int32_t* list, int n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_gemm_s8<<<n, kS8Threads, 0, s>>>(t, reinterpret_cast<const int4*>(list));
+  k_gemm_s8<<<n, kS8Threads, kS8Smem, s>>>(t, reinterpret_cast<const int4*>(list));
   return cudaGetLastError();
 }
 

@@ -262,3 +262,16 @@ def test_operand_reuse_needs_a_previous_execute(ozk):
             ozk._lib.OZ2_EINVAL
     assert lib.ozaki2_execute_reuse(plan._h, 2, C.byref(m), C.byref(c), 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
     assert lib.ozaki2_execute_reuse(None, 0, C.byref(m), C.byref(c), 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
+
+
+def test_complex_plan_host_facts(ozk):
+    """A complex plan: three real products sharing exponents, t and the
+    modulus set chosen for inner length 2K; batched executes refuse it."""
+    M, N, K, p = 100, 80, 60, 256
+    plan = ozk.ComplexPlan((M, N, K, p))
+    par = o.complex_params(K, p)
+    assert plan.info["count"] == 3 and plan.info["t"] == par.t and plan.info["L"] == par.L
+    assert plan.moduli() == par.moduli
+    lib = ozk.lib()
+    arr = (ozk._lib.Problem * 3)()
+    assert lib.ozaki2_execute_batched(plan._h, 3, arr, 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
