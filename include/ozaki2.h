@@ -307,13 +307,12 @@ OZ2_API int ozaki2_gemm(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat
    more (ozaki2_info.workspace_bytes of the same shape above 64 MiB, e.g.
    1024^3 at p = 256) are rejected with OZ2_ERANGE before any device work.
    The first call on a device looks up the arrays' device addresses (once per
-   device, with that device current); make that first call before any stream
-   capture.  Each call writes its tables into the array with small kernels on
-   `stream` (their parameters carry the bytes), so it does not wait on the
-   host for earlier work on the stream.  Every call shares the arrays and
-   rewrites them: calls that overlap on the GPU (different streams, or
-   concurrent host threads) race, so order them on one stream.  Default
-   options.  The device status word of the most recent call on the current
+   device, with that device current).  Each call writes its tables into the
+   array with small kernels on `stream` (their parameters carry the bytes), so
+   it does not wait on the host for earlier work on the stream.  Every call
+   shares the arrays and rewrites them: calls that overlap on the GPU
+   (different streams, or concurrent host threads) race, so order them on one
+   stream.  Default options.  The device status word of the most recent call on the current
    device (cleared at the start of each call) is read by ozaki2_noalloc_check. */
 OZ2_API int ozaki2_gemm_noalloc(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A,
                                 const ozaki2_mat* B, ozaki2_mat* C, void* stream);

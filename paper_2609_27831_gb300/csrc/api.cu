@@ -858,23 +858,33 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
   const int want = pl->opts.grid > 0 ? pl->opts.grid : d.sms;
   const int slots = pl->tile2 ? std::max(1, want / 2) : want;
   const int grid = std::max(1, std::min(slots, nunits));
-  // greedy list scheduling: every unit, in (problem, modulus, tile) order, goes
-  // to the least-loaded CTA; the cost of a unit is its accumulation jobs times
-  // (K blocks per job + a fixed epilogue share)
+  // greedy list scheduling, longest first: every unit goes to the least-loaded
+  // CTA, the units in decreasing cost (the two-limb moduli's three-plane units
+  // first), each cost class in (problem, modulus, tile) order; the cost of a
+  // unit is its accumulation jobs times (K blocks per job + a fixed epilogue
+  // share).  Taking the large units first keeps the largest CTA load within
+  // one small unit of the mean (1024^3 at p = 256: 440 against a mean of 429.5
+  // and 460 in plain unit order).
   std::vector<std::vector<int>> lists(grid);
   {
-    using Load = std::pair<int64_t, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < grid; ++c) heap.push(Load(0, c));
+    std::vector<int64_t> cost(nunits);
     for (int u = 0; u < nunits; ++u) {
       const ProbHost& h = pl->probs[units[u].prob];
       const int planes = units[u].ell < h.L1 ? 1 : 3;
       const int64_t kblocks = (std::min<int64_t>(h.K, h.kchunk) + kBK - 1) / kBK;
-      const int64_t cost = (int64_t)planes * h.nchunks * (kblocks + 4);
+      cost[u] = (int64_t)planes * h.nchunks * (kblocks + 4);
+    }
+    std::vector<int> order(nunits);
+    for (int u = 0; u < nunits; ++u) order[u] = u;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<int64_t, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < grid; ++c) heap.push(Load(0, c));
+    for (int u : order) {
       Load top = heap.top();
       heap.pop();
       lists[top.second].push_back(u);
-      top.first += cost;
+      top.first += cost[u];
       heap.push(top);
     }
   }
@@ -919,7 +929,11 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
       for (int c = 0; c < gg; ++c) heap.push(Load(0, c));
       const int64_t kblocks = (std::min<int64_t>(h.K, h.kchunk) + kBK - 1) / kBK;
-      for (int u = 0; u < (int)gu.size(); ++u) {
+      std::vector<int> order;                      // longest first, as above
+      for (int pass = 0; pass < 2; ++pass)
+        for (int u = 0; u < (int)gu.size(); ++u)
+          if ((gu[u].ell < gr.L1) == (pass == 1)) order.push_back(u);
+      for (int u : order) {
         const int planes = gu[u].ell < gr.L1 ? 1 : 3;
         Load top = heap.top();
         heap.pop();
@@ -1228,7 +1242,7 @@ static int launch_slots(const ozaki2_plan_s* pl) {
 static int alloc_launch_block(LaunchBlock& lb, int slots) {
   const size_t probs_bytes = align_up(sizeof(ProbDev) * slots, 128);
   lb.tmap_off = probs_bytes;
-  lb.bytes = probs_bytes + sizeof(CUtensorMap) * 5 * slots;   // A planes, B planes, CRT table, u tiles, residue table
+  lb.bytes = probs_bytes + sizeof(CUtensorMap) * kMapsPerProblem * slots;
   int rc = OZ2_OK;
   if (injected_alloc_failure() || cudaMalloc(&lb.d_mem, lb.bytes) != cudaSuccess) {
     lb.d_mem = nullptr;
@@ -1258,6 +1272,25 @@ static int encode_planes(CUtensorMap* map, void* base, int64_t K, int64_t rows, 
                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? OZ2_OK : OZ2_ECUDA;
+}
+
+// v_l of the plane GEMM as a [L][M][N] uint16 tensor (row pitch N, modulus
+// pitch upitch), stored in 32 x 32 tiles staged with the 64-byte swizzle.
+// Needs rows of 16-byte multiples (N a multiple of 8); 0 when N is not.
+static int encode_u_store(CUtensorMap* map, uint16_t* u, int64_t N, int64_t M, int L, int64_t upitch,
+                          int32_t* ok) {
+  *ok = 0;
+  if (N % 8 != 0) return OZ2_OK;
+  const cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)M, (cuuint64_t)L};
+  const cuuint64_t strides[2] = {(cuuint64_t)N * 2, (cuuint64_t)upitch * 2};
+  const cuuint32_t box[3] = {32u, 32u, 1u};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  const CUresult r = get_encode()(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, u, dims, strides, box, es,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return OZ2_ECUDA;
+  *ok = 1;
+  return OZ2_OK;
 }
 
 // Fill the launch image (ProbDev + tensor maps) for the given problems.
@@ -1331,6 +1364,8 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     if (rc) return rc;
     rc = encode_planes(&tm[2 * i + 1], P.pb, h.K, h.N, h.Kp, h.G, pl->tile2 ? kBN / 2 : kBN);
     if (rc) return rc;
+    rc = encode_u_store(&tm[5 * count + i], P.u, h.N, h.M, h.L, P.upitch, &P.u_map);
+    if (rc) return rc;
     if (h.crt_mode != 0) {
       // mode 1: the whole table in K blocks; mode 2: K block x cw columns of
       // a table padded to whole chunks
@@ -1370,10 +1405,12 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
       int gfirst = 0;                                    // planes of the groups before this one
       for (size_t q = 0; q < g; ++q) gfirst += h.groups[q].G;
       if (Q.dbg_prods) Q.dbg_prods += (int64_t)gfirst * h.M * h.N;
-      CUtensorMap* gm = tm + 5 * count + 5 * g;
+      CUtensorMap* gm = tm + kMapsPerProblem * (count + g);
       int rc = encode_planes(&gm[0], Q.pa, h.K, h.M, h.Kp, gr.G, kBM);
       if (rc) return rc;
       rc = encode_planes(&gm[1], Q.pb, h.K, h.N, h.Kp, gr.G, pl->tile2 ? kBN / 2 : kBN);
+      if (rc) return rc;
+      rc = encode_u_store(&gm[5], Q.u, h.N, h.M, gr.L, Q.upitch, &Q.u_map);
       if (rc) return rc;
       if (h.res_mode != 0) {
         const int rows = pl->rtabs[gr.res_key].rows;
@@ -1448,7 +1485,7 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
       DevTables gt = d.groups[g].tab;
       gt.spin_limit = pl->spin_limit;
       gt.probs = pd + count + g;
-      gt.tmaps = tmp + 5 * count + 5 * g;
+      gt.tmaps = tmp + kMapsPerProblem * (count + g);
       if (timing) OZ2_CU(cudaEventRecord(pl->evg[2 * g], s));
       for (int c = 0; c < 6; ++c)
         if (d.res[c].n) OZ2_CU(launch_residues(gt, c, d.res[c].ptr, d.res[c].n, d.res[c].smem, s));
@@ -1520,7 +1557,7 @@ static int execute_impl(ozaki2_plan_s* pl, int count, const ozaki2_problem* prob
   if (rc) return rc;
   const int slots = launch_slots(pl);
   const size_t tmap_off = align_up(sizeof(ProbDev) * slots, 128);
-  const size_t lb_bytes = tmap_off + sizeof(CUtensorMap) * 5 * slots;
+  const size_t lb_bytes = tmap_off + sizeof(CUtensorMap) * kMapsPerProblem * slots;
   std::vector<uint8_t> img;
   rc = build_image(pl, probs, static_cast<uint8_t*>(ws), img, tmap_off, lb_bytes);
   if (rc) return rc;
@@ -2218,7 +2255,7 @@ int noalloc_run(int64_t M, int64_t N, int64_t K, int p, const ozaki2_mat* A, con
   if (rc) return rc;
   const size_t lb_off = align_up(ti.b.img.size(), 256);
   const size_t probs_bytes = align_up(sizeof(ProbDev), 128);
-  const size_t lb_bytes = probs_bytes + 5 * sizeof(CUtensorMap);
+  const size_t lb_bytes = probs_bytes + kMapsPerProblem * sizeof(CUtensorMap);
   if (lb_off + lb_bytes > kNoAllocStatusOff) return OZ2_ERANGE;
   install_table_image(pl, ti, nd->tables);
   pl->dev.tab.status = reinterpret_cast<int32_t*>(nd->tables + kNoAllocStatusOff);

@@ -362,62 +362,83 @@ __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t
   P.c_sign[coff] = neg ? 1 : 0;
 }
 
+// Multi-digit arithmetic on ND little-endian 32-bit digits, one PTX carry
+// chain each (add.cc / addc.cc / addc: one integer add per digit).  The
+// compiler emits no carry-flag instructions of its own, so the chain's
+// statements may be separated by its loads and moves.
+template <int ND>
+__device__ __forceinline__ uint32_t add_digits(const uint32_t (&a)[ND], const uint32_t (&b)[ND], uint32_t (&s)[ND]) {
+  uint32_t c;
+  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(s[0]) : "r"(a[0]), "r"(b[0]));
+#pragma unroll
+  for (int d = 1; d < ND; ++d) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(s[d]) : "r"(a[d]), "r"(b[d]));
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(c));
+  return c;
+}
+// carry out of a + b only
+template <int ND>
+__device__ __forceinline__ uint32_t carry_digits(const uint32_t (&a)[ND], const uint32_t (&b)[ND]) {
+  uint32_t c, t;
+  asm volatile("add.cc.u32 %0, %1, %2;" : "=r"(t) : "r"(a[0]), "r"(b[0]));
+#pragma unroll
+  for (int d = 1; d < ND; ++d) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(t) : "r"(a[d]), "r"(b[d]));
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(c));
+  return c;
+}
+// s = a - b mod 2^(32 ND)
+template <int ND>
+__device__ __forceinline__ void sub_digits(const uint32_t (&a)[ND], const uint32_t (&b)[ND], uint32_t (&s)[ND]) {
+  asm volatile("sub.cc.u32 %0, %1, %2;" : "=r"(s[0]) : "r"(a[0]), "r"(b[0]));
+#pragma unroll
+  for (int d = 1; d < ND - 1; ++d) asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(s[d]) : "r"(a[d]), "r"(b[d]));
+  asm volatile("subc.u32 %0, %1, %2;" : "=r"(s[ND - 1]) : "r"(a[ND - 1]), "r"(b[ND - 1]));
+}
+
 // The CRT and rounding of one output from R = (S + alpha~ (2^(32 D) - P)) mod
 // 2^(32 D), i.e. R in [0, 2P) (Sec. 4.4): subtract P once if R >= P, take the
 // signed representative, round |c_hat| 2^(e_i + f_j - 2t) to p bits and write
-// the output.  tab: [3][ND] digits of 2^(32 D) - P, 2^(32 D) - (floor(P/2) + 1)
-// and P.  s_mag: scratch column e of a [ND][ldm] digit array.
+// the output.  R holds zeros in digits D .. ND - 1.  tab: [3][ND] digits of
+// 2^(32 ND) - P and 2^(32 ND) - (floor(P/2) + 1) (all ones from digit D on,
+// so that every comparison is one carry chain over ND digits) and of P (zero
+// from digit D on).  s_mag: scratch column e of a [ND][ldm] digit array.
+//   T1 = R + 2^(32 ND) - P carries out iff R >= P (then x0 = T1 = R - P,
+//        else x0 = R);
+//   x0 + 2^(32 ND) - floor(P/2) - 1 carries out iff x0 > floor(P/2): c_hat
+//        = x0 - P is negative, |c_hat| = P - x0;
+//   x0 + 2^(32 ND) - P must not carry out (x0 < P), else the tables or the
+//        sums are inconsistent and the status word records it.
 template <int ND>
 __device__ __forceinline__ void crt_finish(const ProbDev& P, uint32_t (&R)[ND], const uint32_t* s_tab,
                                            uint32_t* s_mag, int ldm, int e, int64_t idx, int ef, int32_t* status) {
   const int D = P.D32;
-  const uint32_t* negP = s_tab;
-  const uint32_t* negH1 = s_tab + ND;
-  const uint32_t* Pd = s_tab + 2 * ND;
-  // pass 1, least significant digit first, three independent carry chains:
-  // R + (2^(32 D) - P) carries out iff R >= P (then x0 = R - P, else x0 = R);
-  // x + (2^(32 D) - floor(P/2) - 1) carries out iff x > floor(P/2), for x = R
-  // and for x = R - P: the sign of c_hat for either choice of x0
-  uint32_t c1 = 0, c3 = 0, c4 = 0;
+  uint32_t tab[ND], x0[ND];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) tab[d] = s_tab[d];                   // 2^(32 ND) - P
+  const bool ge = add_digits<ND>(R, tab, x0) != 0u;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) x0[d] = ge ? x0[d] : R[d];
+  const bool bad = carry_digits<ND>(x0, tab) != 0u;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) tab[d] = s_tab[ND + d];              // 2^(32 ND) - floor(P/2) - 1
+  const bool neg = carry_digits<ND>(x0, tab) != 0u;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) tab[d] = s_tab[2 * ND + d];          // P
+  sub_digits<ND>(tab, x0, R);                                       // P - x0
+  if (bad) atomicOr(status, kStatusCrtRange);
+  int top = -1;
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    if (d < D) {
-      const uint64_t t1 = (uint64_t)R[d] + negP[d] + c1;
-      c1 = (uint32_t)(t1 >> 32);
-      c3 = (uint32_t)(((uint64_t)R[d] + negH1[d] + c3) >> 32);
-      c4 = (uint32_t)(((uint64_t)(uint32_t)t1 + negH1[d] + c4) >> 32);
-    }
+    const uint32_t m = neg ? R[d] : x0[d];
+    R[d] = m;
+    s_mag[d * ldm + e] = m;
+    if (m != 0u) top = d;
   }
-  const bool ge = c1 != 0;
-  const bool neg = ge ? c4 != 0 : c3 != 0;
-  // pass 2: x0, the check x0 < P (x0 + 2^(32 D) - P must not carry out), and
-  // |c_hat| = x0 or P - x0
-  uint32_t cs = 0, cc = 0, br = 0;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    if (d < D) {
-      const uint64_t t1 = (uint64_t)R[d] + negP[d] + cs;
-      cs = (uint32_t)(t1 >> 32);
-      const uint32_t x0 = ge ? (uint32_t)t1 : R[d];
-      cc = (uint32_t)(((uint64_t)x0 + negP[d] + cc) >> 32);
-      const uint64_t tn = (uint64_t)Pd[d] - x0 - br;
-      br = (uint32_t)(tn >> 63);
-      R[d] = neg ? (uint32_t)tn : x0;
-    }
-  }
-  if (cc) atomicOr(status, kStatusCrtRange);
   if (P.dbg_chat != nullptr) {
     uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
     dst[0] = neg;
 #pragma unroll
     for (int d = 0; d < ND; ++d)
       if (d < D) dst[1 + d] = R[d];
-  }
-  int top = -1;
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    s_mag[d * ldm + e] = R[d];
-    if (R[d]) top = d;
   }
   crt_round_write(P, s_mag, ldm, e, ND, top, neg, idx, ef);
 }
@@ -472,9 +493,9 @@ __global__ void __launch_bounds__(kEpb1) k_crt1(DevTables T, const int4* __restr
   uint32_t* s_mag = s_tab + 3 * ND;                           // [ND][kEpb1]
   for (int i = threadIdx.x; i < L * ND; i += kEpb1) s_M[i] = __ldg(cv.Mdig + i);
   for (int i = threadIdx.x; i < ND; i += kEpb1) {
-    s_tab[i] = __ldg(cv.negP + i);
-    s_tab[ND + i] = __ldg(cv.negH1 + i);
-    s_tab[2 * ND + i] = __ldg(cv.P + i);
+    s_tab[i] = i < D ? __ldg(cv.negP + i) : ~0u;           // widened to ND digits (crt_finish)
+    s_tab[ND + i] = i < D ? __ldg(cv.negH1 + i) : ~0u;
+    s_tab[2 * ND + i] = i < D ? __ldg(cv.P + i) : 0u;
   }
   // v_l = (c mod m_l) M_l^{-1} mod m_l as the plane GEMM stored it: 16-byte
   // loads of 8 values; a block covers 16 x 8 = 128 outputs of 8 moduli per
@@ -716,9 +737,9 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
         s_pc[l] = make_uint4(mc.m, mc.mu, 0u, 0u);
       }
       for (int d = t; d < ND; d += kCtThreads) {
-        s_tab[d] = d < P.DS ? __ldg(cv.negP + d) : 0u;
-        s_tab[ND + d] = d < P.DS ? __ldg(cv.negH1 + d) : 0u;
-        s_tab[2 * ND + d] = d < P.DS ? __ldg(cv.P + d) : 0u;
+        s_tab[d] = d < P.D32 ? __ldg(cv.negP + d) : ~0u;   // widened to ND digits (crt_finish)
+        s_tab[ND + d] = d < P.D32 ? __ldg(cv.negH1 + d) : ~0u;
+        s_tab[2 * ND + d] = d < P.D32 ? __ldg(cv.P + d) : 0u;
       }
       __syncthreads();
       if (t == 0) {
@@ -906,15 +927,15 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 // d mod 7 < 2, word d - 7 (g - 1) of the group before.
 template <int ND>
 __global__ void __launch_bounds__(kFinThreads, (ND <= 24 ? 6 : 1)) k_crt_fin_short(DevTables T, const int4* __restrict__ blk) {
-  __shared__ uint32_t s_tab[3 * ND];              // 2^(32 D) - P, 2^(32 D) - floor(P/2) - 1, P
+  __shared__ uint32_t s_tab[3 * ND];              // 2^(32 ND) - P, 2^(32 ND) - floor(P/2) - 1, P
   __shared__ uint32_t s_mag[ND * kFinThreads];    // rounding scratch
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
   const CrtView cv = crt_view(T.crt_pool, P);
   const int D = P.D32, ng = P.crt_ngrp;
   for (int i = threadIdx.x; i < ND; i += kFinThreads) {
-    s_tab[i] = i < D ? __ldg(cv.negP + i) : 0u;
-    s_tab[ND + i] = i < D ? __ldg(cv.negH1 + i) : 0u;
+    s_tab[i] = i < D ? __ldg(cv.negP + i) : ~0u;           // widened to ND digits (crt_finish)
+    s_tab[ND + i] = i < D ? __ldg(cv.negH1 + i) : ~0u;
     s_tab[2 * ND + i] = i < D ? __ldg(cv.P + i) : 0u;
   }
   const int e = threadIdx.x;

@@ -36,9 +36,11 @@ using namespace plane;
 constexpr int kTileABytes = kBM * kBK * 2;            // 16 KB
 constexpr int kTileBBytes = kBN * kBK * 2;            // 32 KB
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + kEpiWarps * 32;         // 320
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kEpiWarps = 8;                          // a multiple of 4 (one per TMEM lane quadrant)
+constexpr int kEpiCols = kBN / (kEpiWarps / 4);       // columns of a slot per epilogue warp
+constexpr int kThreads = 64 + kEpiWarps * 32;
+constexpr int kStageOff = kStages * kStageBytes + 1024;      // v_l staging, after the barriers
+constexpr int kSmemBytes = kStageOff + kEpiWarps * 4096 + 1024 /*align*/;
 // Instruction descriptor: D = f32, A = B = bf16, both K-major, M = 128, N = 256.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
@@ -171,81 +173,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;
     const int quad = warp & 3;          // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;           // column half of the 256-column slot
+    const int half = ew >> 2;           // column range of the 256-column slot
     JobIter it;
     it.init(&T, ubeg, uend);
     Job j;
     int uses[2] = {0, 0};
+    UStage us{nullptr, base + (uint32_t)(kStageOff + ew * 4096), 0u};
     while (it.next(j)) {
       const int s = j.slot;
-      // the job's constants in registers before the wait: they load while it
-      // waits, and the barrier's memory clobber does not reload them
-      const ProbDev& P = T.probs[j.u.prob];
-      const ModConst mc = T.mods[j.u.ell];
-      const float mf = (float)mc.m;
-      const int PM = P.M, PN = P.N;
       const int row = j.u.tm * kBM + quad * 32 + lane;
-      const uint32_t tbase =
-          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kBN + half * 128);
-      uint16_t* urow = P.u + (int64_t)j.u.ell * P.upitch + (int64_t)row * PN;
-      const int col_base = j.u.tn * kBN + half * 128;
-      const bool vec_ok = (PN & 7) == 0;
-      // final coefficient, times M_l^{-1} mod m_l on the last job, so that
-      // the stored value is the CRT's v_l = (c mod m_l) M_l^{-1} mod m_l (Sec. 4.4)
-      uint32_t fin = mc.kfin;
-      if (j.last) fin = barrett32(fin * __ldg(crt_view(T.crt_pool, P).Minv + j.u.ell), mc.m, mc.mu);
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kBN + half * kEpiCols);
+      const EpiConst e = epi_const(T, j, row, j.u.tn * kBN + half * kEpiCols);
+      us.map = T.probs[j.u.prob].u_map ? T.tmaps + 5 * T.count + j.u.prob : nullptr;
       if (!mbar_wait(slot_full + s, (uint32_t)(uses[s] & 1), abort_flag, T.status, T.spin_limit)) break;
       ++uses[s];
       tc_fence_after();
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
-        uint32_t v[32];
-        tmem_ld32(tbase + (uint32_t)(c * 32), v);
-        if (P.dbg_prods != nullptr)
-          dbg_plane_sums(P.dbg_prods, j.plane, j.first, PM, PN, row, col_base + c * 32, tbase + (uint32_t)(c * 32));
-        if (!j.last) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
-            if (j.kmul != 1u) r = barrett32(r * j.kmul, mc.m, mc.mu);
-            v[i] = __float_as_uint(small_u2f(r));
-          }
-          tmem_st32(tbase + (uint32_t)(c * 32), v);
-          if (P.dbg_prods != nullptr)
-            dbg_write_back(P.dbg_prods, j.plane, j.u.ell, P.L1, PM, PN, row, col_base + c * 32,
-                           tbase + (uint32_t)(c * 32));
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            uint32_t r = fmod_small(__uint_as_float(v[i]), mf, mc.rcp);
-            if (fin != 1u) r = barrett32(r * fin, mc.m, mc.mu);
-            v[i] = r;
-          }
-          const int col0 = col_base + c * 32;
-          if (row < PM) {
-            if (vec_ok && col0 + 32 <= PN) {
-              uint4* dst = reinterpret_cast<uint4*>(urow + col0);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                uint4 w;
-                w.x = v[8 * q + 0] | (v[8 * q + 1] << 16);
-                w.y = v[8 * q + 2] | (v[8 * q + 3] << 16);
-                w.z = v[8 * q + 4] | (v[8 * q + 5] << 16);
-                w.w = v[8 * q + 6] | (v[8 * q + 7] << 16);
-                dst[q] = w;
-              }
-            } else {
-#pragma unroll
-              for (int i = 0; i < 32; ++i)
-                if (col0 + i < PN) urow[col0 + i] = (uint16_t)v[i];
-            }
-          }
-        }
-      }
-      if (!j.last) tmem_wait_st();
+      epi_job<kEpiCols / 32>(j, e, tbase, us);
       tc_fence_before();
       mbar_arrive(slot_free + s);
     }
+    if (lane == 0) bulk_wait_all();                  // the v_l stores are complete before the CTA exits
   }
 
   tc_fence_before();

@@ -25,6 +25,11 @@ constexpr int kMaxKChunk = 1024;   // 127^2 * 1024 + 16191 < 2^24: fp32 accumula
 constexpr uint32_t kDefaultSpinLimit = 1u << 26;
 
 constexpr int kMaxP = 2048;
+// Tensor maps per problem descriptor, at i + n count for problem i of count:
+// A planes (2 i), B planes (2 i + 1), tensor-core CRT table (n = 2), u tiles
+// read by the CRT (n = 3), residue table (n = 4), v_l tiles stored by the
+// plane GEMM (n = 5).
+constexpr int kMapsPerProblem = 6;
 constexpr int kMaxK = 133000;      // Sec. 4.3(a) implementation cap
 
 // Per-modulus constants (index = position in the global modulus list).
@@ -93,7 +98,7 @@ struct ProbDev {
   int32_t res_nchunk;    // res_mode 2: chunks
   int32_t crt_nslot;     // crt_mode 2: TMEM accumulator slots (1 or 2)
   int32_t res_nabuf;     // res_mode 2: byte buffers (A) in TMEM (2 or 4)
-  int32_t pad9;
+  int32_t u_map;         // 1: tensor map 5 * count + i stores v_l tiles (N a multiple of 8)
   int32_t* dbg_prods;    // optional (K within one chunk): [G][M][N] exact plane sums before reduction
 };
 
@@ -138,7 +143,7 @@ struct DevTables {
   const ProbDev* probs;
   const Unit* units;
   const int32_t* cta_begin;  // [grid + 1] unit ranges per persistent CTA
-  const CUtensorMap* tmaps;  // [2 * count]: A planes, B planes
+  const CUtensorMap* tmaps;  // [kMapsPerProblem * count]: see kMapsPerProblem
   int32_t* status;           // device status word
   int32_t count;
   uint32_t spin_limit;       // iterations of a bounded mbarrier wait before it gives up

@@ -734,16 +734,32 @@ __device__ __forceinline__ float cmod_f32(float y, float mf, float rcp, float hm
   return r;
 }
 
-// A value congruent to y0 + 128 y1 (mod m) for the two byte sums of a
-// two-limb modulus (table halves |T0| <= 64, |T1| <= 63, at most 448 bytes):
-// y1 is reduced with a round-to-nearest quotient only (|r1| < 1.5 m), so that
-// |y0 + 128 r1| <= 448 255 64 + 192 16191 < 2^24 is an exact fp32 integer
-// (and cmod_f32's quotient stays exact: |y / m| < 2^22).
-__device__ __forceinline__ float pair_f32(uint32_t y0bits, uint32_t y1bits, float mf, float rcp) {
+// Centered residue of y0 + 128 y1 (mod m) for the two byte sums of a
+// two-limb modulus: m is an odd prime below 2^14, the table halves satisfy
+// |T0| <= 64 and |T1| <= 63, and an integer has at most 265 bytes (t <=
+// 2112), so |y0|, |y1| <= 265 255 64 < 2^23.
+// For an exact fp32 integer |y| < 2^23 and rcp = RN(1/m): |y rcp - y/m| <=
+// |y|/m 2^-24 < 1/(2m), while an odd m keeps y/m at least 1/(2m) away from
+// every half-integer, so q = RN(y rcp) (one fma with the 1.5 2^23 addend) is
+// the nearest integer to y/m and y - q m is the centered residue in
+// [-(m - 1)/2, (m - 1)/2], with no correction step.  That gives r1 for y1,
+// then x = y0 + 128 r1 (|x| < 4.4e6 + 1.1e6 < 2^23, exact) and r for x.
+// The + 0.0f turns a -0 (all bytes of a zero element carry the sign) into +0.
+__device__ __forceinline__ float cmod2_f32(uint32_t y0bits, uint32_t y1bits, float mf, float rcp) {
   const float y1 = __uint_as_float(y1bits);
-  const float q = fmaf(y1, rcp, 12582912.0f) - 12582912.0f;
-  const float r1 = fmaf(-q, mf, y1);
-  return fmaf(128.f, r1, __uint_as_float(y0bits));
+  const float q1 = fmaf(y1, rcp, 12582912.0f) - 12582912.0f;
+  const float x = fmaf(128.f, fmaf(-q1, mf, y1), __uint_as_float(y0bits));
+  const float q = fmaf(x, rcp, 12582912.0f) - 12582912.0f;
+  return fmaf(-q, mf, x) + 0.0f;
+}
+
+// Balanced base-128 split of an integer |r| < 2^13: r = lo + 128 hi with lo
+// in (-64, 64].  hi = RN((r - 0.5) / 128): r - 0.5 and its scaling are exact,
+// (r - 0.5) / 128 is never a half-integer, and |r - 0.5 - 128 hi| < 64 gives
+// lo = r - 128 hi in [-63, 64].
+__device__ __forceinline__ void split128(float r, float& lo, float& hi) {
+  hi = fmaf(r - 0.5f, 0.0078125f, 12582912.0f) - 12582912.0f;
+  lo = fmaf(-128.f, hi, r);
 }
 
 __global__ void __launch_bounds__(kRmThreads, 1)
@@ -1039,13 +1055,10 @@ __global__ void __launch_bounds__(kRmThreads, 1)
               for (int i = 0; i < 4; ++i) {
                 if (c0 + 2 * i < ncols) {
                   const float4 mc = s_mc[lb + i];
-                  // x + 0.0f: a -0 residue (all-zero bytes) becomes +0; then
-                  // lo, hi and lo + hi are never -0
-                  const float x = cmod_f32(pair_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y), mc.x, mc.y, mc.z) + 0.0f;
-                  // balanced base-128 split: x = lo + 128 hi, lo in (-64, 64]
-                  float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
-                  float lo = fmaf(-128.f, hi, x);
-                  if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
+                  // x is +0 for a zero residue; then lo, hi and lo + hi are never -0
+                  const float x = cmod2_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y);
+                  float lo, hi;
+                  split128(x, lo, hi);
                   dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
                   dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
                   dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
@@ -1064,10 +1077,9 @@ __global__ void __launch_bounds__(kRmThreads, 1)
                 } else if ((q & 1) == 0 && colx < ncols) {   // a pair starts at an even column
                   const int l = L1 + ((colx - L1) >> 1);
                   const float4 mc = s_mc[l];
-                  const float x = cmod_f32(pair_f32(y[q], y[q + 1], mc.x, mc.y), mc.x, mc.y, mc.z) + 0.0f;
-                  float hi = fmaf(x, 0.0078125f, 12582912.0f) - 12582912.0f;
-                  float lo = fmaf(-128.f, hi, x);
-                  if (lo <= -64.f) { lo += 128.f; hi -= 1.f; }
+                  const float x = cmod2_f32(y[q], y[q + 1], mc.x, mc.y);
+                  float lo, hi;
+                  split128(x, lo, hi);
                   uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (l - L1)) * pstride;
                   dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
                   dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);

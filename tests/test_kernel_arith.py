@@ -59,3 +59,39 @@ def test_fp32_rounded_quotient_is_exact_for_two_limb_moduli():
         rcp = np.float64(np.float32(1.0 / m))
         q = np.rint(y.astype(np.float64) * rcp).astype(np.int64)
         assert np.array_equal(q, np.floor_divide(2 * y + m, 2 * m)), m
+
+
+def test_tensor_core_two_limb_reduction_needs_no_correction():
+    """The warp-specialised tensor-core residues reduce a two-limb modulus
+    from the byte sums y0 (table halves |T0| <= 64) and y1 (|T1| <= 63) of at
+    most 265 bytes: r1 = y1 - RN(y1 rcp) m, x = y0 + 128 r1, r = x - RN(x rcp) m,
+    with no correction step.  Exhaustive over every |y1| <= 265 * 255 * 63 and
+    every |x| <= 265 * 255 * 64 + 128 * 8095 for a spread of the moduli: the
+    rounded quotient is round(y / m) and the remainder the centered residue."""
+    mods = [m for m in o.Params(1024, 2048).moduli if m > 255]
+    pick = sorted(set([mods[0], mods[-1]] + mods[:: max(1, len(mods) // 8)]))
+    y1max = 265 * 255 * 63
+    xmax = 265 * 255 * 64 + 128 * 8095
+    assert max(y1max, xmax) < 2 ** 23
+    for bound in (y1max, xmax):
+        y = np.arange(-bound, bound + 1, dtype=np.int64)
+        yf = y.astype(np.float64)
+        for m in pick:
+            rcp = np.float64(np.float32(1) / np.float32(m))     # RN(1/m), as the host computes it
+            assert rcp == np.float64(np.float32(1.0 / m))
+            q = np.rint(yf * rcp).astype(np.int64)              # y rcp is exact in binary64
+            r = y - q * m
+            assert r.min() >= -(m - 1) // 2 and r.max() <= (m - 1) // 2, m
+            assert np.array_equal(np.mod(r - y, m), np.zeros_like(y)), m
+
+
+def test_balanced_split_by_shifted_rounding():
+    """split128: hi = RN((r - 0.5) / 128), lo = r - 128 hi is the balanced
+    base-128 split (lo in (-64, 64]) for every |r| <= 8095."""
+    r = np.arange(-8095, 8096, dtype=np.int64)
+    h = (r.astype(np.float64) - 0.5) / 128.0
+    assert not np.any(h - np.floor(h) == 0.5)
+    hi = np.rint(h).astype(np.int64)
+    lo = r - 128 * hi
+    assert lo.min() == -63 and lo.max() == 64
+    assert np.array_equal(lo + 128 * hi, r)
