@@ -245,7 +245,7 @@ struct DevState {
   ListRef tct[9];               // tensor-core CRT tile lists (smem = kpad_max, lmax = L max)
   int tct_npad[9] = {0};
   std::vector<ListRef> cmt;     // tensor-core CRT sum tiles, one list per TMEM layout (smem = chunk width)
-  ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = groups max)
+  ListRef finl;                 // finish blocks of long accumulators (smem = D max, lmax = output limbs max)
   ListRef fsh[9];               // finish blocks of one-lane classes after the tensor-core sums
   std::vector<ListRef> rmt;     // warp-specialised tensor-core residue tiles, one list per TMEM layout (smem = cw)
   ListRef rtt;                  // tensor-core residue tiles (smem = kpad_max, lmax = L max)
@@ -772,7 +772,7 @@ struct TableImage {
   std::vector<std::array<int, 3>> cmt_seg, rmt_seg;
   size_t o_fsh[9] = {0};            // short finish blocks per one-lane class (after the tensor-core sums)
   int n_fsh[9] = {0};
-  int n_finl = 0, finl_dmax = 0, finl_gmax = 0;
+  int n_finl = 0, finl_dmax = 0, finl_nlmax = 0;
   size_t o_rmt = 0;
   size_t o_rtt = 0;                 // tensor-core residue tile list
   int n_rtt = 0, rtt_kpad = 0, rtt_npad = 0, rtt_l = 0;
@@ -1019,7 +1019,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       } else {
         for (int64_t bb = 0; bb < nt; ++bb) finl.push_back(make_int4(pi, (int)bb, 0, 0));
         ti.finl_dmax = std::max(ti.finl_dmax, h.D32);
-        ti.finl_gmax = std::max(ti.finl_gmax, h.crt_ngrp);
+        ti.finl_nlmax = std::max(ti.finl_nlmax, h.nl);
       }
     } else {
       const int epb = crt_class_elems_per_block(h.crt_cls);
@@ -1078,7 +1078,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     if (h.crt_mode == 0 && ti.crt_l[h.crt_cls] < h.L) return OZ2_EINTERNAL;
     if (h.crt_mode == 1 && (ti.tct_l[h.crt_cls] < h.L || ti.tct_kpad[h.crt_cls] < h.crt_kpad)) return OZ2_EINTERNAL;
     if (h.crt_mode == 2 && (h.crt_cw % 32 != 0 || h.crt_nvbuf * (h.crt_kpad / 2) + h.crt_nslot * h.crt_cw > 512 ||
-                            (h.crt_cls > 4 && (ti.finl_dmax < h.D32 || ti.finl_gmax < h.crt_ngrp))))
+                            (h.crt_cls > 4 && (ti.finl_dmax < h.D32 || ti.finl_nlmax < h.nl))))
       return OZ2_EINTERNAL;
   }
   std::vector<int4> cmt, rmt;
@@ -1094,7 +1094,7 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
     ti.na_rmt.push_back(side_a_prefix(kv.second));
     rmt.insert(rmt.end(), kv.second.begin(), kv.second.end());
   }
-  if (!finl.empty() && 3 * ti.finl_dmax * 4 + (ti.finl_dmax + 2 * ti.finl_gmax) * 128 * 4 > 200 * 1024)
+  if (!finl.empty() && crt_finish_long_smem(ti.finl_dmax, ti.finl_nlmax) > 200 * 1024)
     return OZ2_EINTERNAL;
   ti.o_cmt = ti.b.add(cmt.data(), cmt.size() * 16);
   for (int c = 0; c < 9; ++c) {
@@ -1158,7 +1158,7 @@ static void install_table_image(ozaki2_plan_s* pl, const TableImage& ti, uint8_t
   d.cmt.clear();
   for (const auto& sg : ti.cmt_seg)
     d.cmt.push_back(ListRef{reinterpret_cast<const int32_t*>(base + ti.o_cmt) + 4 * sg[0], sg[1], sg[2], 0});
-  d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_gmax};
+  d.finl = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_finl), ti.n_finl, ti.finl_dmax, ti.finl_nlmax};
   for (int c = 0; c < 9; ++c) d.fsh[c] = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_fsh[c]), ti.n_fsh[c], 0, 0};
   d.rtt = ListRef{reinterpret_cast<const int32_t*>(base + ti.o_rtt), ti.n_rtt, ti.rtt_kpad, ti.rtt_l, ti.na_rtt};
   d.rmt.clear();

@@ -281,14 +281,19 @@ __device__ __forceinline__ int crt_ef(const ProbDev& P, int64_t idx) {
   return __ldg(P.e + row) + __ldg(P.f + col);
 }
 
-// Round |c_hat| (nd digits in column e of s_mag, highest nonzero digit `top`,
-// -1 for zero) times 2^(e_i + f_j - 2t) to p bits, round-half-even, and write
-// output idx (limbs, exponent and sign, or a binary64 value); ef = e_i + f_j.
+// Round |c_hat| times 2^(e_i + f_j - 2t) to p bits, round-half-even, and
+// write output idx (limbs, exponent and sign, or a binary64 value); ef =
+// e_i + f_j.  Digits wbase .. wbase + nd - 1 of |c_hat| are in column e of
+// s_mag (row w - wbase for digit w), `top` is the highest nonzero digit (-1
+// for zero, else within the window), and sticky_below is nonzero iff a digit
+// below wbase is (the window covers every digit the rounding reads but the
+// sticky ones).
 __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t* s_mag, int ldm, int e, int nd,
-                                             int top, bool neg, int64_t idx, int ef) {
+                                             int top, bool neg, int64_t idx, int ef, int wbase = 0,
+                                             uint32_t sticky_below = 0u) {
   const int64_t row = idx / P.N, col = idx - row * P.N;
   auto mag_word = [&](int w) -> uint32_t {
-    return (w >= 0 && w < nd) ? s_mag[w * ldm + e] : 0u;
+    return (w >= wbase && w < wbase + nd) ? s_mag[(w - wbase) * ldm + e] : 0u;
   };
   const int p = P.p, nl = P.nl;
   if (top < 0) {
@@ -308,8 +313,8 @@ __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t
   if (rpos >= 0) {
     const uint32_t rb = (mag_word(rpos >> 5) >> (rpos & 31)) & 1u;
     const uint32_t lsb = (mag_word(sh >> 5) >> (sh & 31)) & 1u;
-    uint32_t sticky = mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u);
-    for (int w = (rpos >> 5) - 1; w >= 0 && !sticky; --w) sticky = mag_word(w);
+    uint32_t sticky = (mag_word(rpos >> 5) & ((1u << (rpos & 31)) - 1u)) | sticky_below;
+    for (int w = (rpos >> 5) - 1; w >= wbase && !sticky; --w) sticky = mag_word(w);
     up = rb & ((sticky != 0u) | lsb);
   }
   // the 2 nl output words: F = floor(|c_hat| 2^(64 nl - n)) with the low
@@ -816,32 +821,36 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
 }
 
 // ---------------------------------------------------------------------------
-// Finish of long accumulators (crt_mode 2, more than 40 digits): one thread
-// per output, R assembled from the tensor-core chunk sums into shared memory
-// as a [D][128] digit column per thread, then the same steps as crt_finish with
-// digit-serial carries: subtract P once if R >= P (R + (2^(32 D) - P) carries
-// out of digit D - 1 exactly when R >= P), the sign test against floor(P/2)
-// + 1, |c_hat| = P - x0 for negative results, and the rounding.
+// Finish of long accumulators (crt_mode 2, more than 24 digits): one thread
+// per output, digit-serial, with no copy of R in shared memory.  Digit d of
+//   R = (sum_g Q_g 2^(224 g) + alpha~ (2^(32 D) - P)) mod 2^(32 D)
+// is rebuilt from the group words (read coalesced across the block, straight
+// from global memory) each time it is needed:
+//   pass 1: the carries out of R + (2^(32 D) - P) (R >= P: x0 = R - P, else
+//           x0 = R) and of x + (2^(32 D) - floor(P/2) - 1) for x = R and
+//           x = R - P (x0 > floor(P/2): c_hat = x0 - P is negative);
+//   pass 2: the digits of |c_hat| = x0 or P - x0, the check x0 < P, the
+//           highest nonzero digit, and a window of the W = 2 nl + 4 highest
+//           digits D - W .. D - 1 in shared memory (the OR of the digits
+//           below it kept as a sticky word);
+//   the rounding reads its words from the window.  When |c_hat| is so small
+//   that a word below the window is needed, a third pass writes the window
+//   from the lowest needed word on.
 // Block list entry: {problem, block of 128 outputs, 0, 0}.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 128;
-
-// asynchronous 4-byte copy global -> shared (completes at cp.async.wait_group)
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
 
 __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const int4* __restrict__ blk) {
   extern __shared__ __align__(16) uint32_t sf[];
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
   const int D = P.D32, ng = P.crt_ngrp;
+  const int W = 2 * P.nl + 4;
   const CrtView cv = crt_view(T.crt_pool, P);
-  uint32_t* s_P = sf;                   // [D]
-  uint32_t* s_negP = s_P + D;           // [D]
+  uint32_t* s_negP = sf;                // [D]
   uint32_t* s_negH1 = s_negP + D;       // [D]
-  uint32_t* s_R = s_negH1 + D;          // [D][128]
-  uint32_t* s_W = s_R + D * kFinThreads;   // [2 ng][128]: words 7, 8 of every group
+  uint32_t* s_P = s_negH1 + D;          // [D]
+  uint32_t* s_win = s_P + D;            // [W][128]
   for (int i = threadIdx.x; i < D; i += kFinThreads) {
     s_P[i] = __ldg(cv.P + i);
     s_negP[i] = __ldg(cv.negP + i);
@@ -853,69 +862,95 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   if (idx >= (int64_t)P.M * P.N) return;
   const int ef = crt_ef(P, idx);
   const int64_t up = P.upitch;
-  // the group words, copied asynchronously (all in flight at once; coalesced
-  // across the block): words 0..6 of group d / 7 in digit order, and the
-  // overlap words 7, 8 of every group
-  const uint32_t* const qcol = P.crt_q + idx;   // in a register across the copies' memory clobbers
-  for (int d = 0; d < D; ++d) {
-    const int g = d / 7;
-    if (g < ng) cp_async4(s_R + d * kFinThreads + e, qcol + ((int64_t)g * 9 + (d - 7 * g)) * up);
-    else s_R[d * kFinThreads + e] = 0u;
-  }
-  for (int g = 0; g < ng; ++g) {
-    cp_async4(s_W + (2 * g) * kFinThreads + e, qcol + ((int64_t)g * 9 + 7) * up);
-    cp_async4(s_W + (2 * g + 1) * kFinThreads + e, qcol + ((int64_t)g * 9 + 8) * up);
-  }
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-  const uint64_t alpha = P.crt_alpha[idx];
-  // pass 1, least significant digit first: R = (S + alpha~ (2^(32 D) - P)) mod
-  // 2^(32 D), and the carries out of R + (2^(32 D) - P) (R >= P), of
-  // R + (2^(32 D) - floor(P/2) - 1) and of (R - P) + the same (the sign of the
-  // signed representative either way)
-  uint64_t carry = 0;
+  const uint32_t* const qcol = P.crt_q + idx;
+  const uint32_t alpha = __ldg(P.crt_alpha + idx);
+  // the digits of R in order, to f(d, R_d): word k of group g is digit 7 g
+  // + k (k < 7); words 7 and 8 of group g add into digits 7 g + 7 and
+  // 7 g + 8.  The nine words of group g + 1 are loaded while group g's
+  // digits are carried.
+  auto for_each_digit = [&](auto&& f) {
+    uint32_t wc[9], wn[9];
+    auto load = [&](int g, uint32_t (&w)[9]) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[k] = g < ng ? __ldg(qcol + ((int64_t)g * 9 + k) * up) : 0u;
+    };
+    load(0, wc);
+    uint32_t prev7 = 0, prev8 = 0;
+    uint64_t carry = 0;
+    for (int g = 0; 7 * g < D; ++g) {
+      load(g + 1, wn);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const int d = 7 * g + k;
+        if (d < D) {
+          uint64_t x = carry + (uint64_t)alpha * s_negP[d] + wc[k];
+          if (k == 0) x += prev7;
+          if (k == 1) x += prev8;
+          carry = x >> 32;
+          f(d, (uint32_t)x);
+        }
+      }
+      prev7 = wc[7];
+      prev8 = wc[8];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) wc[k] = wn[k];
+    }
+  };
+  // pass 1
   uint32_t c1 = 0, c3 = 0, c4 = 0;
-  for (int d = 0; d < D; ++d) {
-    const int g = d / 7, k = d - 7 * g;
-    uint64_t x = carry + alpha * s_negP[d] + s_R[d * kFinThreads + e];
-    if (k < 2 && g >= 1 && g - 1 < ng) x += s_W[(2 * (g - 1) + k) * kFinThreads + e];
-    const uint32_t r = (uint32_t)x;
-    carry = x >> 32;
-    s_R[d * kFinThreads + e] = r;
-    const uint64_t t1 = (uint64_t)r + s_negP[d] + c1;       // R - P
+  for_each_digit([&](int d, uint32_t r) {
+    const uint64_t t1 = (uint64_t)r + s_negP[d] + c1;        // R - P
     c1 = (uint32_t)(t1 >> 32);
-    const uint64_t t3 = (uint64_t)r + s_negH1[d] + c3;
-    c3 = (uint32_t)(t3 >> 32);
-    const uint64_t t4 = (uint64_t)(uint32_t)t1 + s_negH1[d] + c4;
-    c4 = (uint32_t)(t4 >> 32);
-  }
+    c3 = (uint32_t)(((uint64_t)r + s_negH1[d] + c3) >> 32);
+    c4 = (uint32_t)(((uint64_t)(uint32_t)t1 + s_negH1[d] + c4) >> 32);
+  });
   const bool ge = c1 != 0;               // R >= P: x0 = R - P
   const bool neg = ge ? c4 != 0 : c3 != 0;
-  // pass 2: |c_hat| = x0, or P - x0 for negative results; x0 < P is checked
-  uint32_t cs = 0, br = 0, cc = 0;
+  uint32_t* const dbg = P.dbg_chat != nullptr ? P.dbg_chat + idx * (int64_t)(D + 1) : nullptr;
+  if (dbg) dbg[0] = neg;
+  // pass 2 (and 3): |c_hat| digit by digit; digits from wbase on go to the
+  // window, the ones below it into the sticky word
   int top = -1;
-  for (int d = 0; d < D; ++d) {
-    const uint32_t r = s_R[d * kFinThreads + e];
-    const uint64_t t1 = (uint64_t)r + s_negP[d] + cs;
-    cs = (uint32_t)(t1 >> 32);
-    const uint32_t x0 = ge ? (uint32_t)t1 : r;
-    const uint64_t tc = (uint64_t)x0 + s_negP[d] + cc;     // carry out iff x0 >= P
-    cc = (uint32_t)(tc >> 32);
-    uint32_t mag = x0;
-    if (neg) {
+  uint32_t topv = 0, sticky = 0, bad = 0;
+  auto magnitude = [&](int wbase, bool dump) {
+    uint32_t cs = 0, cc = 0, br = 0;
+    top = -1;
+    sticky = 0;
+    for_each_digit([&](int d, uint32_t r) {
+      const uint64_t t1 = (uint64_t)r + s_negP[d] + cs;
+      cs = (uint32_t)(t1 >> 32);
+      const uint32_t x0 = ge ? (uint32_t)t1 : r;
+      cc = (uint32_t)(((uint64_t)x0 + s_negP[d] + cc) >> 32);   // carry out iff x0 >= P
       const uint64_t tn = (uint64_t)s_P[d] - x0 - br;
-      mag = (uint32_t)tn;
       br = (uint32_t)(tn >> 63);
+      const uint32_t mag = neg ? (uint32_t)tn : x0;
+      if (mag) {
+        top = d;
+        topv = mag;
+      }
+      if (d >= wbase) {
+        if (d < wbase + W) s_win[(d - wbase) * kFinThreads + e] = mag;
+      } else {
+        sticky |= mag;
+      }
+      if (dump) dbg[1 + d] = mag;
+    });
+    bad = cc;
+  };
+  int wbase = D > W ? D - W : 0;
+  magnitude(wbase, dbg != nullptr);
+  if (bad) atomicOr(T.status, kStatusCrtRange);
+  if (top >= 0) {
+    // lowest word the rounding reads: the one holding the round bit (or 0
+    // when |c_hat| has at most p bits)
+    const int n = 32 * top + 32 - __clz(topv);
+    const int lo = n > P.p ? (n - P.p - 1) >> 5 : 0;
+    if (lo < wbase) {
+      wbase = lo;
+      magnitude(wbase, false);
     }
-    s_R[d * kFinThreads + e] = mag;
-    if (mag) top = d;
   }
-  if (cc) atomicOr(T.status, kStatusCrtRange);
-  if (P.dbg_chat != nullptr) {
-    uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
-    dst[0] = neg;
-    for (int d = 0; d < D; ++d) dst[1 + d] = s_R[d * kFinThreads + e];
-  }
-  crt_round_write(P, s_R, kFinThreads, e, D, top, neg, idx, ef);
+  crt_round_write(P, s_win, kFinThreads, e, W, top, neg, idx, ef, wbase, sticky);
 }
 
 // The finish of short accumulators (D <= ND digits, used up to 24) after the
@@ -1496,10 +1531,12 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
+int crt_finish_long_smem(int dmax, int nlmax) { return 3 * dmax * 4 + (2 * nlmax + 4) * kFinThreads * 4; }
+
+cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int nlmax,
                                    cudaStream_t s) {
   if (nblk == 0) return cudaSuccess;
-  const int smem = 3 * dmax * 4 + dmax * kFinThreads * 4 + 2 * gmax * kFinThreads * 4;
+  const int smem = crt_finish_long_smem(dmax, nlmax);
   k_crt_fin_long<<<nblk, kFinThreads, smem, s>>>(t, reinterpret_cast<const int4*>(blk));
   return cudaGetLastError();
 }

@@ -183,7 +183,8 @@ int crt_mm_chunk(int kpad, int npad, int* nslot);
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
 // the finish of one-lane classes after the tensor-core sums (the host uses it up to 24 digits)
 cudaError_t launch_crt_fin_short(const DevTables& t, int cls, const int32_t* blk, int nblk, cudaStream_t s);
-cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int gmax,
+int crt_finish_long_smem(int dmax, int nlmax);
+cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int nlmax,
                                    cudaStream_t s);
 // Tensor-core residues: persistent tiles of 4 lines x 32 k.
 cudaError_t launch_residues_tc(const DevTables& t, const int32_t* tiles, int ntiles, int kpad_max, int npad_max,
