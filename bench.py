@@ -245,10 +245,10 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # one pass, the full size); the source summaries are under profiles/.  A
 # kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_4096_p2048": {"scan": 403938240, "residues": 83432203520, "gemm": 157047812288,
-                        "crt_sums": 23148799872, "crt_finish": 16030045888},
-    "gemm_1024_p256": {"scan": 25206464, "residues": 440552128, "gemm": 569037696, "crt_sums": 222713088,
-                       "crt_finish": 121899328},
+    "gemm_4096_p2048": {"scan": 403863104, "residues": 82734957504, "gemm": 121629064768,
+                        "crt_sums": 23148131264, "crt_finish": 20064052480},
+    "gemm_1024_p256": {"scan": 25205952, "residues": 440532608, "gemm": 560699136, "crt_sums": 222623872,
+                       "crt_finish": 121983360},
 }
 
 
