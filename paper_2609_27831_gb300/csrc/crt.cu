@@ -840,21 +840,59 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 128;
 
+// Carry chains over a group of N digits with the carry (or borrow) in and
+// out as a register: cin must be 0 or 1; the chain starts by turning it into
+// the carry flag (cin + 0xffffffff carries out iff cin = 1).
+template <int N>
+__device__ __forceinline__ uint32_t add_chain(const uint32_t (&a)[N], const uint32_t (&b)[N], uint32_t (&s)[N],
+                                              uint32_t cin) {
+  uint32_t t, c;
+  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(t) : "r"(cin));
+#pragma unroll
+  for (int d = 0; d < N; ++d) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(s[d]) : "r"(a[d]), "r"(b[d]));
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(c));
+  return c;
+}
+template <int N>
+__device__ __forceinline__ uint32_t carry_chain(const uint32_t (&a)[N], const uint32_t (&b)[N], uint32_t cin) {
+  uint32_t t, c;
+  asm volatile("add.cc.u32 %0, %1, 0xffffffff;" : "=r"(t) : "r"(cin));
+#pragma unroll
+  for (int d = 0; d < N; ++d) asm volatile("addc.cc.u32 %0, %1, %2;" : "=r"(t) : "r"(a[d]), "r"(b[d]));
+  asm volatile("addc.u32 %0, 0, 0;" : "=r"(c));
+  return c;
+}
+// s = a - b - bin, returns the borrow out (bin 0 or 1)
+template <int N>
+__device__ __forceinline__ uint32_t sub_chain(const uint32_t (&a)[N], const uint32_t (&b)[N], uint32_t (&s)[N],
+                                              uint32_t bin) {
+  uint32_t t;
+  asm volatile("sub.cc.u32 %0, 0, %1;" : "=r"(t) : "r"(bin));
+#pragma unroll
+  for (int d = 0; d < N; ++d) asm volatile("subc.cc.u32 %0, %1, %2;" : "=r"(s[d]) : "r"(a[d]), "r"(b[d]));
+  asm volatile("subc.u32 %0, 0, 0;" : "=r"(t));
+  return t & 1u;
+}
+
 __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const int4* __restrict__ blk) {
   extern __shared__ __align__(16) uint32_t sf[];
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
   const int D = P.D32, ng = P.crt_ngrp;
+  const int DG = 7 * ((D + 6) / 7);     // digits rounded up to whole groups of seven
   const int W = 2 * P.nl + 4;
   const CrtView cv = crt_view(T.crt_pool, P);
-  uint32_t* s_negP = sf;                // [D]
-  uint32_t* s_negH1 = s_negP + D;       // [D]
-  uint32_t* s_P = s_negH1 + D;          // [D]
-  uint32_t* s_win = s_P + D;            // [W][128]
-  for (int i = threadIdx.x; i < D; i += kFinThreads) {
-    s_P[i] = __ldg(cv.P + i);
-    s_negP[i] = __ldg(cv.negP + i);
-    s_negH1[i] = __ldg(cv.negH1 + i);
+  // tables over DG digits: 2^(32 DG) - P and 2^(32 DG) - floor(P/2) - 1
+  // (all ones from digit D on, so that every carry chain may run over whole
+  // groups: R is zero there) and P (zero from digit D on)
+  uint32_t* s_negP = sf;                // [DG]
+  uint32_t* s_negH1 = s_negP + DG;      // [DG]
+  uint32_t* s_P = s_negH1 + DG;         // [DG]
+  uint32_t* s_win = s_P + DG;           // [W][128]
+  for (int i = threadIdx.x; i < DG; i += kFinThreads) {
+    s_P[i] = i < D ? __ldg(cv.P + i) : 0u;
+    s_negP[i] = i < D ? __ldg(cv.negP + i) : ~0u;
+    s_negH1[i] = i < D ? __ldg(cv.negH1 + i) : ~0u;
   }
   __syncthreads();
   const int e = threadIdx.x;
@@ -864,11 +902,11 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   const int64_t up = P.upitch;
   const uint32_t* const qcol = P.crt_q + idx;
   const uint32_t alpha = __ldg(P.crt_alpha + idx);
-  // the digits of R in order, to f(d, R_d): word k of group g is digit 7 g
-  // + k (k < 7); words 7 and 8 of group g add into digits 7 g + 7 and
-  // 7 g + 8.  The nine words of group g + 1 are loaded while group g's
-  // digits are carried.
-  auto for_each_digit = [&](auto&& f) {
+  // R seven digits at a time, to f(g, r): word k of group g is digit 7 g + k
+  // (k < 7); words 7 and 8 of group g add into digits 7 g + 7 and 7 g + 8;
+  // digits from D on are zero.  The nine words of group g + 1 are loaded
+  // while group g's digits are formed.
+  auto for_each_group = [&](auto&& f) {
     uint32_t wc[9], wn[9];
     auto load = [&](int g, uint32_t (&w)[9]) {
 #pragma unroll
@@ -879,61 +917,74 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     uint64_t carry = 0;
     for (int g = 0; 7 * g < D; ++g) {
       load(g + 1, wn);
+      uint32_t r[7];
 #pragma unroll
       for (int k = 0; k < 7; ++k) {
         const int d = 7 * g + k;
-        if (d < D) {
-          uint64_t x = carry + (uint64_t)alpha * s_negP[d] + wc[k];
-          if (k == 0) x += prev7;
-          if (k == 1) x += prev8;
-          carry = x >> 32;
-          f(d, (uint32_t)x);
-        }
+        uint64_t x = carry + (uint64_t)alpha * s_negP[d] + wc[k];
+        if (k == 0) x += prev7;
+        if (k == 1) x += prev8;
+        carry = x >> 32;
+        r[k] = d < D ? (uint32_t)x : 0u;
       }
+      f(g, r);
       prev7 = wc[7];
       prev8 = wc[8];
 #pragma unroll
       for (int k = 0; k < 9; ++k) wc[k] = wn[k];
     }
   };
-  // pass 1
+  auto tab7 = [&](const uint32_t* t, int g, uint32_t (&v)[7]) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = t[7 * g + k];
+  };
+  // pass 1: R >= P (R + 2^(32 DG) - P carries out), and the sign of x0 for
+  // either choice (x + 2^(32 DG) - floor(P/2) - 1 carries out iff x > floor(P/2))
   uint32_t c1 = 0, c3 = 0, c4 = 0;
-  for_each_digit([&](int d, uint32_t r) {
-    const uint64_t t1 = (uint64_t)r + s_negP[d] + c1;        // R - P
-    c1 = (uint32_t)(t1 >> 32);
-    c3 = (uint32_t)(((uint64_t)r + s_negH1[d] + c3) >> 32);
-    c4 = (uint32_t)(((uint64_t)(uint32_t)t1 + s_negH1[d] + c4) >> 32);
+  for_each_group([&](int g, const uint32_t (&r)[7]) {
+    uint32_t np[7], nh[7], t1[7];
+    tab7(s_negP, g, np);
+    tab7(s_negH1, g, nh);
+    c1 = add_chain<7>(r, np, t1, c1);                        // R - P
+    c3 = carry_chain<7>(r, nh, c3);
+    c4 = carry_chain<7>(t1, nh, c4);
   });
   const bool ge = c1 != 0;               // R >= P: x0 = R - P
   const bool neg = ge ? c4 != 0 : c3 != 0;
   uint32_t* const dbg = P.dbg_chat != nullptr ? P.dbg_chat + idx * (int64_t)(D + 1) : nullptr;
   if (dbg) dbg[0] = neg;
-  // pass 2 (and 3): |c_hat| digit by digit; digits from wbase on go to the
-  // window, the ones below it into the sticky word
+  // pass 2 (and 3): |c_hat| = x0 or P - x0 digit by digit; digits from
+  // wbase on go to the window, the ones below it into the sticky word
   int top = -1;
   uint32_t topv = 0, sticky = 0, bad = 0;
   auto magnitude = [&](int wbase, bool dump) {
     uint32_t cs = 0, cc = 0, br = 0;
     top = -1;
     sticky = 0;
-    for_each_digit([&](int d, uint32_t r) {
-      const uint64_t t1 = (uint64_t)r + s_negP[d] + cs;
-      cs = (uint32_t)(t1 >> 32);
-      const uint32_t x0 = ge ? (uint32_t)t1 : r;
-      cc = (uint32_t)(((uint64_t)x0 + s_negP[d] + cc) >> 32);   // carry out iff x0 >= P
-      const uint64_t tn = (uint64_t)s_P[d] - x0 - br;
-      br = (uint32_t)(tn >> 63);
-      const uint32_t mag = neg ? (uint32_t)tn : x0;
-      if (mag) {
-        top = d;
-        topv = mag;
+    for_each_group([&](int g, const uint32_t (&r)[7]) {
+      uint32_t np[7], pp[7], x0[7], pm[7];
+      tab7(s_negP, g, np);
+      tab7(s_P, g, pp);
+      cs = add_chain<7>(r, np, x0, cs);                      // R - P
+#pragma unroll
+      for (int k = 0; k < 7; ++k) x0[k] = ge ? x0[k] : r[k];
+      cc = carry_chain<7>(x0, np, cc);                       // carries out iff x0 >= P
+      br = sub_chain<7>(pp, x0, pm, br);                     // P - x0
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const int d = 7 * g + k;
+        const uint32_t mag = neg ? pm[k] : x0[k];
+        if (mag) {
+          top = d;
+          topv = mag;
+        }
+        if (d >= wbase) {
+          if (d < wbase + W) s_win[(d - wbase) * kFinThreads + e] = mag;
+        } else {
+          sticky |= mag;
+        }
+        if (dump && d < D) dbg[1 + d] = mag;
       }
-      if (d >= wbase) {
-        if (d < wbase + W) s_win[(d - wbase) * kFinThreads + e] = mag;
-      } else {
-        sticky |= mag;
-      }
-      if (dump) dbg[1 + d] = mag;
     });
     bad = cc;
   };
@@ -1531,7 +1582,7 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
   return cudaGetLastError();
 }
 
-int crt_finish_long_smem(int dmax, int nlmax) { return 3 * dmax * 4 + (2 * nlmax + 4) * kFinThreads * 4; }
+int crt_finish_long_smem(int dmax, int nlmax) { return 3 * (dmax + 6) * 4 + (2 * nlmax + 4) * kFinThreads * 4; }
 
 cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int nlmax,
                                    cudaStream_t s) {
