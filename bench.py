@@ -246,7 +246,7 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # kernel changed since its capture is absent.
 NCU_TRAFFIC = {
     "gemm_4096_p2048": {"scan": 403863104, "residues": 82734957504, "gemm": 121629064768,
-                        "crt_sums": 23148131264, "crt_finish": 20064052480},
+                        "crt_sums": 23148131264},
     "gemm_1024_p256": {"scan": 25205952, "residues": 440532608, "gemm": 560699136, "crt_sums": 222623872,
                        "crt_finish": 121983360},
 }
