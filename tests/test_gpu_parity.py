@@ -220,6 +220,30 @@ def test_p2048_small(ozk):
     assert got3["plan"].info["crt_mode"] == 0 and got3["plan"].info["res_mode"] == 0
 
 
+@pytest.mark.parametrize("p", [1024, 2048])
+def test_long_finish_small_and_zero_results(ozk, p):
+    """The finish of long accumulators keeps only the highest digits of |c_hat|
+    in shared memory and moves that window down when a word below it is
+    needed: outputs whose large terms cancel (|c_hat| far below its usual
+    size), an exact zero, and ordinary ones, every stage bit-exact."""
+    A = mat_from_values([
+        [(1, 0), (1, 0), (1, -1000), (0, 0)],
+        [(3, 5), (-3, 5), (5, -3000), (1, -3100)],
+        [(1, 0), (1, 0), (0, 0), (0, 0)],
+        [(5, 2), (7, 1), (-9, -40), (11, -3)],
+    ], p)
+    B = mat_from_values([
+        [(1, 0), (7, 10), (1, 0)],
+        [(-1, 0), (7, 10), (-1, 0)],
+        [(1, 0), (1, -5), (1, -2000)],
+        [(1, 0), (3, 1), (0, 0)],
+    ], p)
+    got, ref = assert_full_parity(ozk, A, B, p, truth=False)
+    assert got["plan"].info["crt_mode"] == 2 and got["plan"].info["crt_digits"] > 24
+    assert ref["chat"][2, 0] == 0 and ref["chat"][0, 0] != 0
+    assert abs(ref["chat"][0, 0]).bit_length() < abs(ref["chat"][0, 1]).bit_length() - 64
+
+
 @pytest.mark.parametrize("p", [300, 700])
 def test_crt_engines_bit_exact(ozk, p):
     """The CRT engines (automatic: the tensor-core sums above 20 digits, CUDA
