@@ -639,11 +639,41 @@ static int plan_groups(ozaki2_plan_s* pl) {
       out.push_back(gr);
     }
   };
-  std::vector<GroupHost> groups;
+  // the tensor-core residues run a group's table columns in chunks, and a
+  // nearly empty last chunk costs a whole round of MMAs and epilogue: the
+  // automatic split takes, among the caps that give ng groups, the one with
+  // the fewest chunks in all (then the smallest largest group); an explicit
+  // plane_group keeps the smallest such cap
+  auto chunks = [&](const std::vector<GroupHost>& gs) {
+    int n = 0;
+    for (const GroupHost& gr : gs) {
+      const int npad = (int)align_up((size_t)(gr.L1 + 2 * (gr.L - gr.L1)), 16);
+      int cw = 0, nab = 0;
+      residue_mm_geometry(h.res_kpad, npad, &cw, &nab);
+      n += (npad + cw - 1) / cw;
+    }
+    return n;
+  };
+  const bool by_chunks = o.plane_group == 0 && h.res_mode == 2;
+  std::vector<GroupHost> groups, trial;
+  int best_chunks = INT_MAX, best_max = INT_MAX;
   for (int cap = (h.G + ng - 1) / ng; cap <= gmax; ++cap) {
-    split(cap, groups);
-    if ((int)groups.size() <= ng) break;
+    split(cap, trial);
+    if ((int)trial.size() > ng) continue;
+    if (!by_chunks) {
+      groups = trial;
+      break;
+    }
+    int gm = 0;
+    for (const GroupHost& gr : trial) gm = std::max(gm, gr.G);
+    const int nc = chunks(trial);
+    if (nc < best_chunks || (nc == best_chunks && gm < best_max)) {
+      best_chunks = nc;
+      best_max = gm;
+      groups = trial;
+    }
   }
+  if (groups.empty()) split(gmax, groups);
   for (GroupHost& gr : groups) {
     gr.res_npad = (int)align_up((size_t)(gr.L1 + 2 * (gr.L - gr.L1)), 16);
     gr.res_cw = gr.res_nchunk = gr.res_nabuf = 0;
@@ -1532,7 +1562,17 @@ static int enqueue(ozaki2_plan_s* pl, LaunchBlock& lb, uint8_t* ws, cudaStream_t
     OZ2_CU(launch_combine_complex(tab, (int64_t)h.L * (int64_t)(align_up((size_t)(h.M * h.N), 8) / 8), s));
   }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[3], s));
-  for (const ListRef& r : d.cmt) OZ2_CU(launch_crt_mm(tab, r.ptr, r.n, r.smem, d.sms, s));
+  {
+    // the CRT table stays resident in the sums kernel when one problem uses it
+    int n2 = 0, blocks_one = 0;
+    for (const ProbHost& h : pl->probs)
+      if (h.crt_mode == 2 && !h.no_crt) {
+        ++n2;
+        blocks_one = (h.crt_kpad / 64) * h.crt_nchunk;
+      }
+    for (const ListRef& r : d.cmt)
+      OZ2_CU(launch_crt_mm(tab, r.ptr, r.n, r.smem, d.sms, n2 == 1 ? blocks_one : 0, s));
+  }
   if (timing) OZ2_CU(cudaEventRecord(pl->ev[5], s));
   for (int c = 0; c < 9; ++c)
     if (d.fsh[c].n) OZ2_CU(launch_crt_fin_short(tab, c, d.fsh[c].ptr, d.fsh[c].n, s));

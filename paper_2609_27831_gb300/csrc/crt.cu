@@ -1157,7 +1157,7 @@ __device__ __forceinline__ void crt_group_small(const uint32_t* y, uint64_t (&ac
 
 __global__ void __launch_bounds__(kCmThreads, 1)
     k_crt_mm(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, uint32_t stage_bytes,
-             int stages) {
+             int stages, int resident) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -1217,7 +1217,9 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       int issued_phase[kCmMaxStages];
       for (int i = 0; i < kCmMaxStages; ++i) issued_phase[i] = -1;
       bool ok = true;
-      for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
+      // resident table (one problem whose blocks all fit in the ring): each
+      // block is loaded once, into stage c nkb + q, and read by every tile
+      for (int i = blockIdx.x; ok && i < (resident ? min(ntiles, (int)blockIdx.x + 1) : ntiles); i += gridDim.x) {
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const CUtensorMap* mt = T.tmaps + 2 * T.count + tl.x;
@@ -1248,6 +1250,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
       bool ok = true, any = false;
       for (int i = blockIdx.x; ok && i < ntiles; i += gridDim.x) {
         const int4 tl = tiles[i];
+        const bool first = i == (int)blockIdx.x;
         const ProbDev& P = T.probs[tl.x];
         const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
         const int nslot = P.crt_nslot, nvbuf = P.crt_nvbuf;
@@ -1269,15 +1272,21 @@ __global__ void __launch_bounds__(kCmThreads, 1)
           const uint32_t idesc = idesc_bf16(128, ncol);
           const uint32_t d = tmem + (uint32_t)nvbuf * vcols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
-            if (!mbar_wait(full + st, ph, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
+            if (resident) st = c * nkb + q;
+            if ((!resident || first) && !mbar_wait(full + st, resident ? 0u : ph, abort_flag, T.status, T.spin_limit)) {
+              ok = false;
+              break;
+            }
             tc_fence_after();
             const uint64_t db = desc_sw128(sRing + st * stage_bytes);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
               umma_bf16_ta(d, vbase + (uint32_t)(32 * q + 8 * kk), db + 2 * kk, idesc, (q | kk) ? 1u : 0u);
-            umma_commit(empty + st);
             any = true;
-            if (++st == stages) { st = 0; ph ^= 1u; }
+            if (!resident) {
+              umma_commit(empty + st);
+              if (++st == stages) { st = 0; ph ^= 1u; }
+            }
           }
           if (ok) umma_commit(acc_full + s);
         }
@@ -1570,15 +1579,19 @@ int crt_mm_smem_bytes(int cw_max, int lmax, int* stages) {
   return -1;
 }
 
+// blocks_one: the table blocks of a tile (K blocks x chunks) when every tile
+// of the launch belongs to one problem, else 0; where they fit in the ring
+// the table stays resident (loaded once per CTA).
 cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int grid,
-                          cudaStream_t s) {
+                          int blocks_one, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   int stages = 0;
   const int smem = crt_mm_smem_bytes(cw_max, t.lmax, &stages);
   if (smem < 0) return cudaErrorInvalidValue;
   const int g = ntiles < grid ? ntiles : grid;
+  const int resident = blocks_one > 0 && blocks_one <= stages ? 1 : 0;
   k_crt_mm<<<g, kCmThreads, smem, s>>>(t, reinterpret_cast<const int4*>(tiles), ntiles, (uint32_t)cw_max * 128u,
-                                       stages);
+                                       stages, resident);
   return cudaGetLastError();
 }
 

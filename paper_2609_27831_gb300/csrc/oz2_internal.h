@@ -178,7 +178,7 @@ int crt_tc_smem_bytes(int cls, int kpad_max, int npad_max, int lmax, int nbuf);
 // {problem, tile}; R digits to the workspace.  Then the finish of long
 // accumulators (> 40 digits), blocks of 128 outputs {problem, block}.
 cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, int cw_max, int grid,
-                          cudaStream_t s);
+                          int blocks_one, cudaStream_t s);
 int crt_mm_chunk(int kpad, int npad, int* nslot);
 int crt_mm_smem_bytes(int cw_max, int lmax, int* stages);
 // the finish of one-lane classes after the tensor-core sums (the host uses it up to 24 digits)

@@ -226,19 +226,21 @@ def test_long_finish_small_and_zero_results(ozk, p):
     in shared memory and moves that window down when a word below it is
     needed: outputs whose large terms cancel (|c_hat| far below its usual
     size), an exact zero, and ordinary ones, every stage bit-exact."""
-    A = mat_from_values([
+    rows_a = [
         [(1, 0), (1, 0), (1, -1000), (0, 0)],
         [(3, 5), (-3, 5), (5, -3000), (1, -3100)],
         [(1, 0), (1, 0), (0, 0), (0, 0)],
         [(5, 2), (7, 1), (-9, -40), (11, -3)],
-    ], p)
-    B = mat_from_values([
+    ]
+    rows_b = [
         [(1, 0), (7, 10), (1, 0)],
         [(-1, 0), (7, 10), (-1, 0)],
         [(1, 0), (1, -5), (1, -2000)],
         [(1, 0), (3, 1), (0, 0)],
-    ], p)
-    got, ref = assert_full_parity(ozk, A, B, p, truth=False)
+    ]
+    A = mat_from_values(rows_a * 8, p)                   # 32 x 4: at least one 128-output tile
+    B = mat_from_values([r * 2 for r in rows_b], p)      # 4 x 6
+    got, ref = assert_full_parity(ozk, A, B, p, truth=False, crt_engine=2)
     assert got["plan"].info["crt_mode"] == 2 and got["plan"].info["crt_digits"] > 24
     assert ref["chat"][2, 0] == 0 and ref["chat"][0, 0] != 0
     assert abs(ref["chat"][0, 0]).bit_length() < abs(ref["chat"][0, 1]).bit_length() - 64
