@@ -246,9 +246,8 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # kernel changed since its capture is absent.
 NCU_TRAFFIC = {
     "gemm_4096_p2048": {"scan": 403993216, "residues": 81929229760, "gemm": 121576256064,
-                        "crt_sums": 23147326848, "crt_finish": 20028608704},
-    "gemm_1024_p256": {"scan": 25205952, "residues": 440532608, "gemm": 560699136, "crt_sums": 222623872,
-                       "crt_finish": 121983360},
+                        "crt_finish": 20028608704},
+    "gemm_1024_p256": {"scan": 25205952, "residues": 440532608, "gemm": 560699136, "crt_finish": 121983360},
 }
 
 
