@@ -1155,9 +1155,10 @@ __device__ __forceinline__ void crt_group_small(const uint32_t* y, uint64_t (&ac
   for (int w = 0; w < 7; ++w) acc[w] -= crt_group_bias<NQ>(w);
 }
 
+template <bool resident>
 __global__ void __launch_bounds__(kCmThreads, 1)
     k_crt_mm(const __grid_constant__ DevTables T, const int4* __restrict__ tiles, int ntiles, uint32_t stage_bytes,
-             int stages, int resident) {
+             int stages) {
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -1589,9 +1590,11 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
   const int smem = crt_mm_smem_bytes(cw_max, t.lmax, &stages);
   if (smem < 0) return cudaErrorInvalidValue;
   const int g = ntiles < grid ? ntiles : grid;
-  const int resident = blocks_one > 0 && blocks_one <= stages ? 1 : 0;
-  k_crt_mm<<<g, kCmThreads, smem, s>>>(t, reinterpret_cast<const int4*>(tiles), ntiles, (uint32_t)cw_max * 128u,
-                                       stages, resident);
+  const int4* tl = reinterpret_cast<const int4*>(tiles);
+  if (blocks_one > 0 && blocks_one <= stages)
+    k_crt_mm<true><<<g, kCmThreads, smem, s>>>(t, tl, ntiles, (uint32_t)cw_max * 128u, stages);
+  else
+    k_crt_mm<false><<<g, kCmThreads, smem, s>>>(t, tl, ntiles, (uint32_t)cw_max * 128u, stages);
   return cudaGetLastError();
 }
 
@@ -1624,7 +1627,9 @@ cudaError_t launch_crt_fin_short(const DevTables& t, int cls, const int32_t* blk
 }
 
 cudaError_t init_crt_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_crt_mm, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_crt_mm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_crt_mm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_crt_fin_long, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess) e = crt1_attr<8>();
