@@ -203,6 +203,23 @@ def test_planes_streamed_in_modulus_groups(ozk):
     assert ozk.Plan([(200, 150, 300, 256), (64, 64, 64, 53)], plane_group=20).info["plane_groups"] == 1
 
 
+def test_automatic_groups_take_the_fewest_residue_chunks(ozk):
+    """Among the group boundaries that give the fewest groups within the plane
+    budget, the automatic split takes the one whose groups need the fewest
+    tensor-core residue chunks (96 table columns each at p = 2048): 4096^3
+    at p = 2048 splits its 54 one-limb and 275 two-limb moduli as 54 + 131
+    and 144 (447 + 432 planes, 4 + 3 chunks) rather than in equal halves
+    (441 + 438 planes, whose second group's 292 columns need a fourth chunk
+    of 4 columns)."""
+    inf = ozk.Plan((4096, 4096, 4096, 2048)).info
+    assert inf["plane_groups"] == 2 and inf["group_planes"] == 447
+    cols = [54 + 2 * 131, 2 * 144]
+    assert [-(-(-(-c // 16) * 16) // 96) for c in cols] == [4, 3]
+    assert 54 + 3 * 131 == 447 and 3 * 144 == 432 and 447 + 432 == 879
+    # an explicit group size keeps the smallest cap that gives the count
+    assert ozk.Plan((4096, 4096, 4096, 2048), plane_group=441).info["group_planes"] == 441
+
+
 def test_plane_group_option_errors(ozk):
     for bad in (-2, 1, 2):
         with pytest.raises(ozk.OzakiError) as ei:
