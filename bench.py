@@ -245,7 +245,7 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # one pass, the full size); the source summaries are under profiles/.  A
 # kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_4096_p2048": {"scan": 403867776, "residues": 82299521856, "gemm": 121764652672,
+    "gemm_4096_p2048": {"scan": 403867776, "gemm": 121764652672,
                         "crt_sums": 23147779392, "crt_finish": 19971525760},
     "gemm_1024_p256": {"scan": 25205376, "residues": 440525568, "gemm": 562085952,
                        "crt_sums": 222810624, "crt_finish": 122014912},

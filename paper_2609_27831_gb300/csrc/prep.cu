@@ -718,9 +718,20 @@ struct RmLayout {
   }
 };
 
-// bf16 bits of an integer 0 <= x < 256 (exact): 2^23 + x has x in its low mantissa bits
-__device__ __forceinline__ uint32_t bf16_byte(uint32_t x) {
-  return __float_as_uint(__uint_as_float(0x4B000000u | x) - 8388608.0f) >> 16;
+// The four bytes b_i of x with the element's sign s as bf16 pairs
+// {s b0, s b1}, {s b2, s b3} (low half first).  kb is the fp32 s 2^23
+// (0x4B000000 or 0xCB000000): the byte permute puts b_i into its low mantissa
+// bits, giving s (2^23 + b_i), and subtracting kb leaves s b_i exactly (+0
+// for b_i = 0); a byte has at most 8 significant bits, so the top half of its
+// fp32 value is that value in bf16.
+__device__ __forceinline__ void signed_bf16_bytes(uint32_t x, uint32_t kb, uint32_t& c01, uint32_t& c23) {
+  const float k = __uint_as_float(kb);
+  const uint32_t f0 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7540)) - k);
+  const uint32_t f1 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7541)) - k);
+  const uint32_t f2 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7542)) - k);
+  const uint32_t f3 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7543)) - k);
+  c01 = __byte_perm(f0, f1, 0x7632);
+  c23 = __byte_perm(f2, f3, 0x7632);
 }
 
 // Centered residue of an exact fp32 integer y (|y| < 2^24): y - q m with q the
@@ -905,8 +916,9 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     // once: the exponents first, then one batch with the limbs of the first
     // 32 columns and the two below them (the round bit and the first sticky
     // limbs), before the wait for the buffer.  The element's sign goes onto the
-    // bf16 bytes (-0 for a zero byte is harmless: the epilogue's + 0.0f turns a
-    // -0 result into +0).  Group bg takes the tiles t with t & 1 == bg.
+    // bf16 bytes (a zero byte stays +0; a sum can still be -0, which the
+    // epilogue's + 0.0f turns into +0).  Group bg takes the tiles t with
+    // t & 1 == bg.
     const int bg = (warp - 2) >> 2;
     const int quad = warp & 3;
     const int row = quad * 32 + lane;
@@ -954,7 +966,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       uint64_t sticky = (srb & ((1ull << (rbpos & 63)) - 1ull)) | (rb_hi ? lm0[1] : 0ull) | lm0[0];
       for (int j = lq - 3; j >= 1 && !sticky; --j) sticky |= S(j);
       uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(lm0[2] >> (Bb & 63)) & 1u))) : 0u;
-      const uint32_t sgn = neg ? 0x80008000u : 0u;
+      const uint32_t kb = neg ? 0xCB000000u : 0x4B000000u;   // -2^23 or 2^23 as fp32
       if (ause > 0 && ok) ok = mbar_wait(a_free + ab, (uint32_t)((ause - 1) & 1), abort_flag, T.status, T.spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
@@ -982,8 +994,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           const uint64_t y = (uint64_t)__funnelshift_r(word(w), word(w + 1), bs) + carry;
           const uint32_t x = nz ? (uint32_t)y : 0u;
           carry = (uint32_t)(y >> 32);
-          col[2 * w] = (bf16_byte(x & 0xffu) | (bf16_byte((x >> 8) & 0xffu) << 16)) | sgn;
-          col[2 * w + 1] = (bf16_byte((x >> 16) & 0xffu) | (bf16_byte(x >> 24) << 16)) | sgn;
+          signed_bf16_bytes(x, kb, col[2 * w], col[2 * w + 1]);
         }
         tmem_st32(abase + c0, col);
       }

@@ -95,3 +95,49 @@ def test_balanced_split_by_shifted_rounding():
     lo = r - 128 * hi
     assert lo.min() == -63 and lo.max() == 64
     assert np.array_equal(lo + 128 * hi, r)
+
+
+def _byte_perm(x, y, sel):
+    """Byte permute: result byte n is byte (sel >> 4 n) & 7 of the pair
+    (x low, y high), as the CUDA byte-permute intrinsic defines it."""
+    src = [(x >> (8 * i)) & 0xFF for i in range(4)] + [(y >> (8 * i)) & 0xFF for i in range(4)]
+    return sum(src[(sel >> (4 * n)) & 7] << (8 * n) for n in range(4))
+
+
+def _f32(bits):
+    return np.array([bits], dtype=np.uint32).view(np.float32)[0]
+
+
+def _bits(f):
+    return int(np.array([f], dtype=np.float32).view(np.uint32)[0])
+
+
+def test_signed_bf16_bytes_of_the_residue_builder():
+    """The tensor-core residue kernel turns byte b of an integer with sign s
+    into bf16 s b: the byte permute gives the fp32 s (2^23 + b), subtracting
+    s 2^23 leaves s b exactly (+0 for b = 0), and the top half of its bits is
+    the bf16 value (low half zero).  Checked for every byte position, byte and
+    sign, against bf16 bits derived independently from the value."""
+    def bf16_of(v):                       # sign, 8-bit exponent, 7 mantissa bits
+        if v == 0:
+            return 0
+        sgn = 0x8000 if v < 0 else 0
+        a = abs(v)
+        e = a.bit_length() - 1
+        assert a == (a >> max(e - 7, 0)) << max(e - 7, 0)     # <= 8 significant bits
+        man = ((a << 7) >> e) & 0x7F
+        return sgn | ((127 + e) << 7) | man
+    for kb, s in ((0x4B000000, 1), (0xCB000000, -1)):
+        k = _f32(kb)
+        for pos, sel in enumerate((0x7540, 0x7541, 0x7542, 0x7543)):
+            for b in range(256):
+                x = (b << (8 * pos)) | (0xA5 << (8 * ((pos + 1) % 4)))   # other bytes ignored
+                f = np.float32(_f32(_byte_perm(x, kb, sel)) - k)
+                fb = _bits(f)
+                assert float(f) == s * b
+                if b == 0:
+                    assert fb == 0                                   # +0, never -0
+                assert fb & 0xFFFF == 0 and fb >> 16 == bf16_of(s * b)
+    # the pair packing takes the top halves: {f0 >> 16, f1 >> 16}
+    f0, f1 = _bits(np.float32(-3.0)), _bits(np.float32(200.0))
+    assert _byte_perm(f0, f1, 0x7632) == (f0 >> 16) | (f1 & 0xFFFF0000)
