@@ -28,6 +28,19 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Row and column of output idx = row N + col: a 32-bit division while idx
+// fits in 32 bits (N is a positive 32-bit count), the 64-bit one beyond.
+__device__ __forceinline__ void out_row_col(const ProbDev& P, int64_t idx, int64_t& row, int64_t& col) {
+  if (((uint64_t)idx >> 32) == 0u) {
+    const uint32_t n = (uint32_t)P.N, r = (uint32_t)idx / n;
+    row = r;
+    col = (uint32_t)idx - r * n;
+  } else {
+    row = idx / P.N;
+    col = idx - row * P.N;
+  }
+}
+
 // two small non-negative integers (<= 256) as a packed bf16 pair (low, high)
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) {
   return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
@@ -163,8 +176,8 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
 #pragma unroll
   for (int i = 0; i < DPL; ++i) mag[i] = neg ? R2[i] : R[i];
 
-  const int64_t row = valid ? idx / P.N : 0;
-  const int64_t col = valid ? idx - row * P.N : 0;
+  int64_t row = 0, col = 0;
+  if (valid) out_row_col(P, idx, row, col);
   if (P.dbg_chat != nullptr && valid) {
     uint32_t* dst = P.dbg_chat + idx * (int64_t)(D + 1);
     if (lam == 0) dst[0] = neg;
@@ -277,7 +290,8 @@ __global__ void __launch_bounds__(256) k_crt(DevTables T, const int4* __restrict
 // e_i + f_j of output idx (row i, column j), loaded where a kernel starts so
 // that the rounding does not wait for it
 __device__ __forceinline__ int crt_ef(const ProbDev& P, int64_t idx) {
-  const int64_t row = idx / P.N, col = idx - row * P.N;
+  int64_t row, col;
+  out_row_col(P, idx, row, col);
   return __ldg(P.e + row) + __ldg(P.f + col);
 }
 
@@ -291,7 +305,8 @@ __device__ __forceinline__ int crt_ef(const ProbDev& P, int64_t idx) {
 __device__ __forceinline__ void crt_round_write(const ProbDev& P, const uint32_t* s_mag, int ldm, int e, int nd,
                                              int top, bool neg, int64_t idx, int ef, int wbase = 0,
                                              uint32_t sticky_below = 0u) {
-  const int64_t row = idx / P.N, col = idx - row * P.N;
+  int64_t row, col;
+  out_row_col(P, idx, row, col);
   auto mag_word = [&](int w) -> uint32_t {
     return (w >= wbase && w < wbase + nd) ? s_mag[(w - wbase) * ldm + e] : 0u;
   };
