@@ -242,13 +242,14 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # DRAM traffic of each stage per execute (dram__bytes_read.sum +
 # dram__bytes_write.sum over the stage's launches, averaged over the four
 # executes of one ncu capture of the committed kernels on the same workload,
-# one pass, the full size); the source summaries are under profiles/.  A
-# kernel changed since its capture is absent.
+# one pass, the full size; the finish at 1024^3, p = 256 from its own
+# capture of one launch after its last change); the source summaries are
+# under profiles/.  A kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_4096_p2048": {"scan": 403867776, "gemm": 121764652672,
-                        "crt_sums": 23147779392, "crt_finish": 19971525760},
+    "gemm_4096_p2048": {"scan": 403876480, "residues": 82625082752, "gemm": 121762978816,
+                        "crt_sums": 23148609216, "crt_finish": 19631553472},
     "gemm_1024_p256": {"scan": 25205376, "residues": 440525568, "gemm": 562085952,
-                       "crt_sums": 222810624, "crt_finish": 122014912},
+                       "crt_sums": 222810624, "crt_finish": 125142528},
 }
 
 
