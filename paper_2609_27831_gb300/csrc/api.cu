@@ -341,7 +341,7 @@ static int modulus_prefix(int64_t inner, int t, int force_L, Big* P) {
   return big_cmp(*P, bound) <= 0 ? -1 : L;
 }
 
-// Tensor-core residue table [rows][kpad] (bf16 bits) of the moduli
+// Tensor-core residue table [rows][kpad] (f16 bits) of the moduli
 // l0 .. l0 + L - 1 of the list (L1 of them one-limb): row l (one-limb) =
 // cen(2^(8 b) mod m), rows L1 + 2 (l - L1) + {0, 1} (two-limb) = the balanced
 // base-128 halves of cen(2^(8 b) mod m).  Shared by problems and modulus
@@ -354,11 +354,13 @@ static int res_table_key(ozaki2_plan_s* pl, int l0, int L, int L1, int nb, int k
   ResTable rt;
   rt.l0 = l0; rt.L = L; rt.kpad = kpad; rt.npad = npad; rt.rows = rows;
   rt.bits.assign((size_t)rows * kpad, 0);
-  auto bf = [](int x) -> uint16_t {   // exact for |x| <= 256
-    float f = (float)x;
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return (uint16_t)(u >> 16);
+  auto bf = [](int x) -> uint16_t {   // f16 bits of an integer |x| <= 2048 (exact)
+    if (x == 0) return 0;
+    const uint16_t sgn = x < 0 ? 0x8000u : 0u;
+    const uint32_t a = (uint32_t)(x < 0 ? -x : x);
+    int e = 0;
+    while ((a >> (e + 1)) != 0u) ++e;           // a in [2^e, 2^(e+1))
+    return (uint16_t)(sgn | (uint32_t)(e + 15) << 10 | ((a << (10 - e)) & 0x3FFu));
   };
   const auto& mlist = modulus_list();
   for (int l = 0; l < L; ++l) {
@@ -1374,7 +1376,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
       const cuuint64_t strides[1] = {(cuuint64_t)h.res_kpad * 2};
       const cuuint32_t box[2] = {64u, (cuuint32_t)(h.res_mode == 1 ? h.res_npad : h.res_cw)};
       const cuuint32_t es[2] = {1u, 1u};
-      if (get_encode()(&tm[4 * count + i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.res_tab[i], dims, strides,
+      if (get_encode()(&tm[4 * count + i], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, pl->dev.res_tab[i], dims, strides,
                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return OZ2_ECUDA;
@@ -1448,7 +1450,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
         const cuuint64_t strides[1] = {(cuuint64_t)h.res_kpad * 2};
         const cuuint32_t box[2] = {64u, (cuuint32_t)(h.res_mode == 1 ? gr.res_npad : gr.res_cw)};
         const cuuint32_t es[2] = {1u, 1u};
-        if (get_encode()(&gm[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, pl->dev.groups[g].res_tab, dims, strides,
+        if (get_encode()(&gm[4], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, pl->dev.groups[g].res_tab, dims, strides,
                          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
           return OZ2_ECUDA;

@@ -91,8 +91,14 @@ __device__ __forceinline__ void st_plane(uint16_t* p, uint32_t bits) { __stcg(re
 __device__ __forceinline__ void st_plane2(uint16_t* p, uint32_t v) { __stcg(reinterpret_cast<unsigned int*>(p), v); }
 __device__ __forceinline__ void st_plane4(uint16_t* p, uint2 v) { __stcg(reinterpret_cast<uint2*>(p), v); }
 
-__device__ __forceinline__ uint32_t bf16_pair_u(uint32_t lo, uint32_t hi) {   // two ints <= 256
-  return (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
+// Bytes b0, b1 (sel 0x5140) or b2, b3 (sel 0x7362) of x as an f16 pair (low
+// half first): the byte permute puts each byte under the f16 exponent bits of
+// 2^10 (0x64), where the mantissa's unit is 1, giving 1024 + b exactly; one
+// packed subtraction of 1024 leaves b.
+__device__ __forceinline__ uint32_t f16_byte_pair(uint32_t x, uint32_t sel) {
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(__byte_perm(x, 0x64646464u, sel)), "r"(0x64006400u));
+  return r;
 }
 
 __device__ __forceinline__ uint32_t bf16_bits(int r) {
@@ -413,7 +419,10 @@ __global__ void __launch_bounds__(256) k_residue(DevTables T, const int4* __rest
 //   Y[e][j] = sum_b beta_b T[j][b]   ==  |a_hat| (mod m_l)  (or its halves),
 // one GEMM per tile of 128 elements with K = bytes of a (t+1)-bit integer.
 // Products are below 2^15 and sums below 2^15 * K < 2^24 for K < 512 bytes,
-// so bf16 operands and the fp32 TMEM accumulator are exact.  The epilogue
+// so f16 operands (bytes and table entries are integers below 2^11) and the
+// fp32 TMEM accumulator are exact; f16 rather than bf16 because a byte
+// becomes an f16 with one byte permute and one packed subtraction per two.
+// The epilogue
 // reduces each column mod m (fp32 reciprocal + fma, exact), applies the sign,
 // centers, splits two-limb residues and writes the bf16 planes.
 //
@@ -636,8 +645,8 @@ __global__ void __launch_bounds__(kRtThreads, 2)
           x = (uint32_t)y;
           carry = (uint32_t)(y >> 32);
         }
-        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w, 128)) = bf16_pair_u(x & 0xffu, (x >> 8) & 0xffu);
-        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w + 2, 128)) = bf16_pair_u((x >> 16) & 0xffu, x >> 24);
+        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w, 128)) = f16_byte_pair(x, 0x5140u);
+        *reinterpret_cast<uint32_t*>(gA + tc::sw128_offset(t, 4 * w + 2, 128)) = f16_byte_pair(x, 0x7362u);
       }
       s_neg[b * 128 + t] = nz ? flag : 2;
     }
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(kRtThreads, 2)
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      const uint32_t idesc = idesc_bf16(128, P.res_npad);
+      const uint32_t idesc = idesc_f16(128, P.res_npad);      // f16 bytes and f16 table
       const uint32_t tb = (uint32_t)P.res_npad * 128;
       const uint32_t d = tmem + (uint32_t)(b * tcols);
       for (int q = 0; q < P.res_kpad / 64; ++q) {
@@ -681,7 +690,7 @@ __global__ void __launch_bounds__(kRtThreads, 2)
 // every sum below 2^24.  Per tile of 4 lines x 32 consecutive k (128
 // elements; TMEM lane e is line e / 32, k e % 32: 32-byte runs on both sides
 // for the limb reads and the plane writes) the bytes live in tensor memory as
-// the A operand (two bf16 bytes per 32-bit column, two buffers), the table
+// the A operand (two f16 bytes per 32-bit column, two or four buffers), the table
 // streams through a shared-memory ring as B in blocks of 64 bytes x cw
 // columns, and Y runs in chunks of cw columns through two accumulator slots:
 //   [A0 .. A(nabuf-1): kpad/2 each][slot 0: cw][slot 1: cw]  <= 512 TMEM columns
@@ -718,20 +727,15 @@ struct RmLayout {
   }
 };
 
-// The four bytes b_i of x with the element's sign s as bf16 pairs
-// {s b0, s b1}, {s b2, s b3} (low half first).  kb is the fp32 s 2^23
-// (0x4B000000 or 0xCB000000): the byte permute puts b_i into its low mantissa
-// bits, giving s (2^23 + b_i), and subtracting kb leaves s b_i exactly (+0
-// for b_i = 0); a byte has at most 8 significant bits, so the top half of its
-// fp32 value is that value in bf16.
-__device__ __forceinline__ void signed_bf16_bytes(uint32_t x, uint32_t kb, uint32_t& c01, uint32_t& c23) {
-  const float k = __uint_as_float(kb);
-  const uint32_t f0 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7540)) - k);
-  const uint32_t f1 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7541)) - k);
-  const uint32_t f2 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7542)) - k);
-  const uint32_t f3 = __float_as_uint(__uint_as_float(__byte_perm(x, kb, 0x7543)) - k);
-  c01 = __byte_perm(f0, f1, 0x7632);
-  c23 = __byte_perm(f2, f3, 0x7632);
+// The four bytes b_i of x times the element's sign s as f16 pairs
+// {s b0, s b1}, {s b2, s b3} (low half first): the byte permute makes the
+// pair {1024 + b0, 1024 + b1} (each byte under the f16 exponent bits of 2^10,
+// where the mantissa's unit is 1), and one packed fma with s2 = {s, s} and
+// c2 = {-1024 s, -1024 s} leaves s b_i exactly (every value involved is an
+// integer below 2^11; +0 for b_i = 0).
+__device__ __forceinline__ void signed_f16_bytes(uint32_t x, uint32_t s2, uint32_t c2, uint32_t& c01, uint32_t& c23) {
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(c01) : "r"(__byte_perm(x, 0x64646464u, 0x5140)), "r"(s2), "r"(c2));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(c23) : "r"(__byte_perm(x, 0x64646464u, 0x7362)), "r"(s2), "r"(c2));
 }
 
 // Centered residue of an exact fp32 integer y (|y| < 2^24): y - q m with q the
@@ -884,7 +888,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           }
           tc_fence_after();
           const int ncol = min(cw, npad - c * cw);             // a multiple of 16
-          const uint32_t idesc = idesc_bf16(128, ncol);
+          const uint32_t idesc = idesc_f16(128, ncol);             // f16 bytes and f16 table
           const uint32_t d = tmem + (uint32_t)nabuf * acols + (uint32_t)(s * cw);
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(full + st, ph, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
@@ -916,7 +920,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
     // once: the exponents first, then one batch with the limbs of the first
     // 32 columns and the two below them (the round bit and the first sticky
     // limbs), before the wait for the buffer.  The element's sign goes onto the
-    // bf16 bytes (a zero byte stays +0; a sum can still be -0, which the
+    // f16 bytes (a zero byte stays +0; a sum can still be -0, which the
     // epilogue's + 0.0f turns into +0).  Group bg takes the tiles t with
     // t & 1 == bg.
     const int bg = (warp - 2) >> 2;
@@ -966,7 +970,8 @@ __global__ void __launch_bounds__(kRmThreads, 1)
       uint64_t sticky = (srb & ((1ull << (rbpos & 63)) - 1ull)) | (rb_hi ? lm0[1] : 0ull) | lm0[0];
       for (int j = lq - 3; j >= 1 && !sticky; --j) sticky |= S(j);
       uint32_t carry = nz ? (rb & ((sticky != 0ull) | ((uint32_t)(lm0[2] >> (Bb & 63)) & 1u))) : 0u;
-      const uint32_t kb = neg ? 0xCB000000u : 0x4B000000u;   // -2^23 or 2^23 as fp32
+      const uint32_t s2 = neg ? 0xBC00BC00u : 0x3C003C00u;   // {s, s} in f16
+      const uint32_t c2 = neg ? 0x64006400u : 0xE400E400u;   // {-1024 s, -1024 s}
       if (ause > 0 && ok) ok = mbar_wait(a_free + ab, (uint32_t)((ause - 1) & 1), abort_flag, T.status, T.spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
@@ -994,7 +999,7 @@ __global__ void __launch_bounds__(kRmThreads, 1)
           const uint64_t y = (uint64_t)__funnelshift_r(word(w), word(w + 1), bs) + carry;
           const uint32_t x = nz ? (uint32_t)y : 0u;
           carry = (uint32_t)(y >> 32);
-          signed_bf16_bytes(x, kb, col[2 * w], col[2 * w + 1]);
+          signed_f16_bytes(x, s2, c2, col[2 * w], col[2 * w + 1]);
         }
         tmem_st32(abase + c0, col);
       }

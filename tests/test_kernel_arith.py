@@ -104,40 +104,50 @@ def _byte_perm(x, y, sel):
     return sum(src[(sel >> (4 * n)) & 7] << (8 * n) for n in range(4))
 
 
-def _f32(bits):
-    return np.array([bits], dtype=np.uint32).view(np.float32)[0]
+def _f16_bits(v):
+    """f16 bits derived from the value alone (sign, 5-bit exponent with bias
+    15, 10 mantissa bits) for an integer |v| < 2^11."""
+    if v == 0:
+        return 0
+    sgn = 0x8000 if v < 0 else 0
+    a = abs(v)
+    e = a.bit_length() - 1
+    return sgn | ((15 + e) << 10) | (((a << 10) >> e) & 0x3FF)
 
 
-def _bits(f):
-    return int(np.array([f], dtype=np.float32).view(np.uint32)[0])
+def _f16(bits):
+    return np.array([bits], dtype=np.uint16).view(np.float16)[0]
 
 
-def test_signed_bf16_bytes_of_the_residue_builder():
-    """The tensor-core residue kernel turns byte b of an integer with sign s
-    into bf16 s b: the byte permute gives the fp32 s (2^23 + b), subtracting
-    s 2^23 leaves s b exactly (+0 for b = 0), and the top half of its bits is
-    the bf16 value (low half zero).  Checked for every byte position, byte and
-    sign, against bf16 bits derived independently from the value."""
-    def bf16_of(v):                       # sign, 8-bit exponent, 7 mantissa bits
-        if v == 0:
-            return 0
-        sgn = 0x8000 if v < 0 else 0
-        a = abs(v)
-        e = a.bit_length() - 1
-        assert a == (a >> max(e - 7, 0)) << max(e - 7, 0)     # <= 8 significant bits
-        man = ((a << 7) >> e) & 0x7F
-        return sgn | ((127 + e) << 7) | man
-    for kb, s in ((0x4B000000, 1), (0xCB000000, -1)):
-        k = _f32(kb)
-        for pos, sel in enumerate((0x7540, 0x7541, 0x7542, 0x7543)):
-            for b in range(256):
-                x = (b << (8 * pos)) | (0xA5 << (8 * ((pos + 1) % 4)))   # other bytes ignored
-                f = np.float32(_f32(_byte_perm(x, kb, sel)) - k)
-                fb = _bits(f)
-                assert float(f) == s * b
-                if b == 0:
-                    assert fb == 0                                   # +0, never -0
-                assert fb & 0xFFFF == 0 and fb >> 16 == bf16_of(s * b)
-    # the pair packing takes the top halves: {f0 >> 16, f1 >> 16}
-    f0, f1 = _bits(np.float32(-3.0)), _bits(np.float32(200.0))
-    assert _byte_perm(f0, f1, 0x7632) == (f0 >> 16) | (f1 & 0xFFFF0000)
+def _h2(word):
+    return _f16(word & 0xFFFF), _f16(word >> 16)
+
+
+def test_f16_bytes_of_the_tensor_core_residue_builders():
+    """Both tensor-core residue kernels feed the bytes of |a_hat| to the MMA
+    as f16.  The byte permute with 0x64646464 puts byte b under the exponent
+    bits of 2^10 (0x64xx is 1024 + b: the mantissa's unit is 1 there); then
+    the unsigned form subtracts 1024 (packed) and the signed form takes one
+    packed fma with {s, s} and {-1024 s, -1024 s}.  Every intermediate is an
+    integer below 2^11, so each step is exact in f16; checked for every byte,
+    byte position and sign against f16 bits derived from the value."""
+    for v in (1, 127, -64, 255, 1024, 1279, -1279):
+        assert float(_f16(_f16_bits(v))) == v                   # the bits rule itself
+    m1024 = _f16(0x6400)
+    assert float(_f16(0x3C00)) == 1.0 and float(m1024) == 1024.0
+    for sel, lo_pos in ((0x5140, 0), (0x7362, 2)):
+        for b in range(256):
+            for other in (0x00, 0xFF, 0x5A):
+                x = (b << (8 * lo_pos)) | (other << (8 * (lo_pos + 1)))
+                x |= 0xA5A50000 if lo_pos == 0 else 0x0000A5A5     # the bytes the selector skips
+                lo, hi = _h2(_byte_perm(x, 0x64646464, sel))
+                assert float(lo) == 1024 + b and float(hi) == 1024 + other
+                # unsigned: one packed subtraction of {1024, 1024}
+                u = (np.float16(lo - m1024), np.float16(hi - m1024))
+                assert [int(t.view(np.uint16)) for t in u] == [_f16_bits(b), _f16_bits(other)]
+                # signed: fma(p, s, -1024 s); the product and the sum are exact
+                for s2, c2, sg in ((0x3C003C00, 0xE400E400, 1), (0xBC00BC00, 0x64006400, -1)):
+                    s_lo, c_lo = _h2(s2)[0], _h2(c2)[0]
+                    assert float(s_lo) == sg and float(c_lo) == -1024 * sg
+                    r = np.float16(np.float16(lo * s_lo) + c_lo)
+                    assert int(r.view(np.uint16)) == _f16_bits(sg * b)   # +0, never -0, for b = 0
