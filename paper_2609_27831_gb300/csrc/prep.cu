@@ -1043,63 +1043,71 @@ __global__ void __launch_bounds__(kRmThreads, 1)
         // per tile), whatever the chunk width
         const int gfirst = ((sub - c * (cw >> 5) - tcount) % 3 + 3) % 3;
         for (int g = 32 * gfirst; g < ncolp; g += 96) {
-          // in pieces of 8 columns (a rolled loop: the epilogue's code stays
-          // small next to the builders' in the instruction cache); pieces
-          // hold whole pairs (L1 and every piece start are even)
+          // 16 columns per TMEM load, reduced as two pieces of 8 (a rolled
+          // loop: the epilogue's code stays small next to the builders' in
+          // the instruction cache); pieces hold whole pairs (L1 and every
+          // piece start are even)
           const int gcols = min(32, ncolp - g);           // 32 or 16
 #pragma unroll 1
-          for (int pc = 0; pc < gcols; pc += 8) {
-            uint32_t y[8];
-            tmem_ld8(trow + (uint32_t)(g + pc), y);
+          for (int pc2 = 0; pc2 < gcols; pc2 += 16) {
+            uint32_t y16[16];
+            tmem_ld16(trow + (uint32_t)(g + pc2), y16);
             if (!valid) continue;
-            const int c0 = j0 + g + pc;
-            if (c0 + 8 <= L1) {
-              // 8 one-limb moduli: planes c0 .. c0 + 7
-              uint16_t* dp = dst0 + (int64_t)c0 * pstride;
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const float4 mc = s_mc[c0 + q];
-                const float r = cmod_f32(__uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
-                *dp = (uint16_t)(__float_as_uint(r) >> 16);
-                dp += pstride;
-              }
-            } else if (c0 >= L1) {
-              // 4 two-limb pairs: moduli l = L1 + (c0 - L1) / 2 + i, planes L1 + 3 (l - L1) + {0, 1, 2}
-              const int lb = L1 + ((c0 - L1) >> 1);
-              uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (lb - L1)) * pstride;
+            for (int hh = 0; hh < 2; ++hh) {
+              const int pc = pc2 + 8 * hh;
+              uint32_t y[8];
 #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                if (c0 + 2 * i < ncols) {
-                  const float4 mc = s_mc[lb + i];
-                  // x is +0 for a zero residue; then lo, hi and lo + hi are never -0
-                  const float x = cmod2_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y);
-                  float lo, hi;
-                  split128(x, lo, hi);
-                  dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
-                  dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
-                  dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
-                }
-                dp += 3 * pstride;
-              }
-            } else {
-              // the piece that holds the last one-limb moduli and the first pairs
+              for (int q = 0; q < 8; ++q) y[q] = y16[8 * hh + q];
+              const int c0 = j0 + g + pc;
+              if (c0 + 8 <= L1) {
+                // 8 one-limb moduli: planes c0 .. c0 + 7
+                uint16_t* dp = dst0 + (int64_t)c0 * pstride;
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const int colx = c0 + q;
-                if (colx < L1) {
-                  const float4 mc = s_mc[colx];
+                for (int q = 0; q < 8; ++q) {
+                  const float4 mc = s_mc[c0 + q];
                   const float r = cmod_f32(__uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
-                  dst0[(int64_t)colx * pstride] = (uint16_t)(__float_as_uint(r) >> 16);
-                } else if ((q & 1) == 0 && colx < ncols) {   // a pair starts at an even column
-                  const int l = L1 + ((colx - L1) >> 1);
-                  const float4 mc = s_mc[l];
-                  const float x = cmod2_f32(y[q], y[q + 1], mc.x, mc.y);
-                  float lo, hi;
-                  split128(x, lo, hi);
-                  uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (l - L1)) * pstride;
-                  dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
-                  dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
-                  dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
+                  *dp = (uint16_t)(__float_as_uint(r) >> 16);
+                  dp += pstride;
+                }
+              } else if (c0 >= L1) {
+                // 4 two-limb pairs: moduli l = L1 + (c0 - L1) / 2 + i, planes L1 + 3 (l - L1) + {0, 1, 2}
+                const int lb = L1 + ((c0 - L1) >> 1);
+                uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (lb - L1)) * pstride;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  if (c0 + 2 * i < ncols) {
+                    const float4 mc = s_mc[lb + i];
+                    // x is +0 for a zero residue; then lo, hi and lo + hi are never -0
+                    const float x = cmod2_f32(y[2 * i], y[2 * i + 1], mc.x, mc.y);
+                    float lo, hi;
+                    split128(x, lo, hi);
+                    dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
+                    dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
+                    dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
+                  }
+                  dp += 3 * pstride;
+                }
+              } else {
+                // the piece that holds the last one-limb moduli and the first pairs
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const int colx = c0 + q;
+                  if (colx < L1) {
+                    const float4 mc = s_mc[colx];
+                    const float r = cmod_f32(__uint_as_float(y[q]), mc.x, mc.y, mc.z) + 0.0f;
+                    dst0[(int64_t)colx * pstride] = (uint16_t)(__float_as_uint(r) >> 16);
+                  } else if ((q & 1) == 0 && colx < ncols) {   // a pair starts at an even column
+                    const int l = L1 + ((colx - L1) >> 1);
+                    const float4 mc = s_mc[l];
+                    const float x = cmod2_f32(y[q], y[q + 1], mc.x, mc.y);
+                    float lo, hi;
+                    split128(x, lo, hi);
+                    uint16_t* dp = dst0 + (int64_t)(L1 + 3 * (l - L1)) * pstride;
+                    dp[0] = (uint16_t)(__float_as_uint(lo) >> 16);
+                    dp[pstride] = (uint16_t)(__float_as_uint(hi) >> 16);
+                    dp[2 * pstride] = (uint16_t)(__float_as_uint(lo + hi) >> 16);
+                  }
                 }
               }
             }
