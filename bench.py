@@ -312,7 +312,7 @@ def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False)
     if info.get("res_mode") == 2:
         # the byte products on the tensor cores: 2 flops per byte multiply-add
         ach = 2.0 * res_macs / (stages["residues"] / 1e3) / 1e12
-        out["residues"] = {"kernel": "k_residue_mm (integerize + residues as an exact bf16 byte GEMM)",
+        out["residues"] = {"kernel": "k_residue_mm (integerize + residues as an exact f16 byte GEMM, kind::f16 rate)",
                            "bound": "tensor", "achieved": round(ach, 1), "peak": tpk, "unit": "TFLOP/s",
                            "frac": round(ach / tpk, 4), "peak_source": tsrc, "traffic": traffic.get("residues")}
     else:
