@@ -455,6 +455,32 @@ def measure_single(g: Gpu, ozk, name: str, steps: int, warmup: int, world: int =
     return res
 
 
+def host_link_rates(torch, dev, stream, nbytes: int = 1 << 30, reps: int = 3):
+    """This box's pinned host <-> device copy rates (GB/s, best of a few
+    copies of one buffer each way, CUDA events on the copy stream), reported
+    beside the end-to-end figure, which they bound from below."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name in ("h2d", "d2h"):
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                if name == "h2d":
+                    d.copy_(h, non_blocking=True)
+                else:
+                    h.copy_(d, non_blocking=True)
+                e1.record(stream)
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        out[name] = round(best, 1)
+    out["how"] = "one 1 GiB pinned buffer each way, best of 3 copies"
+    del h, d
+    return out
+
+
 def measure_e2e(g: Gpu, ozk, plan, A, B, bufs, ws, steps, world, barrier):
     """End to end through the C ABI: pinned host inputs copied in and the
     result copied out every step, double-buffered on two copy streams so that
@@ -505,6 +531,7 @@ def measure_e2e(g: Gpu, ozk, plan, A, B, bufs, ws, steps, world, barrier):
                 hC[b][k].copy_(getattr(bufC[b], k), non_blocking=True)
             ev_out[b].record(s_out)
 
+    link = host_link_rates(torch, dev, s_in)
     barrier()
     torch.cuda.synchronize()
     t0.record(s_in)
@@ -528,7 +555,8 @@ def measure_e2e(g: Gpu, ozk, plan, A, B, bufs, ws, steps, world, barrier):
     work = 2.0 * M * N * dA.shape[1]
     return {"value": replica_value(world, work, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "copies": "pinned host buffers, every step, double-buffered on two copy streams"}
+            "copies": "pinned host buffers, every step, double-buffered on two copy streams",
+            "host_link_gbs": link}
 
 
 def measure_batched(g: Gpu, ozk, steps: int = 5, warmup: int = 3, tune: bool = True):
