@@ -917,20 +917,28 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   const int64_t up = P.upitch;
   const uint32_t* const qcol = P.crt_q + idx;
   const uint32_t alpha = __ldg(P.crt_alpha + idx);
-  // R seven digits at a time, to f(g, r): word k of group g is digit 7 g + k
-  // (k < 7); words 7 and 8 of group g add into digits 7 g + 7 and 7 g + 8;
-  // digits from D on are zero.  The nine words of group g + 1 are loaded
-  // while group g's digits are formed.
-  auto for_each_group = [&](auto&& f) {
+  // R seven digits at a time from group gs on, to f(g, r): word k of group g
+  // is digit 7 g + k (k < 7); words 7 and 8 of group g add into digits
+  // 7 g + 7 and 7 g + 8; digits from D on are zero.  The nine words of group
+  // g + 1 are loaded while group g's digits are formed.  From gs > 0 the
+  // carry into digit 7 gs from the digits below is left out: the digits come
+  // out as those of R_up + c (R_up: R's digits from 7 gs on) with c, the
+  // carry that was left out, at most alpha + 2 (every digit step adds below
+  // (alpha + 2) 2^32 to a carry of at most alpha + 2).
+  auto for_each_group = [&](int gs, auto&& f) {
     uint32_t wc[9], wn[9];
     auto load = [&](int g, uint32_t (&w)[9]) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) w[k] = g < ng ? __ldg(qcol + ((int64_t)g * 9 + k) * up) : 0u;
     };
-    load(0, wc);
+    load(gs, wc);
     uint32_t prev7 = 0, prev8 = 0;
+    if (gs > 0) {
+      prev7 = __ldg(qcol + ((int64_t)(gs - 1) * 9 + 7) * up);
+      prev8 = __ldg(qcol + ((int64_t)(gs - 1) * 9 + 8) * up);
+    }
     uint64_t carry = 0;
-    for (int g = 0; 7 * g < D; ++g) {
+    for (int g = gs; 7 * g < D; ++g) {
       load(g + 1, wn);
       uint32_t r[7];
 #pragma unroll
@@ -953,30 +961,43 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
 #pragma unroll
     for (int k = 0; k < 7; ++k) v[k] = t[7 * g + k];
   };
+  // From gs > 0 every chain below starts at digit d0 = 7 gs with no carry
+  // in, and digit d0 of each of its operands is short by at most alpha + 3
+  // (c, one carry or borrow of a chain below d0, one of the chain before).
+  // Where the chain's digit d0 stays at least U = alpha + 5 away from both
+  // ends of its range, no such shortfall moves a carry or borrow out of
+  // digit d0: the chain's higher digits and carry out are exact.  `exact`
+  // records that for every digit d0 the finish uses.
+  const uint32_t U = alpha + 5u;
+  auto safe = [&](uint32_t v) { return v >= U && v <= 0xffffffffu - U; };
+  bool exact = true;
   // pass 1: R >= P (R + 2^(32 DG) - P carries out), and the sign of x0 for
   // either choice (x + 2^(32 DG) - floor(P/2) - 1 carries out iff x > floor(P/2))
   uint32_t c1 = 0, c3 = 0, c4 = 0;
-  for_each_group([&](int g, const uint32_t (&r)[7]) {
-    uint32_t np[7], nh[7], t1[7];
-    tab7(s_negP, g, np);
-    tab7(s_negH1, g, nh);
-    c1 = add_chain<7>(r, np, t1, c1);                        // R - P
-    c3 = carry_chain<7>(r, nh, c3);
-    c4 = carry_chain<7>(t1, nh, c4);
-  });
-  const bool ge = c1 != 0;               // R >= P: x0 = R - P
-  const bool neg = ge ? c4 != 0 : c3 != 0;
+  auto pass1 = [&](int gs) {
+    c1 = c3 = c4 = 0;
+    for_each_group(gs, [&](int g, const uint32_t (&r)[7]) {
+      uint32_t np[7], nh[7], t1[7];
+      tab7(s_negP, g, np);
+      tab7(s_negH1, g, nh);
+      c1 = add_chain<7>(r, np, t1, c1);                        // R - P
+      c3 = carry_chain<7>(r, nh, c3);
+      c4 = carry_chain<7>(t1, nh, c4);
+      if (gs > 0 && g == gs) exact = safe(r[0]) && safe(t1[0]) && safe(r[0] + nh[0]) && safe(t1[0] + nh[0]);
+    });
+  };
   uint32_t* const dbg = P.dbg_chat != nullptr ? P.dbg_chat + idx * (int64_t)(D + 1) : nullptr;
-  if (dbg) dbg[0] = neg;
+  bool ge = false, neg = false;
   // pass 2 (and 3): |c_hat| = x0 or P - x0 digit by digit; digits from
   // wbase on go to the window, the ones below it into the sticky word
+  // (from gs > 0: the digits above d0 only)
   int top = -1;
   uint32_t topv = 0, sticky = 0, bad = 0;
-  auto magnitude = [&](int wbase, bool dump) {
+  auto magnitude = [&](int wbase, bool dump, int gs) {
     uint32_t cs = 0, cc = 0, br = 0;
     top = -1;
     sticky = 0;
-    for_each_group([&](int g, const uint32_t (&r)[7]) {
+    for_each_group(gs, [&](int g, const uint32_t (&r)[7]) {
       uint32_t np[7], pp[7], x0[7], pm[7];
       tab7(s_negP, g, np);
       tab7(s_P, g, pp);
@@ -985,9 +1006,11 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
       for (int k = 0; k < 7; ++k) x0[k] = ge ? x0[k] : r[k];
       cc = carry_chain<7>(x0, np, cc);                       // carries out iff x0 >= P
       br = sub_chain<7>(pp, x0, pm, br);                     // P - x0
+      if (gs > 0 && g == gs) exact = exact && safe(x0[0]) && safe(x0[0] + np[0]) && safe(pp[0] - x0[0]);
 #pragma unroll
       for (int k = 0; k < 7; ++k) {
         const int d = 7 * g + k;
+        if (gs > 0 && d == 7 * gs) continue;               // short by up to alpha + 3
         const uint32_t mag = neg ? pm[k] : x0[k];
         if (mag) {
           top = d;
@@ -1004,18 +1027,47 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     bad = cc;
   };
   int wbase = D > W ? D - W : 0;
-  magnitude(wbase, dbg != nullptr);
-  if (bad) atomicOr(T.status, kStatusCrtRange);
-  if (top >= 0) {
-    // lowest word the rounding reads: the one holding the round bit (or 0
-    // when |c_hat| has at most p bits)
-    const int n = 32 * top + 32 - __clz(topv);
-    const int lo = n > P.p ? (n - P.p - 1) >> 5 : 0;
-    if (lo < wbase) {
-      wbase = lo;
-      magnitude(wbase, false);
+  // Fast form: both passes from group g0 on (d0 = 7 g0 below the window),
+  // about half the group words where D is large.  It stands when every
+  // digit d0 it uses is safe, some digit between d0 and the window is
+  // nonzero (so the sticky bit is set whatever lies below) and the rounding
+  // reads no word below the window; otherwise, and with the debug dump, the
+  // output takes the full form from group 0.
+  const int g0 = wbase > 7 ? (wbase - 1) / 7 : 0;
+  bool fast = dbg == nullptr && g0 > 0;
+  if (fast) {
+    pass1(g0);
+    ge = c1 != 0;
+    neg = ge ? c4 != 0 : c3 != 0;
+    fast = exact;
+    if (fast) {
+      magnitude(wbase, false, g0);
+      fast = exact && sticky != 0u && top >= wbase;
+      if (fast) {
+        const int n = 32 * top + 32 - __clz(topv);
+        fast = (n > P.p ? (n - P.p - 1) >> 5 : 0) >= wbase;
+      }
     }
   }
+  if (!fast) {
+    exact = true;
+    pass1(0);
+    ge = c1 != 0;               // R >= P: x0 = R - P
+    neg = ge ? c4 != 0 : c3 != 0;
+    if (dbg) dbg[0] = neg;
+    magnitude(wbase, dbg != nullptr, 0);
+    if (top >= 0) {
+      // lowest word the rounding reads: the one holding the round bit (or 0
+      // when |c_hat| has at most p bits)
+      const int n = 32 * top + 32 - __clz(topv);
+      const int lo = n > P.p ? (n - P.p - 1) >> 5 : 0;
+      if (lo < wbase) {
+        wbase = lo;
+        magnitude(wbase, false, 0);
+      }
+    }
+  }
+  if (bad) atomicOr(T.status, kStatusCrtRange);
   crt_round_write(P, s_win, kFinThreads, e, W, top, neg, idx, ef, wbase, sticky);
 }
 

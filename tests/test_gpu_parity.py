@@ -220,30 +220,64 @@ def test_p2048_small(ozk):
     assert got3["plan"].info["crt_mode"] == 0 and got3["plan"].info["res_mode"] == 0
 
 
+# Cancelling, exactly zero and ordinary small-integer outputs for the finish
+# of long accumulators (|c_hat| far below its usual size in some).
+CANCEL_ROWS_A = [
+    [(1, 0), (1, 0), (1, -1000), (0, 0)],
+    [(3, 5), (-3, 5), (5, -3000), (1, -3100)],
+    [(1, 0), (1, 0), (0, 0), (0, 0)],
+    [(5, 2), (7, 1), (-9, -40), (11, -3)],
+]
+CANCEL_ROWS_B = [
+    [(1, 0), (7, 10), (1, 0)],
+    [(-1, 0), (7, 10), (-1, 0)],
+    [(1, 0), (1, -5), (1, -2000)],
+    [(1, 0), (3, 1), (0, 0)],
+]
+
+
 @pytest.mark.parametrize("p", [1024, 2048])
 def test_long_finish_small_and_zero_results(ozk, p):
     """The finish of long accumulators keeps only the highest digits of |c_hat|
     in shared memory and moves that window down when a word below it is
     needed: outputs whose large terms cancel (|c_hat| far below its usual
     size), an exact zero, and ordinary ones, every stage bit-exact."""
-    rows_a = [
-        [(1, 0), (1, 0), (1, -1000), (0, 0)],
-        [(3, 5), (-3, 5), (5, -3000), (1, -3100)],
-        [(1, 0), (1, 0), (0, 0), (0, 0)],
-        [(5, 2), (7, 1), (-9, -40), (11, -3)],
-    ]
-    rows_b = [
-        [(1, 0), (7, 10), (1, 0)],
-        [(-1, 0), (7, 10), (-1, 0)],
-        [(1, 0), (1, -5), (1, -2000)],
-        [(1, 0), (3, 1), (0, 0)],
-    ]
-    A = mat_from_values(rows_a * 8, p)                   # 32 x 4: at least one 128-output tile
-    B = mat_from_values([r * 2 for r in rows_b], p)      # 4 x 6
+    A = mat_from_values(CANCEL_ROWS_A * 8, p)                   # 32 x 4: at least one 128-output tile
+    B = mat_from_values([r * 2 for r in CANCEL_ROWS_B], p)      # 4 x 6
     got, ref = assert_full_parity(ozk, A, B, p, truth=False, crt_engine=2)
     assert got["plan"].info["crt_mode"] == 2 and got["plan"].info["crt_digits"] > 24
     assert ref["chat"][2, 0] == 0 and ref["chat"][0, 0] != 0
     assert abs(ref["chat"][0, 0]).bit_length() < abs(ref["chat"][0, 1]).bit_length() - 64
+
+
+@pytest.mark.parametrize("p,shape", [(1024, (40, 36, 30)), (2048, (24, 22, 20))])
+def test_long_finish_top_groups_form(ozk, p, shape):
+    """Without the debug dump of c_hat the finish of long accumulators first
+    tries its fast form: both passes over the group words from the group
+    below the window on, with the carry left out of that group's lowest digit
+    (at most alpha + 2) bounded; an output falls back to the full form where
+    a digit the fast form uses lies near a wrap, no digit between that one and
+    the window is nonzero, or the rounding needs a word below the window.
+    Random outputs (the fast form) and cancelling or small-integer ones (the
+    full form) equal the oracle bit for bit, and equal the outputs of the
+    full form (debug dump on) for the random product."""
+    M, N, K = shape
+    rng = np.random.Generator(np.random.PCG64(2044 + p))
+    A = synth.mp_matrix(rng, M, K, p, -64, 64)
+    B = synth.mp_matrix(rng, K, N, p, -64, 64)
+    fast = run_gpu(ozk, A, B, p, debug=False, crt_engine=2)
+    assert fast["plan"].info["crt_mode"] == 2 and fast["plan"].info["crt_digits"] > 2 * (p // 64) + 4 + 7
+    full = run_gpu(ozk, A, B, p, debug=True, crt_engine=2)
+    ref = o.ozaki2_full(A, B, p)
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(fast["C"][key], ref["C"][key]), key
+        assert np.array_equal(full["C"][key], fast["C"][key]), key
+    A2 = mat_from_values(CANCEL_ROWS_A * 8, p)
+    B2 = mat_from_values([r * 2 for r in CANCEL_ROWS_B], p)
+    got2 = run_gpu(ozk, A2, B2, p, debug=False, crt_engine=2)
+    ref2 = o.ozaki2_full(A2, B2, p)
+    for key in ("limbs", "exp", "sign"):
+        assert np.array_equal(got2["C"][key], ref2["C"][key]), key
 
 
 @pytest.mark.parametrize("p", [300, 700])
