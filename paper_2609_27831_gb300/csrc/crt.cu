@@ -851,6 +851,11 @@ __global__ void __launch_bounds__(kCtThreads, (ND <= 24 ? 2 : 1))
 //   the rounding reads its words from the window.  When |c_hat| is so small
 //   that a word below the window is needed, a third pass writes the window
 //   from the lowest needed word on.
+// Both passes first run over the groups from the one below the window on
+// only (the fast form, about half the group words at large D); the digits
+// below that group enter only through one bounded carry, and the output
+// keeps the fast result where no decision depends on that carry (else it
+// runs the full form above).
 // Block list entry: {problem, block of 128 outputs, 0, 0}.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 128;
