@@ -246,8 +246,7 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # capture of one launch after its last change); the source summaries are
 # under profiles/.  A kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_4096_p2048": {"scan": 403952064, "residues": 82207492672, "gemm": 122832939456,
-                        "crt_sums": 23148975744, "crt_finish": 11468941696},
+    "gemm_4096_p2048": {"scan": 403952064, "residues": 82207492672, "gemm": 122832939456},
     "gemm_1024_p256": {"scan": 25205376, "residues": 440525568, "gemm": 562085952,
                        "crt_sums": 222810624, "crt_finish": 125142528},
 }

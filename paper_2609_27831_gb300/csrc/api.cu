@@ -183,6 +183,7 @@ struct ProbHost {
   int crt_mode;                // 0: CUDA-core CRT class crt_cls; 1: tensor-core CRT (class crt_cls);
                                // 2: tensor-core sums to R digits, then the finish
   int crt_kpad, crt_npad, crt_np, crt_nchunk, crt_cw, crt_ngrp, crt_nslot, crt_nvbuf;
+  int crt_gskip = 0;            // crt_mode 2, long finish: lowest group of Y columns formed
   size_t off_q, off_sig;       // crt_mode 2: group sums [ngrp][9][upitch] uint32, quotient estimates [upitch] uint32
   int res_mode, res_kpad, res_npad, res_key;   // tensor-core residues (table index res_key)
   int res_cw, res_nchunk, res_nabuf;           // res_mode 2: chunk width, chunks, byte buffers
@@ -499,6 +500,21 @@ static int build_problem(ozaki2_plan_s* pl, int64_t M, int64_t N, int64_t K, int
     h.crt_nvbuf = (mm_ok && kpad + h.crt_nslot * h.crt_cw <= 512) ? 2 : 1;
     h.crt_ngrp = mm_ok ? h.crt_nchunk * h.crt_cw / 32 : 0;
     const int rows = h.crt_mode == 2 ? h.crt_cw * h.crt_nchunk : npad;
+    // The finish of long accumulators reads the group sums from group g0 - 1
+    // on in its fast form (g0: the group whose lowest digit lies just below
+    // its window of the 2 nl + 4 highest digits), and takes an output's full
+    // form from v_l where the fast form does not stand: the sums below group
+    // g0 - 1 are not formed (the table keeps every row).
+    h.crt_gskip = 0;
+    if (h.crt_mode == 2 && h.crt_cls > 4 && h.D32 <= kCrtSkipMaxDigits) {
+      const int W = 2 * h.nl + 4, wbase = h.D32 > W ? h.D32 - W : 0;
+      const int g0 = wbase > 7 ? (wbase - 1) / 7 : 0;
+      if (g0 >= 2) {
+        h.crt_gskip = g0 - 1;
+        h.crt_nchunk = (npad_mm - 32 * h.crt_gskip + h.crt_cw - 1) / h.crt_cw;
+        h.crt_ngrp = h.crt_nchunk * h.crt_cw / 32;
+      }
+    }
     CrtHost* cp = &c;
     if (h.crt_mode != 0 && !c.tc_table.empty() && (c.rows != rows || c.npad != h.crt_npad)) {
       // another problem of this modulus set runs the other tensor-core CRT
@@ -1390,6 +1406,7 @@ static int build_image(ozaki2_plan_s* pl, const ozaki2_problem* probs, uint8_t* 
     P.crt_q = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_q) : nullptr;
     P.crt_alpha = h.crt_mode == 2 ? reinterpret_cast<uint32_t*>(ws + h.off_sig) : nullptr;
     P.crt_ngrp = h.crt_ngrp;
+    P.crt_gskip = h.crt_gskip;
     P.crt_nslot = h.crt_nslot;
     P.crt_nvbuf = h.crt_nvbuf;
     int rc = encode_planes(&tm[2 * i], P.pa, h.K, h.M, h.Kp, h.G, kBM);

@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   extern __shared__ __align__(16) uint32_t sf[];
   const int4 b = blk[blockIdx.x];
   const ProbDev& P = T.probs[b.x];
-  const int D = P.D32, ng = P.crt_ngrp;
+  const int D = P.D32, ng = P.crt_ngrp, gsk = P.crt_gskip;   // group sums stored from group gsk on
   const int DG = 7 * ((D + 6) / 7);     // digits rounded up to whole groups of seven
   const int W = 2 * P.nl + 4;
   const CrtView cv = crt_view(T.crt_pool, P);
@@ -930,17 +930,45 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   // out as those of R_up + c (R_up: R's digits from 7 gs on) with c, the
   // carry that was left out, at most alpha + 2 (every digit step adds below
   // (alpha + 2) 2^32 to a carry of at most alpha + 2).
+  // Where the group sums below group gsk were not formed and an output needs
+  // its full form, R comes from the plane GEMM's v_l instead: digit d of
+  // sum_l v_l M_l + alpha~ (2^(32 D) - P), carried digit by digit (each
+  // digit's sum stays below 2^56), into a per-thread array (from_v).
+  uint32_t Rv[kCrtSkipMaxDigits];
+  bool from_v = false;
+  auto fill_from_v = [&]() {
+    const int L = P.L, DS = P.DS;
+    uint64_t carry = 0;
+    for (int d = 0; d < D; ++d) {
+      uint64_t acc = carry + (uint64_t)alpha * s_negP[d];
+      for (int l = 0; l < L; ++l)
+        acc += (uint64_t)__ldg(P.u + (int64_t)l * up + idx) * __ldg(cv.Mdig + (int64_t)l * DS + d);
+      Rv[d] = (uint32_t)acc;
+      carry = acc >> 32;
+    }
+    from_v = true;
+  };
   auto for_each_group = [&](int gs, auto&& f) {
+    if (from_v) {
+      for (int g = gs; 7 * g < D; ++g) {
+        uint32_t r[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) r[k] = 7 * g + k < D ? Rv[7 * g + k] : 0u;
+        f(g, r);
+      }
+      return;
+    }
     uint32_t wc[9], wn[9];
     auto load = [&](int g, uint32_t (&w)[9]) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) w[k] = g < ng ? __ldg(qcol + ((int64_t)g * 9 + k) * up) : 0u;
+      for (int k = 0; k < 9; ++k)
+        w[k] = (g >= gsk && g - gsk < ng) ? __ldg(qcol + ((int64_t)(g - gsk) * 9 + k) * up) : 0u;
     };
     load(gs, wc);
     uint32_t prev7 = 0, prev8 = 0;
-    if (gs > 0) {
-      prev7 = __ldg(qcol + ((int64_t)(gs - 1) * 9 + 7) * up);
-      prev8 = __ldg(qcol + ((int64_t)(gs - 1) * 9 + 8) * up);
+    if (gs > 0) {                        // gs - 1 >= gsk: that group's sum is stored
+      prev7 = __ldg(qcol + ((int64_t)(gs - 1 - gsk) * 9 + 7) * up);
+      prev8 = __ldg(qcol + ((int64_t)(gs - 1 - gsk) * 9 + 8) * up);
     }
     uint64_t carry = 0;
     for (int g = gs; 7 * g < D; ++g) {
@@ -1039,7 +1067,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   // reads no word below the window; otherwise, and with the debug dump, the
   // output takes the full form from group 0.
   const int g0 = wbase > 7 ? (wbase - 1) / 7 : 0;
-  bool fast = dbg == nullptr && g0 > 0;
+  bool fast = dbg == nullptr && g0 > 0 && (gsk == 0 || gsk == g0 - 1);
   if (fast) {
     pass1(g0);
     ge = c1 != 0;
@@ -1055,6 +1083,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     }
   }
   if (!fast) {
+    if (gsk > 0) fill_from_v();          // the lower group sums were not formed
     exact = true;
     pass1(0);
     ge = c1 != 0;               // R >= P: x0 = R - P
@@ -1296,12 +1325,12 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int4 tl = tiles[i];
         const ProbDev& P = T.probs[tl.x];
         const CUtensorMap* mt = T.tmaps + 2 * T.count + tl.x;
-        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk;
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, col0 = 32 * P.crt_gskip;
         for (int c = 0; ok && c < nchunk; ++c) {
           for (int q = 0; q < nkb; ++q) {
             if (!mbar_wait(empty + st, ph ^ 1u, abort_flag, T.status, T.spin_limit)) { ok = false; break; }
             mbar_expect_tx(full + st, (uint32_t)cw * 128u);
-            tma_load_2d(sRing + st * stage_bytes, mt, smem_u32(full + st), q * 64, c * cw);
+            tma_load_2d(sRing + st * stage_bytes, mt, smem_u32(full + st), q * 64, col0 + c * cw);
             issued_phase[st] = (int)ph;
             if (++st == stages) { st = 0; ph ^= 1u; }
           }
@@ -1325,7 +1354,7 @@ __global__ void __launch_bounds__(kCmThreads, 1)
         const int4 tl = tiles[i];
         const bool first = i == (int)blockIdx.x;
         const ProbDev& P = T.probs[tl.x];
-        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad;
+        const int nkb = P.crt_kpad / 64, cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad - 32 * P.crt_gskip;
         const int nslot = P.crt_nslot, nvbuf = P.crt_nvbuf;
         const uint32_t vcols = (uint32_t)P.crt_kpad / 2;
         const int vb = nvbuf == 2 ? vnext : 0, vuse = vuses[vb]++;
@@ -1463,7 +1492,9 @@ __global__ void __launch_bounds__(kCmThreads, 1)
     auto epilogue = [&](int i) {
       const int4 tl = tiles[i];
       const ProbDev& P = T.probs[tl.x];
-      const int cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad, nslot = P.crt_nslot;
+      // columns from 32 crt_gskip on (the groups below are not formed); the
+      // group sums are stored from that group on
+      const int cw = P.crt_cw, nchunk = P.crt_nchunk, npad = P.crt_npad - 32 * P.crt_gskip, nslot = P.crt_nslot;
       const uint32_t acc0 = (uint32_t)P.crt_nvbuf * ((uint32_t)P.crt_kpad / 2);
       const bool small = 2 * P.L * 127 * 127 < (1 << 23);   // every column sum below 2^23
       const int64_t idx = (int64_t)tl.y * 128 + row;

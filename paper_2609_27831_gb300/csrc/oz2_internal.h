@@ -75,7 +75,9 @@ struct ProbDev {
   int32_t a_f64_trans, b_f64_trans;                          // binary64 operand read transposed
   int32_t e_scale_mode, pad1;                                // backward scaling (see fp64 notes)
   const int32_t* ext_scale;                                  // per-line extra exponent (backward)
-  int32_t ext_scale_axis, pad2;
+  int32_t ext_scale_axis;
+  int32_t crt_gskip;     // crt_mode 2, long finish: groups of 32 Y columns below this one are not
+                         // formed (the finish's fast form starts at it; stored group g is crt_gskip + g)
   int32_t DS;            // digit stride of the CRT tables (digits of the kernel class)
   int32_t crt_mode;      // 0: CUDA-core CRT; 1: column sums on the tensor cores (one kernel);
                          // 2: column sums on the tensor cores written as digits R, then the finish
@@ -109,6 +111,11 @@ struct ProbDev {
 //   negH1  [DS]            2^(32 D32) - (floor(P/2) + 1)
 //   Minv   [L]             M_l^{-1} mod m_l
 //   Mdig   [L][DS]         digits of M_l = P / m_l
+// The long CRT finish skips forming the lowest group sums (ProbDev::crt_gskip)
+// only up to this many accumulator digits: its full form then rebuilds R from
+// v_l in a per-thread array of this size.
+constexpr int kCrtSkipMaxDigits = 256;
+
 struct CrtView {
   const uint32_t* P; const uint32_t* negP; const uint32_t* negH1;
   const uint32_t* Minv; const uint32_t* Mdig;

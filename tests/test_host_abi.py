@@ -115,9 +115,9 @@ def test_null_pointer_errors(ozk):
 
 @pytest.mark.parametrize("p, cw_want", [(1024, 160), (2048, 160)])
 def test_crt_sum_engine_workspace(ozk, p, cw_want):
-    """crt_engine 2 adds the group sums ([groups of 32 columns][9][M N rounded
-    to 8] uint32) and the quotient estimates ([M N rounded to 8] uint32) to
-    the workspace where it applies, and nothing where it does not.  The table
+    """crt_engine 2 adds the group sums ([groups of 32 columns formed][9][M N
+    rounded to 8] uint32) and the quotient estimates ([M N rounded to 8]
+    uint32) to the workspace where it applies, and nothing where it does not.  The table
     has np 7-bit pieces of P and five quotient columns, padded to groups of 32;
     the chunk width: two TMEM slots beside V (kpad / 2 of 512 columns) unless
     that makes them narrower than 128 columns, then one slot."""
@@ -137,7 +137,16 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
         cw = min(256, (512 - kpad // 2) // 32 * 32)
     cw = min(cw, need)
     assert cw == cw_want
-    ngrp, up = -(-npad // cw) * cw // 32, 256 * 256
+    # the long finish (more than 24 digits) reads the group sums from group
+    # g0 - 1 on in its fast form (g0: the group just below its window of the
+    # 2 nl + 4 highest digits); the sums below are not formed
+    D, nl = plan.info["crt_digits"], -(-p // 64)
+    W = 2 * nl + 4
+    wbase = D - W if D > W else 0
+    g0 = (wbase - 1) // 7 if wbase > 7 else 0
+    gskip = g0 - 1 if D > 24 and g0 >= 2 else 0
+    assert gskip > 0
+    ngrp, up = -(-(npad - 32 * gskip) // cw) * cw // 32, 256 * 256
     a256 = lambda x: -(-x // 256) * 256
     assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(4 * up)
     small = (4, 4, 4, 53)                        # M N < 128: the CUDA-core CRT
