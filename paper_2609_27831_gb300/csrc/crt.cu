@@ -900,7 +900,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   const ProbDev& P = T.probs[b.x];
   const int D = P.D32, ng = P.crt_ngrp, gsk = P.crt_gskip;   // group sums stored from group gsk on
   const int DG = 7 * ((D + 6) / 7);     // digits rounded up to whole groups of seven
-  const int W = 2 * P.nl + 4;
+  const int W = 2 * P.nl + 4, Wcap = W + 6;   // window digits: used, held
   const CrtView cv = crt_view(T.crt_pool, P);
   // tables over DG digits: 2^(32 DG) - P and 2^(32 DG) - floor(P/2) - 1
   // (all ones from digit D on, so that every carry chain may run over whole
@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   uint32_t* s_negP = sf;                // [DG]
   uint32_t* s_negH1 = s_negP + DG;      // [DG]
   uint32_t* s_P = s_negH1 + DG;         // [DG]
-  uint32_t* s_win = s_P + DG;           // [W][128]
+  uint32_t* s_win = s_P + DG;           // [Wcap][128]
   for (int i = threadIdx.x; i < DG; i += kFinThreads) {
     s_P[i] = i < D ? __ldg(cv.P + i) : 0u;
     s_negP[i] = i < D ? __ldg(cv.negP + i) : ~0u;
@@ -1050,7 +1050,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
           topv = mag;
         }
         if (d >= wbase) {
-          if (d < wbase + W) s_win[(d - wbase) * kFinThreads + e] = mag;
+          if (d < wbase + Wcap) s_win[(d - wbase) * kFinThreads + e] = mag;
         } else {
           sticky |= mag;
         }
@@ -1060,12 +1060,13 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     bad = cc;
   };
   int wbase = D > W ? D - W : 0;
-  // Fast form: both passes from group g0 on (d0 = 7 g0 below the window),
-  // about half the group words where D is large.  It stands when every
-  // digit d0 it uses is safe, some digit between d0 and the window is
-  // nonzero (so the sticky bit is set whatever lies below) and the rounding
-  // reads no word below the window; otherwise, and with the debug dump, the
-  // output takes the full form from group 0.
+  // Fast form: both passes from group g0 on (d0 = 7 g0, just below the
+  // window), about half the group words where D is large; its window holds
+  // every digit above d0 (at most W + 6).  It stands when every digit d0 it
+  // uses is safe, the round bit lies above d0 and some bit between d0 and
+  // the round bit is nonzero (the sticky bit is then set whatever lies
+  // below); otherwise, and with the debug dump, the output takes the full
+  // form from group 0.
   const int g0 = wbase > 7 ? (wbase - 1) / 7 : 0;
   bool fast = dbg == nullptr && g0 > 0 && (gsk == 0 || gsk == g0 - 1);
   if (fast) {
@@ -1074,12 +1075,19 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     neg = ge ? c4 != 0 : c3 != 0;
     fast = exact;
     if (fast) {
-      magnitude(wbase, false, g0);
-      fast = exact && sticky != 0u && top >= wbase;
+      const int wf = 7 * g0 + 1;                           // the lowest exact digit
+      magnitude(wf, false, g0);
+      fast = exact && top >= wf;
       if (fast) {
-        const int n = 32 * top + 32 - __clz(topv);
-        fast = (n > P.p ? (n - P.p - 1) >> 5 : 0) >= wbase;
+        const int rpos = 32 * top + 32 - __clz(topv) - P.p - 1;
+        fast = rpos >= 32 * wf;
+        if (fast) {
+          uint32_t st = s_win[((rpos >> 5) - wf) * kFinThreads + e] & ((1u << (rpos & 31)) - 1u);
+          for (int w = (rpos >> 5) - 1; w >= wf && !st; --w) st = s_win[(w - wf) * kFinThreads + e];
+          fast = st != 0u;
+        }
       }
+      if (fast) wbase = wf;
     }
   }
   if (!fast) {
@@ -1102,7 +1110,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     }
   }
   if (bad) atomicOr(T.status, kStatusCrtRange);
-  crt_round_write(P, s_win, kFinThreads, e, W, top, neg, idx, ef, wbase, sticky);
+  crt_round_write(P, s_win, kFinThreads, e, min(Wcap, D - wbase), top, neg, idx, ef, wbase, sticky);
 }
 
 // The finish of short accumulators (D <= ND digits, used up to 24) after the
@@ -1701,7 +1709,9 @@ cudaError_t launch_crt_mm(const DevTables& t, const int32_t* tiles, int ntiles, 
   return cudaGetLastError();
 }
 
-int crt_finish_long_smem(int dmax, int nlmax) { return 3 * (dmax + 6) * 4 + (2 * nlmax + 4) * kFinThreads * 4; }
+// tables (three of up to dmax + 6 digits) and the window of 2 nl + 10 digits
+// per output (2 nl + 4, and six more for the fast form's window)
+int crt_finish_long_smem(int dmax, int nlmax) { return 3 * (dmax + 6) * 4 + (2 * nlmax + 10) * kFinThreads * 4; }
 
 cudaError_t launch_crt_finish_long(const DevTables& t, const int32_t* blk, int nblk, int dmax, int nlmax,
                                    cudaStream_t s) {
