@@ -915,13 +915,15 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
     s_negH1[i] = i < D ? __ldg(cv.negH1 + i) : ~0u;
   }
   __syncthreads();
-  const int e = threadIdx.x;
-  const int64_t idx = (int64_t)b.y * kFinThreads + e;
-  if (idx >= (int64_t)P.M * P.N) return;
-  const int ef = crt_ef(P, idx);
+  const int e = threadIdx.x, lane = e & 31;
+  // lanes past the last output do no output work but join the warp-wide
+  // rebuild of R below
+  const bool valid = (int64_t)b.y * kFinThreads + e < (int64_t)P.M * P.N;
+  const int64_t idx = valid ? (int64_t)b.y * kFinThreads + e : 0;
+  const int ef = valid ? crt_ef(P, idx) : 0;
   const int64_t up = P.upitch;
   const uint32_t* const qcol = P.crt_q + idx;
-  const uint32_t alpha = __ldg(P.crt_alpha + idx);
+  const uint32_t alpha = valid ? __ldg(P.crt_alpha + idx) : 0u;
   // R seven digits at a time from group gs on, to f(g, r): word k of group g
   // is digit 7 g + k (k < 7); words 7 and 8 of group g add into digits
   // 7 g + 7 and 7 g + 8; digits from D on are zero.  The nine words of group
@@ -931,23 +933,11 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   // carry that was left out, at most alpha + 2 (every digit step adds below
   // (alpha + 2) 2^32 to a carry of at most alpha + 2).
   // Where the group sums below group gsk were not formed and an output needs
-  // its full form, R comes from the plane GEMM's v_l instead: digit d of
-  // sum_l v_l M_l + alpha~ (2^(32 D) - P), carried digit by digit (each
-  // digit's sum stays below 2^56), into a per-thread array (from_v).
+  // its full form, R comes from the plane GEMM's v_l instead, digit d of
+  // sum_l v_l M_l + alpha~ (2^(32 D) - P), built by the whole warp (below)
+  // into the owning thread's array (from_v).
   uint32_t Rv[kCrtSkipMaxDigits];
   bool from_v = false;
-  auto fill_from_v = [&]() {
-    const int L = P.L, DS = P.DS;
-    uint64_t carry = 0;
-    for (int d = 0; d < D; ++d) {
-      uint64_t acc = carry + (uint64_t)alpha * s_negP[d];
-      for (int l = 0; l < L; ++l)
-        acc += (uint64_t)__ldg(P.u + (int64_t)l * up + idx) * __ldg(cv.Mdig + (int64_t)l * DS + d);
-      Rv[d] = (uint32_t)acc;
-      carry = acc >> 32;
-    }
-    from_v = true;
-  };
   auto for_each_group = [&](int gs, auto&& f) {
     if (from_v) {
       for (int g = gs; 7 * g < D; ++g) {
@@ -1068,7 +1058,7 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
   // below); otherwise, and with the debug dump, the output takes the full
   // form from group 0.
   const int g0 = wbase > 7 ? (wbase - 1) / 7 : 0;
-  bool fast = dbg == nullptr && g0 > 0 && (gsk == 0 || gsk == g0 - 1);
+  bool fast = valid && dbg == nullptr && g0 > 0 && (gsk == 0 || gsk == g0 - 1);
   if (fast) {
     pass1(g0);
     ge = c1 != 0;
@@ -1090,8 +1080,51 @@ __global__ void __launch_bounds__(kFinThreads) k_crt_fin_long(DevTables T, const
       if (fast) wbase = wf;
     }
   }
+  // R from v_l for each lane whose fast form did not stand while the lower
+  // group sums were not formed, one such lane at a time by the whole warp:
+  // lane j sums the digits d = j mod 32 over every modulus (the digits of
+  // M_l read coalesced across the lanes, v_l one broadcast word; each sum is
+  // below L 2^46 + alpha~ 2^32 < 2^56), then every lane runs the same carry
+  // chain over the digits (each fetched from its lane) and the owner keeps
+  // them.
+  {
+    const unsigned need = __ballot_sync(0xffffffffu, valid && !fast && gsk > 0);
+    const int L = P.L, DS = P.DS;
+    for (unsigned m = need; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const int64_t sidx = __shfl_sync(0xffffffffu, idx, src);
+      const uint32_t salpha = __shfl_sync(0xffffffffu, alpha, src);
+      constexpr int kJ = kCrtSkipMaxDigits / 32;
+      uint64_t acc[kJ];
+#pragma unroll
+      for (int j = 0; j < kJ; ++j) {
+        const int d = 32 * j + lane;
+        acc[j] = d < D ? (uint64_t)salpha * s_negP[d] : 0ull;
+      }
+      for (int l = 0; l < L; ++l) {
+        const uint64_t v = __ldg(P.u + (int64_t)l * up + sidx);
+        const uint32_t* ml = cv.Mdig + (int64_t)l * DS;
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) {
+          const int d = 32 * j + lane;
+          if (32 * j < D && d < D) acc[j] += v * __ldg(ml + d);
+        }
+      }
+      uint64_t c = 0;
+#pragma unroll
+      for (int j = 0; j < kJ; ++j) {
+        if (32 * j >= D) break;
+        for (int ln = 0; ln < 32 && 32 * j + ln < D; ++ln) {
+          const uint64_t x = __shfl_sync(0xffffffffu, acc[j], ln) + c;
+          c = x >> 32;
+          if (lane == src) Rv[32 * j + ln] = (uint32_t)x;
+        }
+      }
+      if (lane == src) from_v = true;
+    }
+  }
+  if (!valid) return;
   if (!fast) {
-    if (gsk > 0) fill_from_v();          // the lower group sums were not formed
     exact = true;
     pass1(0);
     ge = c1 != 0;               // R >= P: x0 = R - P
