@@ -246,7 +246,8 @@ DP4A_MACS_PER_SM_CLK = 64 * 4
 # capture of one launch after its last change); the source summaries are
 # under profiles/.  A kernel changed since its capture is absent.
 NCU_TRAFFIC = {
-    "gemm_4096_p2048": {"scan": 403952064, "residues": 82207492672, "gemm": 122832939456},
+    "gemm_4096_p2048": {"scan": 403911680, "residues": 82033706496, "gemm": 121773933248,
+                        "crt_sums": 20133005952, "crt_finish": 11299742848},
     "gemm_1024_p256": {"scan": 25205376, "residues": 440525568, "gemm": 562085952,
                        "crt_sums": 222810624, "crt_finish": 125142528},
 }
@@ -273,10 +274,11 @@ def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False)
       sum_l v_l M_l, L per output and digit of M_l: M N L ceil(bits(P)/32),
       against the IMAD.WIDE rate.
     crt_sums (tensor-core CRT): the exact bf16 products of the column sums
-      Y = V B, 2 M N (2L) np flops with np 7-bit pieces of P, against the
-      bf16 tensor peak.
-    crt_finish (after the sums): the bytes it moves, the group words it reads
-      (D + 2 ceil(D/7) per output), the 4-byte quotient estimate and the
+      Y = V B that are formed, 2 M N (2L) (np - 32 s) flops with np 7-bit
+      pieces of P and s groups of 32 not formed (`crt_skip_groups`: below the
+      long finish's fast form), against the bf16 tensor peak.
+    crt_finish (after the sums): the bytes it moves, the group words formed
+      (9 per group of 32 pieces), the 4-byte quotient estimate and the
       output (8 nl + 5 bytes), against HBM.
     scan: the bytes of the two exponent vectors' inputs, against HBM.
 
@@ -321,7 +323,7 @@ def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False)
         alu("crt", "k_crt1 / k_crt (direct CRT sum + quotient correction + rounding)", M * N * L * md,
             SMS * IMAD_WIDE_PER_SM_CLK * clk, "imad64")
     if "crt_sums" in stages:
-        np_ = info["crt_pieces"]
+        np_ = info["crt_pieces"] - 32 * info.get("crt_skip_groups", 0)
         fl = 2.0 * M * N * (2 * L) * np_
         ach = fl / (stages["crt_sums"] / 1e3) / 1e12
         out["crt_sums"] = {"kernel": "k_crt_mm (CRT column sums as an exact bf16 GEMM + group carries)",
@@ -330,7 +332,8 @@ def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False)
                            "traffic": traffic.get("crt_sums")}
         D = info["crt_digits"]
         nl = -(-p // 64)
-        fb = M * N * (4 * (D + 2 * -(-D // 7)) + 4 + 8 * nl + 5)
+        ngrp = -(-(info["crt_pieces"] + 5) // 32) - info.get("crt_skip_groups", 0)
+        fb = M * N * (4 * 9 * ngrp + 4 + 8 * nl + 5)
         ach = fb / (stages["crt_finish"] / 1e3) / 1e9
         pk = float(peaks["hbm_gbs"])
         out["crt_finish"] = {"kernel": f"{finish_kernel(D)} (CRT finish from the group sums + rounding)",
@@ -359,10 +362,9 @@ def stage_rooflines(info, M, N, K, p, stages, workload, sustained: bool = False)
               "gemm": G * (M + N) * Kp * pb + v_bytes,
               "crt": v_bytes + c_out}
     if "crt_sums" in stages:
-        ngrp = -(-(info["crt_pieces"] + 5) // 32)
-        D = info["crt_digits"]
+        ngrp = -(-(info["crt_pieces"] + 5) // 32) - info.get("crt_skip_groups", 0)
         nbytes["crt_sums"] = v_bytes + M * N * (ngrp * 9 * 4 + 4)
-        nbytes["crt_finish"] = M * N * (4 * (D + 2 * -(-D // 7)) + 4) + c_out
+        nbytes["crt_finish"] = M * N * (4 * 9 * ngrp + 4) + c_out
     hpk = float(peaks["hbm_gbs"])
     for name, ms in stages.items():
         if name in out and name in nbytes:

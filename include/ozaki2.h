@@ -143,6 +143,8 @@ typedef struct {
   int plane_groups; /* modulus groups the planes of problem 0 are streamed in (1: not streamed) */
   int group_planes; /* planes of the largest group (= G when not streamed) */
   int gemm_tile;    /* plane GEMM tile in use: 1 (128 x 256, one SM) or 2 (256 x 256, CTA pairs) */
+  int crt_skip_groups; /* crt_mode 2 with the long finish: groups of 32 column sums (7-bit pieces
+                       of P) below the ones the finish's fast form reads, not formed (0: none) */
 } ozaki2_info;
 
 typedef struct {

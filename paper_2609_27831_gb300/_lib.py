@@ -34,7 +34,7 @@ class Info(C.Structure):
                 ("G", C.c_int), ("crt_digits", C.c_int), ("units", C.c_int),
                 ("jobs", C.c_int), ("workspace_bytes", C.c_size_t), ("crt_mode", C.c_int),
                 ("res_mode", C.c_int), ("plane_groups", C.c_int), ("group_planes", C.c_int),
-                ("gemm_tile", C.c_int)]
+                ("gemm_tile", C.c_int), ("crt_skip_groups", C.c_int)]
 
 
 class Problem(C.Structure):

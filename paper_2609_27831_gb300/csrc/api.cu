@@ -1840,6 +1840,7 @@ int ozaki2_plan_info(ozaki2_plan pl, ozaki2_info* out) {
   out->L1 = h.L1;
   out->G = h.G;
   out->crt_digits = h.D32;
+  out->crt_skip_groups = h.crt_gskip;
   out->units = (int)std::min<int64_t>(INT_MAX, pl->total_units);
   out->jobs = (int)std::min<int64_t>(INT_MAX, pl->total_jobs);
   out->workspace_bytes = pl->ws_bytes;

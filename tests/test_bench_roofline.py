@@ -70,3 +70,20 @@ def test_tensor_core_residues_against_the_tensor_peak():
     macs = (M + N) * K * -(-283 // 8) * (54 + 2 * 16)
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(2.0 * macs / 0.5e-3 / 1e12, abs=0.05)
+
+
+def test_skipped_crt_groups_are_not_counted():
+    """Where the long finish's fast form leaves the lowest groups of 32 column
+    sums unformed (crt_skip_groups), the CRT sums count only the formed
+    columns' products and the group words written, and the finish the group
+    words it reads."""
+    M = N = 256
+    K = 4096
+    info = _info(L=329, L1=54, G=879, t=2076, crt_digits=133, crt_pieces=635, crt_skip_groups=8)
+    st = {"scan": 0.02, "residues": 2.0, "gemm": 4.0, "crt_sums": 1.0, "crt_finish": 0.3}
+    out = bench.stage_rooflines(info, M, N, K, 2048, st, "none")
+    assert out["crt_sums"]["achieved"] == pytest.approx(2.0 * M * N * 658 * (635 - 256) / 1e-3 / 1e12, abs=0.05)
+    ngrp = -(-(635 + 5) // 32) - 8                       # 20 groups, 12 formed
+    assert out["crt_sums"]["hbm"]["bytes"] == 329 * M * N * 2 + M * N * (ngrp * 9 * 4 + 4)
+    per = 4 * 9 * ngrp + 4 + 8 * 32 + 5
+    assert out["crt_finish"]["achieved"] == pytest.approx(M * N * per / 0.3e-3 / 1e9, abs=0.05)

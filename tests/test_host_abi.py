@@ -145,7 +145,7 @@ def test_crt_sum_engine_workspace(ozk, p, cw_want):
     wbase = D - W if D > W else 0
     g0 = (wbase - 1) // 7 if wbase > 7 else 0
     gskip = g0 - 1 if D > 24 and g0 >= 2 else 0
-    assert gskip > 0
+    assert gskip > 0 and plan.info["crt_skip_groups"] == gskip
     ngrp, up = -(-(npad - 32 * gskip) // cw) * cw // 32, 256 * 256
     a256 = lambda x: -(-x // 256) * 256
     assert plan.info["workspace_bytes"] - base["workspace_bytes"] == a256(4 * ngrp * 9 * up) + a256(4 * up)
