@@ -1211,7 +1211,10 @@ __global__ void __launch_bounds__(kFinThreads, (ND <= 24 ? 6 : 1)) k_crt_fin_sho
 //   Q_g = sum_{q < 32} Y_{32 g + q} 2^(7 q),   S = sum_g Q_g 2^(224 g),
 // with piece q in word 7 q / 32 at shift 7 q mod 32 (both constants); each
 // Q_g is written on its own as 9 words (7 carried word sums and the carry),
-// and the finish adds the groups and alpha~ (2^(32 D) - P).
+// and the finish adds the groups and alpha~ (2^(32 D) - P).  With
+// crt_gskip > 0 (the long finish, whose fast form reads no lower group) the
+// columns start at 32 crt_gskip: the groups below are not formed, and stored
+// group i is group crt_gskip + i.
 //   warp 0      TMA producer of the B blocks, in (chunk, K block) order
 //   warp 1      MMA issuer: chunks into the slots in turn (one slot: always
 //               slot 0); commits per ring stage, per chunk and per tile
