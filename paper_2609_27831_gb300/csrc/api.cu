@@ -1054,10 +1054,10 @@ static int build_table_image(ozaki2_plan_s* pl, int sms, TableImage& ti) {
       ti.tct_l[h.crt_cls] = std::max(ti.tct_l[h.crt_cls], h.L);
     } else if (h.crt_mode == 2) {
       // sums on the tensor cores, then the finish from the group sums: R in
-      // registers up to 24 digits (k_crt_fin_short), else in shared memory
-      // (k_crt_fin_long, ahead from 28 digits on: at 37 digits 1.53 vs 1.75
-      // ms at 2048^3, its 40 registers keep more warps resident); both load
-      // every group word at once
+      // registers up to 24 digits (k_crt_fin_short, every group word loaded
+      // at once), else digit-serial passes over the group words with a window
+      // of the highest digits in shared memory (k_crt_fin_long, its fast form
+      // from the group below the window on)
       const int64_t nt = (h.M * h.N + 127) / 128;
       if (nt > INT_MAX) return OZ2_ERANGE;
       std::vector<int4>& cl = cmt_by[{h.crt_kpad, h.crt_cw, h.crt_nslot}];
