@@ -301,3 +301,22 @@ def test_complex_plan_host_facts(ozk):
     lib = ozk.lib()
     arr = (ozk._lib.Problem * 3)()
     assert lib.ozaki2_execute_batched(plan._h, 3, arr, 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
+
+
+@pytest.mark.parametrize("p", [600, 800, 1024, 1500, 2048])
+def test_crt_groups_skipped_below_the_fast_finish(ozk, p):
+    """The CRT sums leave unformed exactly the groups of 32 column sums below
+    group g0 - 1, g0 being the group whose lowest digit lies just below the
+    long finish's window of 2 nl + 4 digits (the same rule the finish applies
+    to choose its fast form), and only for the long finish (more than 24
+    digits)."""
+    plan = ozk.Plan((256, 256, 64, p), crt_engine=2)
+    inf = plan.info
+    D, nl = inf["crt_digits"], -(-p // 64)
+    W = 2 * nl + 4
+    wbase = D - W if D > W else 0
+    g0 = (wbase - 1) // 7 if wbase > 7 else 0
+    want = g0 - 1 if inf["crt_mode"] == 2 and D > 24 and g0 >= 2 else 0
+    assert inf["crt_skip_groups"] == want
+    if p >= 1024:
+        assert want > 0
