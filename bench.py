@@ -249,7 +249,7 @@ NCU_TRAFFIC = {
     "gemm_4096_p2048": {"scan": 403911680, "residues": 82033706496, "gemm": 121773933248,
                         "crt_sums": 20133005952, "crt_finish": 11299742848},
     "gemm_1024_p256": {"scan": 25205376, "residues": 440525568, "gemm": 562085952,
-                       "crt_sums": 222810624, "crt_finish": 125142528},
+                       "crt_finish": 125142528},
 }
 
 
