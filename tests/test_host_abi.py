@@ -303,7 +303,7 @@ def test_complex_plan_host_facts(ozk):
     assert lib.ozaki2_execute_batched(plan._h, 3, arr, 256, 1 << 30, None) == ozk._lib.OZ2_EINVAL
 
 
-@pytest.mark.parametrize("p", [600, 800, 1024, 1500, 2048])
+@pytest.mark.parametrize("p", [256, 300, 600, 800, 1024, 1500, 2048])
 def test_crt_groups_skipped_below_the_fast_finish(ozk, p):
     """The CRT sums leave unformed exactly the groups of 32 column sums below
     group g0 - 1, g0 being the group whose lowest digit lies just below the
@@ -320,3 +320,6 @@ def test_crt_groups_skipped_below_the_fast_finish(ozk, p):
     assert inf["crt_skip_groups"] == want
     if p >= 1024:
         assert want > 0
+    if D <= 24:                                          # the short finish reads every group
+        assert want == 0
+    assert ozk.Plan((256, 256, 64, p), crt_engine=3).info["crt_skip_groups"] == 0
